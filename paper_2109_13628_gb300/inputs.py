@@ -1,0 +1,280 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA parity tests and bench.py.
+
+This module holds no arithmetic of the immersed interface method itself: it only builds
+grids, level sets, right-hand sides, boundary data and bounding regions in the shapes of the
+paper's flows (cylinders, nonconvex bodies, Lamb-Oseen / Gaussian vorticity).  Both the
+oracle and the CUDA path consume what it returns; neither is imported here.
+
+Conventions (used everywhere in this project):
+  * a box [x0,x1]x[y0,y1] split into nx x ny cells of size h; nodes (i, j), i = 0..nx,
+    j = 0..ny; unknowns live on interior nodes i = 1..nx-1, j = 1..ny-1;
+  * node arrays have shape (ny+1, nx+1), interior arrays (ny-1, nx-1), x fastest;
+  * level set phi < 0 is solid, phi >= 0 is fluid;
+  * a bounding region R_k is the inclusive node box (lx, rx, ly, ry) (Sec. 3.1, Eq. sum_R_def).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Grid:
+    x0: float
+    x1: float
+    y0: float
+    y1: float
+    nx: int
+    ny: int
+
+    @property
+    def h(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    def nodes(self):
+        """Node coordinates as (X, Y), each of shape (ny+1, nx+1)."""
+        x = self.x0 + self.h * np.arange(self.nx + 1)
+        y = self.y0 + self.h * np.arange(self.ny + 1)
+        return np.meshgrid(x, y)
+
+    def interior(self):
+        X, Y = self.nodes()
+        return X[1:-1, 1:-1], Y[1:-1, 1:-1]
+
+
+def square_grid(n: int, half: float = 2.0) -> Grid:
+    return Grid(-half, half, -half, half, n, n)
+
+
+# ----------------------------------------------------------------------------- level sets
+def phi_circle(X, Y, xc, yc, R):
+    return np.hypot(X - xc, Y - yc) - R
+
+
+def phi_ellipse(X, Y, xc, yc, a, b, angle):
+    c, s = math.cos(angle), math.sin(angle)
+    xr = c * (X - xc) + s * (Y - yc)
+    yr = -s * (X - xc) + c * (Y - yc)
+    return (np.sqrt((xr / a) ** 2 + (yr / b) ** 2) - 1.0) * min(a, b)
+
+
+def phi_annulus(X, Y, xc, yc, r_in, r_out):
+    r = np.hypot(X - xc, Y - yc)
+    return np.maximum(r_in - r, r - r_out)
+
+
+def phi_star(X, Y, xc, yc, r0=0.5, amp=0.15, petals=5):
+    dx, dy = X - xc, Y - yc
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    return r - (r0 + amp * np.cos(petals * th))
+
+
+def union(*phis):
+    """Solid where any body is solid."""
+    out = phis[0]
+    for p in phis[1:]:
+        out = np.minimum(out, p)
+    return out
+
+
+def region_around(grid: Grid, phi_body, margin: int = 3):
+    """Inclusive node box around one body's solid nodes, grown by `margin` nodes beyond the
+    affected layer (solid nodes grown by one node are the affected points)."""
+    js, is_ = np.nonzero(phi_body < 0)
+    lx = int(is_.min()) - 1 - margin
+    rx = int(is_.max()) + 1 + margin
+    ly = int(js.min()) - 1 - margin
+    ry = int(js.max()) + 1 + margin
+    return (lx, rx, ly, ry)
+
+
+# ----------------------------------------------------------------------------- vorticity
+def gaussian_vortices(X, Y, centers, strengths, sigma):
+    """Sum of Gaussian (Lamb-Oseen shaped, Eq. lovorticity with sigma^2 = 2 nu t) vortices."""
+    w = np.zeros_like(X)
+    for (cx, cy), s in zip(centers, strengths):
+        w += s / (2.0 * math.pi * sigma * sigma) * np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / (2.0 * sigma * sigma))
+    return w
+
+
+def lamb_oseen(X, Y, x0, y0, gamma, nu_t):
+    """Lamb-Oseen vorticity and velocity (Eqs. lovorticity, lovelocity)."""
+    dx, dy = X - x0, Y - y0
+    r2 = dx * dx + dy * dy
+    w = gamma / (4.0 * math.pi * nu_t) * np.exp(-r2 / (4.0 * nu_t))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        f = np.where(r2 > 0, gamma / (2.0 * math.pi * r2) * (1.0 - np.exp(-r2 / (4.0 * nu_t))), 0.0)
+    return w, -f * dy, f * dx
+
+
+# ----------------------------------------------------------------------------- manufactured
+def psi_c1(X, Y):
+    """Streamfunction of the single-cylinder manufactured case: sin(pi x/2) sin(pi y/2) + 0.1 log r."""
+    with np.errstate(divide="ignore"):
+        return np.sin(np.pi * X / 2) * np.sin(np.pi * Y / 2) + 0.1 * np.log(np.hypot(X, Y))
+
+
+def omega_c1(X, Y):
+    """-Laplacian of psi_c1 (log r is harmonic away from the origin)."""
+    return (np.pi ** 2 / 2) * np.sin(np.pi * X / 2) * np.sin(np.pi * Y / 2)
+
+
+def bicubic_coeffs(seed: int):
+    """Random coefficients c[a, b] of a polynomial sum c_ab x^a y^b with a, b <= 3."""
+    rng = np.random.default_rng(seed)
+    return rng.normal(size=(4, 4))
+
+
+def bicubic(X, Y, c):
+    out = np.zeros_like(X)
+    for a in range(4):
+        for b in range(4):
+            out = out + c[a, b] * X ** a * Y ** b
+    return out
+
+
+def bicubic_neg_laplacian(X, Y, c):
+    out = np.zeros_like(X)
+    for a in range(4):
+        for b in range(4):
+            if a >= 2:
+                out = out - c[a, b] * a * (a - 1) * X ** (a - 2) * Y ** b
+            if b >= 2:
+                out = out - c[a, b] * b * (b - 1) * X ** a * Y ** (b - 2)
+    return out
+
+
+def box_ring(grid: Grid, node_values):
+    """Pack box-node data in the order used by the solver: bottom row j=0 (i=0..nx), top row
+    j=ny (i=0..nx), left column i=0 (j=1..ny-1), right column i=nx (j=1..ny-1)."""
+    v = np.asarray(node_values)
+    return np.concatenate([v[0, :], v[-1, :], v[1:-1, 0], v[1:-1, -1]]).astype(np.float64)
+
+
+# ----------------------------------------------------------------------------- workloads
+@dataclasses.dataclass
+class Problem:
+    grid: Grid
+    phi: np.ndarray               # (ny+1, nx+1)
+    regions: list                 # [(lx, rx, ly, ry)] per body
+    modes: list                   # 0 fixed psibar, 1 circulation given
+    omega: np.ndarray             # (ny-1, nx-1) interior, zero in the solid
+    psi_box: np.ndarray           # 2 (nx + ny) box ring
+    psi_b_fn: object              # callable (x, y, body) -> psi_b at control points
+    psibar: np.ndarray            # per body: given value (fixed) / expected value (circulation)
+    gamma: np.ndarray | None      # per body circulation (circulation mode) or None
+    exact: np.ndarray | None      # exact node-array streamfunction where known
+    name: str = ""
+
+
+def _mask_interior(grid, phi, field_nodes):
+    w = np.where(phi >= 0, field_nodes, 0.0)
+    return np.ascontiguousarray(w[1:-1, 1:-1])
+
+
+def c1_cylinder(n: int = 128) -> Problem:
+    """Manufactured single-cylinder problem on [-2,2]^2 with n x n cells, circle R=0.5."""
+    g = square_grid(n)
+    X, Y = g.nodes()
+    phi = phi_circle(X, Y, 0.0, 0.0, 0.5)
+    psi = psi_c1(X, Y)
+    return Problem(
+        grid=g, phi=phi, regions=[region_around(g, phi)], modes=[0],
+        omega=_mask_interior(g, phi, omega_c1(X, Y)),
+        psi_box=box_ring(g, psi),
+        psi_b_fn=lambda x, y, body: psi_c1(x, y),
+        psibar=np.zeros(1), gamma=None, exact=psi, name=f"c1_cylinder_{n}")
+
+
+def bicubic_bodies(n: int, seed: int = 0, circulation: bool = True, offsets=(0.3, -0.7, 0.15)) -> Problem:
+    """Polynomial-exactness workload: a bicubic streamfunction psi* around a cylinder, an ellipse
+    and a nonconvex star.  The discrete IIM solution equals psi* at every fluid node (to
+    rounding), for any n.  psi_b = psi* - offset_k so the expected body constants are offset_k."""
+    g = square_grid(n)
+    X, Y = g.nodes()
+    bodies = [phi_circle(X, Y, -0.9, -0.8, 0.45),
+              phi_ellipse(X, Y, 0.9, -0.7, 0.5, 0.3, 0.6),
+              phi_star(X, Y, 0.0, 0.85, 0.55, 0.1, 4)]
+    phi = union(*bodies)
+    c = bicubic_coeffs(seed)
+    psi = bicubic(X, Y, c)
+    regions = [region_around(g, b) for b in bodies]
+    offs = np.array(offsets[: len(bodies)], dtype=np.float64)
+    mode = 1 if circulation else 0
+    return Problem(
+        grid=g, phi=phi, regions=regions, modes=[mode] * len(bodies),
+        omega=_mask_interior(g, phi, bicubic_neg_laplacian(X, Y, c)),
+        psi_box=box_ring(g, psi),
+        psi_b_fn=lambda x, y, body: bicubic(x, y, c) - offs[body],
+        psibar=offs.copy(), gamma=None, exact=psi, name=f"bicubic_{n}_s{seed}")
+
+
+def separated_centers(rng, n_bodies, lo, hi, radii, gap):
+    """Rejection-sample centers in [lo,hi]^2 keeping circles of the given radii `gap` apart."""
+    centers = []
+    for r in radii:
+        for _ in range(10000):
+            c = rng.uniform(lo, hi, size=2)
+            if all(np.hypot(*(c - c2)) >= r + r2 + gap for c2, r2 in zip(centers, radii)):
+                centers.append(c)
+                break
+        else:
+            raise RuntimeError("could not place bodies")
+    return centers
+
+
+def vortex_field(g: Grid, seed: int, count: int = 50, sigma: float = 0.1, lo=None, hi=None):
+    rng = np.random.default_rng(seed)
+    lo = g.x0 if lo is None else lo
+    hi = g.x1 if hi is None else hi
+    centers = rng.uniform(lo, hi, size=(count, 2))
+    strengths = rng.normal(size=count)
+    X, Y = g.nodes()
+    return gaussian_vortices(X, Y, centers, strengths, sigma)
+
+
+def multibody(n: int = 2048, half: float = 4.0, seed: int = 0) -> Problem:
+    """Multiply connected, nonconvex geometry: three circles (R in [0.3, 0.6]), an annulus
+    (0.4 / 0.8) and a five-petal star, centers seeded in [-3,3]^2; 50 Gaussian vortices
+    (sigma = 0.1, strengths N(0,1), seed 1).  Bodies in circulation mode with Gamma_k equal
+    to the vorticity summed over R_k (zero circulation on the body itself)."""
+    g = square_grid(n, half)
+    X, Y = g.nodes()
+    rng = np.random.default_rng(seed)
+    radii_c = rng.uniform(0.3, 0.6, size=3)
+    extent = list(radii_c) + [0.8, 0.65]
+    centers = separated_centers(rng, 5, -3.0, 3.0, extent, 0.25)
+    bodies = [phi_circle(X, Y, centers[k][0], centers[k][1], radii_c[k]) for k in range(3)]
+    bodies.append(phi_annulus(X, Y, centers[3][0], centers[3][1], 0.4, 0.8))
+    bodies.append(phi_star(X, Y, centers[4][0], centers[4][1], 0.5, 0.15, 5))
+    phi = union(*bodies)
+    w_nodes = vortex_field(g, seed + 1, 50, 0.1, -half, half)
+    omega = _mask_interior(g, phi, w_nodes)
+    regions = [region_around(g, b) for b in bodies]
+    return Problem(grid=g, phi=phi, regions=regions, modes=[1] * 5, omega=omega,
+                   psi_box=np.zeros(2 * (g.nx + g.ny)), psi_b_fn=lambda x, y, body: np.zeros_like(x),
+                   psibar=np.zeros(5), gamma=None, exact=None, name=f"multibody_{n}")
+
+
+def ellipses_problem(n: int, seed: int) -> Problem:
+    """One batched-workload problem: [-2,2]^2, 1-4 ellipses (semi-axes in [0.2,0.6], random
+    orientation), Gaussian-vortex right-hand side, circulation mode."""
+    g = square_grid(n)
+    X, Y = g.nodes()
+    rng = np.random.default_rng(seed)
+    nb = int(rng.integers(1, 5))
+    axes = rng.uniform(0.2, 0.6, size=(nb, 2))
+    angles = rng.uniform(0.0, math.pi, size=nb)
+    gap = max(0.25, 8.0 * g.h)
+    centers = separated_centers(rng, nb, -1.3, 1.3, list(axes.max(axis=1)), gap)
+    bodies = [phi_ellipse(X, Y, centers[k][0], centers[k][1], axes[k, 0], axes[k, 1], angles[k]) for k in range(nb)]
+    phi = union(*bodies)
+    w_nodes = vortex_field(g, seed + 7, 50, 0.1)
+    regions = [region_around(g, b) for b in bodies]
+    return Problem(grid=g, phi=phi, regions=regions, modes=[1] * nb,
+                   omega=_mask_interior(g, phi, w_nodes), psi_box=np.zeros(2 * (g.nx + g.ny)),
+                   psi_b_fn=lambda x, y, body: np.zeros_like(x), psibar=np.zeros(nb), gamma=None,
+                   exact=None, name=f"ellipses_{n}_s{seed}")
