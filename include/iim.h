@@ -1,0 +1,166 @@
+/*
+ * iim.h -- C ABI of the GB300 immersed interface Poisson library.
+ *
+ * The library solves the IIM-corrected discrete Poisson problem that reconstructs the
+ * streamfunction (and velocity) from vorticity around several immersed bodies, as stated in
+ * Gabbard, Gillis, Chatelain & van Rees, "An immersed interface method for the 2D
+ * vorticity-velocity Navier-Stokes equations with multiple bodies", Sec. 4.2 (the discrete
+ * problem: Eqs. discretepoisson, poissoncorrections, schur, psirecovery, and the augmented
+ * system with the circulation rows), with the geometry of Sec. 2.2 / App. A and the
+ * polynomial extrapolation of Sec. 2.1.
+ *
+ * Conventions shared by every entry point
+ *   - Grid: the box [x0,x1] x [y0,y1] is split into nx x ny square cells, h = (x1-x0)/nx =
+ *     (y1-y0)/ny.  nx and ny must be powers of two in [16, 2048].  Node (i, j) sits at
+ *     (x0 + i h, y0 + j h), i = 0..nx, j = 0..ny.  Unknowns live on the interior nodes.
+ *   - Layouts (row-major, x fastest, FP64 unless stated otherwise):
+ *       node arrays      (ny+1) x (nx+1), element (i, j) at j*(nx+1) + i
+ *       interior arrays  (ny-1) x (nx-1), element (i, j) at (j-1)*(nx-1) + (i-1)
+ *       box ring         2(nx+ny) values: bottom row j=0 (i=0..nx), top row j=ny (i=0..nx),
+ *                        left column i=0 (j=1..ny-1), right column i=nx (j=1..ny-1)
+ *   - Level set: phi < 0 is solid, phi >= 0 is fluid (a zero counts as fluid).
+ *   - Every array argument is a DEVICE pointer unless marked "host".  All device memory
+ *     passed in is owned by the caller; the library owns only what an iim_geometry
+ *     allocates (released by iim_destroy_geometry).
+ *   - Work is issued on `stream` (NULL = the legacy default stream).  Entry points that
+ *     return statistics synchronize that stream before returning.
+ *   - Every entry point returns an iim_status; no C++ exception crosses the ABI.
+ */
+#ifndef IIM_H
+#define IIM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* iim_stream; /* identical to cudaStream_t */
+typedef struct iim_geometry_s* iim_geometry;
+typedef int iim_status;
+
+enum {
+    IIM_OK = 0,
+    IIM_ERR_INVALID_ARG = -1,   /* null pointer, bad size, grid not a power of two, ... */
+    IIM_ERR_UNDERRESOLVED = -2, /* an A- point has no usable extrapolation direction (Sec. 2.2) */
+    IIM_ERR_BAD_REGION = -3,    /* an affected point lies in no / several R_k, a region's faces
+                                   are not in plain fluid, a body is within 5 nodes of the box,
+                                   or a box node is solid */
+    IIM_ERR_NONFINITE = -4,     /* NaN/Inf met in the inputs or in a residual */
+    IIM_ERR_NOT_CONVERGED = -5, /* iteration caps reached; the best iterate is still written */
+    IIM_ERR_TIMEOUT = -6,       /* a bounded device-side wait ran out */
+    IIM_ERR_CUDA = -7           /* a CUDA runtime call failed (allocation, launch, ...) */
+};
+
+typedef struct { double x0, x1, y0, y1; int nx, ny; } iim_grid;
+
+/* Bounding region R_k of body k: the inclusive box of interior nodes lx..rx, ly..ry (global
+ * node indices).  It must contain every affected point of body k and none of another body,
+ * and its four boundary faces (Eq. sum_dR_def) must pass between plain fluid nodes. */
+typedef struct { int lx, rx, ly, ry; } iim_region;
+
+enum { IIM_BODY_FIXED = 0,       /* psibar_k given (Eq. psibc) */
+       IIM_BODY_CIRCULATION = 1  /* Gamma_k given, psibar_k solved for (Eq. discretecircconstraint) */ };
+
+enum { IIM_FP64 = 0,   /* every step in FP64: the plain iteration */
+       IIM_MIXED = 1   /* FP32 rectangular solves inside FP64 iterative refinement of the
+                          un-reduced residual; FP64 extrapolation weights, residual, Krylov
+                          inner products and circulation rows */ };
+
+typedef struct {
+    int prec;          /* IIM_FP64 or IIM_MIXED */
+    double rtol;       /* target: relative residual ||f - L u||_2 / ||f||_2 of the un-reduced
+                          FP64 system (fluid rows + circulation rows / h^2) */
+    int max_iter;      /* cap on Krylov iterations summed over refinements */
+    int restart;       /* GMRES restart length, 1..64 */
+    int max_refine;    /* cap on outer refinement steps */
+    int guess;         /* 0: start from psi = 0; 1: start from psi_guess */
+    double inner_rtol; /* Krylov tolerance of each correction solve (<= 0: library default,
+                          rtol/20 in FP64 mode, 2e-5 in mixed mode) */
+} iim_opts;
+
+typedef struct {
+    int iters;           /* Krylov iterations, all refinements */
+    int refinements;     /* correction solves performed */
+    int fallback;        /* 1 when a caller guess raised the residual and was dropped */
+    int status;          /* same value as returned */
+    double rel_res;      /* final un-reduced FP64 relative residual */
+    double gmres_rel_res;/* last Krylov relative residual */
+    double circ_err_max; /* max_k |Gamma_k - (-h sum_dRk grad_h psi . n)| over circulation bodies */
+    float ms;            /* wall time of the call on the stream (CUDA events) */
+} iim_stats;
+
+/* Geometry setup (Sec. 2.2, App. A): finds the control points (grid-line crossings of the
+ * zero level set, located by a cubic fit of four level-set samples, Newton and deflation),
+ * the affected points A+ / A-, the fourth-order ghost stencils (Sec. 2.1) and the per-body
+ * labels (from R_k), and allocates the solver's device workspace.
+ *   grid       host; nx, ny powers of two in [16, 2048]
+ *   phi_nodes  node array (device, FP64)
+ *   n_bodies   number of bodies, 0..64; regions, modes: host arrays of that length
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_BAD_REGION, IIM_ERR_UNDERRESOLVED, IIM_ERR_CUDA.
+ * On error *out is NULL and nothing stays allocated.  Synchronizes `stream`. */
+iim_status iim_setup_geometry(const iim_grid* grid, const double* phi_nodes, int n_bodies,
+                              const iim_region* regions, const int* modes, iim_stream stream,
+                              iim_geometry* out);
+
+/* Sizes of the geometry: control points |C|, affected points |A|, bodies.  Host outputs,
+ * any may be NULL. */
+iim_status iim_geometry_info(iim_geometry g, int* n_control, int* n_affected, int* n_bodies);
+
+/* Control points in canonical order (x-edges by (j, i), then y-edges by (j, i)): position,
+ * owning body, edge axis (0 = x, 1 = y), the edge's lower node (i, j) and t = distance from
+ * the fluid node to the crossing in units of h.  Device outputs of length |C|, any NULL. */
+iim_status iim_geometry_control_points(iim_geometry g, double* x, double* y, int* body, int* axis,
+                                       int* edge_i, int* edge_j, double* t, iim_stream stream);
+
+/* Affected points in row-major node order: node (i, j), solid flag (1 = A-), body.
+ * Device outputs of length |A|, any NULL. */
+iim_status iim_geometry_affected_points(iim_geometry g, int* node_i, int* node_j, int* solid,
+                                        int* body, iim_stream stream);
+
+/* IIM Poisson solve (Sec. 4.2 and the full-algorithm step "Velocity Reconstruction",
+ * Sec. 5.5): finds psi with -nabla_h^2 psi_ext = omega at every fluid interior node, psi =
+ * psi_b + psibar_k on body k, box data psi_box, and -h sum_{dR_k} (grad_h psi).n = Gamma_k for
+ * circulation-mode bodies; then u = (d_y psi, -d_x psi) by centered differences of the
+ * fourth-order extension of psi (Sec. 4.2, end).
+ *   omega      interior array; values at solid nodes are ignored
+ *   psi_b      |C| values at the control points (canonical order)
+ *   psi_box    box ring, or NULL for zero box data
+ *   gamma      n_bodies values (entries of fixed-mode bodies ignored), or NULL for zeros
+ *   psibar     n_bodies values: read for fixed bodies, written for circulation bodies
+ *   psi_out    interior array: fluid values, 0 in the solid
+ *   ux_out, uy_out  interior arrays (0 in the solid), or NULL to skip the velocity
+ *   psi_guess  interior array used when opts->guess == 1, else ignored (may be NULL)
+ *   opts       host; NULL = FP64, rtol 1e-10, restart 40, max_iter 2000, max_refine 8
+ *   stats      host, may be NULL
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_NONFINITE, IIM_ERR_NOT_CONVERGED (outputs still hold
+ * the best iterate), IIM_ERR_CUDA.  Synchronizes `stream` (convergence tests read one scalar
+ * per Krylov iteration).  Not re-entrant on one geometry: calls that share an iim_geometry
+ * must be serialized, since they share its workspace. */
+iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* psi_b,
+                             const double* psi_box, const double* gamma, double* psibar,
+                             double* psi_out, double* ux_out, double* uy_out,
+                             const double* psi_guess, const iim_opts* opts, iim_stats* stats,
+                             iim_stream stream);
+
+/* Rectangular Dirichlet-box solve u = -nabla_h^{-2} f (Sec. 4.2: the FFT solution operator,
+ * here a 2D DST-I for the Dirichlet box): -nabla_h^2 u = f on the interior nodes with box data.
+ *   f, u       interior arrays (may alias)
+ *   psi_box    box ring or NULL (zero)
+ *   prec       IIM_FP64 (transforms in FP64) or IIM_MIXED (transforms in FP32)
+ *   work       caller workspace of 2 (nx-1)(ny-1) doubles
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA.  Asynchronous on `stream`. */
+iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box,
+                           double* u, int prec, double* work, iim_stream stream);
+
+/* Text of the last CUDA failure recorded by this thread (empty when none). */
+const char* iim_last_error_message(void);
+
+/* Releases everything the geometry allocated.  NULL is ignored. */
+void iim_destroy_geometry(iim_geometry g);
+
+/* Static, human-readable name of a status code. */
+const char* iim_status_string(iim_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IIM_H */

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libiim.so: the same entry points as include/iim.h, with torch CUDA
+tensors marshalled to device pointers and the current torch stream passed through.  Every
+step of the computation runs in the library's CUDA kernels; there is no CPU fallback, and a
+missing library raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+IIM_OK = 0
+IIM_ERR_INVALID_ARG = -1
+IIM_ERR_UNDERRESOLVED = -2
+IIM_ERR_BAD_REGION = -3
+IIM_ERR_NONFINITE = -4
+IIM_ERR_NOT_CONVERGED = -5
+IIM_ERR_TIMEOUT = -6
+IIM_ERR_CUDA = -7
+IIM_BODY_FIXED, IIM_BODY_CIRCULATION = 0, 1
+IIM_FP64, IIM_MIXED = 0, 1
+
+# (name, restype, argtypes) of every function declared in include/iim.h
+_vp, _i, _d, _ip = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int)
+
+
+class iim_grid(ctypes.Structure):
+    _fields_ = [("x0", _d), ("x1", _d), ("y0", _d), ("y1", _d), ("nx", _i), ("ny", _i)]
+
+
+class iim_region(ctypes.Structure):
+    _fields_ = [("lx", _i), ("rx", _i), ("ly", _i), ("ry", _i)]
+
+
+class iim_opts(ctypes.Structure):
+    _fields_ = [("prec", _i), ("rtol", _d), ("max_iter", _i), ("restart", _i), ("max_refine", _i),
+                ("guess", _i), ("inner_rtol", _d)]
+
+
+class iim_stats(ctypes.Structure):
+    _fields_ = [("iters", _i), ("refinements", _i), ("fallback", _i), ("status", _i), ("rel_res", _d),
+                ("gmres_rel_res", _d), ("circ_err_max", _d), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+SIGNATURES = [
+    ("iim_setup_geometry", _i, [ctypes.POINTER(iim_grid), _vp, _i, ctypes.POINTER(iim_region), _ip, _vp,
+                                ctypes.POINTER(_vp)]),
+    ("iim_geometry_info", _i, [_vp, _ip, _ip, _ip]),
+    ("iim_geometry_control_points", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    ("iim_geometry_affected_points", _i, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("iim_poisson_solve", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
+                               ctypes.POINTER(iim_stats), _vp]),
+    ("iim_box_poisson", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp, _vp]),
+    ("iim_last_error_message", ctypes.c_char_p, []),
+    ("iim_destroy_geometry", None, [_vp]),
+    ("iim_status_string", ctypes.c_char_p, [_i]),
+]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.OUT
+
+
+def load(build_if_missing: bool = True):
+    """Loads libiim.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libiim.so not found at {path}; run paper_2109_13628_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class IIMError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.iim_status_string(status).decode()
+        extra = lib.iim_last_error_message().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({extra})" if extra and status == IIM_ERR_CUDA else ""))
+        self.status = status
+
+
+def _check(st, where):
+    if st != IIM_OK:
+        raise IIMError(st, where)
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_grid(x0, x1, y0, y1, nx, ny):
+    return iim_grid(float(x0), float(x1), float(y0), float(y1), int(nx), int(ny))
+
+
+class Geometry:
+    """Owns an iim_geometry handle (released by iim_destroy_geometry)."""
+
+    def __init__(self, handle, grid, n_bodies, modes):
+        self.handle = handle
+        self.grid = grid
+        self.n_bodies = n_bodies
+        self.modes = list(modes)
+        nc, na, nb = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().iim_geometry_info(handle, nc, na, nb), "iim_geometry_info")
+        self.n_control, self.n_affected = nc.value, na.value
+
+    def close(self):
+        if self.handle:
+            load().iim_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def iim_setup_geometry(grid: iim_grid, phi_nodes: torch.Tensor, regions, modes, stream=None) -> Geometry:
+    lib = load()
+    nb = len(regions)
+    R = (iim_region * max(nb, 1))(*[iim_region(*map(int, r)) for r in regions])
+    M = (ctypes.c_int * max(nb, 1))(*[int(m) for m in modes])
+    out = ctypes.c_void_p()
+    st = lib.iim_setup_geometry(ctypes.byref(grid), _ptr(phi_nodes, torch.float64, (grid.nx + 1) * (grid.ny + 1), "phi"),
+                                nb, R, M, _stream(stream), ctypes.byref(out))
+    _check(st, "iim_setup_geometry")
+    return Geometry(out, grid, nb, modes)
+
+
+def iim_geometry_info(g: Geometry):
+    return g.n_control, g.n_affected, g.n_bodies
+
+
+def iim_geometry_control_points(g: Geometry, stream=None):
+    n = g.n_control
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {k: torch.empty(n, dtype=torch.float64, device=dev) for k in ("x", "y", "t")}
+    out.update({k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("body", "axis", "i", "j")})
+    st = load().iim_geometry_control_points(g.handle, _ptr(out["x"]), _ptr(out["y"]), _ptr(out["body"]), _ptr(out["axis"]),
+                                            _ptr(out["i"]), _ptr(out["j"]), _ptr(out["t"]), _stream(stream))
+    _check(st, "iim_geometry_control_points")
+    return out
+
+
+def iim_geometry_affected_points(g: Geometry, stream=None):
+    n = g.n_affected
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {k: torch.empty(n, dtype=torch.int32, device=dev) for k in ("i", "j", "solid", "body")}
+    st = load().iim_geometry_affected_points(g.handle, _ptr(out["i"]), _ptr(out["j"]), _ptr(out["solid"]),
+                                             _ptr(out["body"]), _stream(stream))
+    _check(st, "iim_geometry_affected_points")
+    return out
+
+
+def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=40, max_refine=8, guess=0, inner_rtol=0.0):
+    return iim_opts(int(prec), float(rtol), int(max_iter), int(restart), int(max_refine), int(guess), float(inner_rtol))
+
+
+def iim_poisson_solve(g: Geometry, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out=None, uy_out=None,
+                      psi_guess=None, opts: iim_opts | None = None, stream=None, check=True):
+    """Returns the iim_stats as a dict; raises IIMError on a non-OK status when `check`."""
+    lib = load()
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    stats = iim_stats()
+    o = opts if opts is not None else default_opts()
+    st = lib.iim_poisson_solve(g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(psi_b, f64, g.n_control, "psi_b"),
+                               _ptr(psi_box, f64, 2 * (g.grid.nx + g.grid.ny), "psi_box"),
+                               _ptr(gamma, f64, g.n_bodies, "gamma"), _ptr(psibar, f64, g.n_bodies, "psibar"),
+                               _ptr(psi_out, f64, NXY, "psi_out"), _ptr(ux_out, f64, NXY, "ux_out"),
+                               _ptr(uy_out, f64, NXY, "uy_out"), _ptr(psi_guess, f64, NXY, "psi_guess"),
+                               ctypes.byref(o), ctypes.byref(stats), _stream(stream))
+    d = stats.as_dict()
+    d["status"] = st
+    if check:
+        _check(st, "iim_poisson_solve")
+    return d
+
+
+def iim_box_poisson(grid: iim_grid, f, psi_box, u, prec, work, stream=None):
+    NXY = (grid.nx - 1) * (grid.ny - 1)
+    st = load().iim_box_poisson(ctypes.byref(grid), _ptr(f, torch.float64, NXY, "f"),
+                                _ptr(psi_box, torch.float64, 2 * (grid.nx + grid.ny), "psi_box"),
+                                _ptr(u, torch.float64, NXY, "u"), int(prec), _ptr(work, torch.float64, None, "work"),
+                                _stream(stream))
+    _check(st, "iim_box_poisson")
+
+
+def iim_status_string(st: int) -> str:
+    return load().iim_status_string(st).decode()
+
+
+def iim_destroy_geometry(g: Geometry):
+    g.close()

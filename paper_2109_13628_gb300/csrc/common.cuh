@@ -1,0 +1,129 @@
+// Shared definitions of the IIM library: complex type, error handling, twiddle tables,
+// geometry and workspace structures.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/iim.h"
+
+namespace iim {
+
+// ------------------------------------------------------------------------- errors
+void record_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define IIM_TRY(call)                                                     \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) {                                          \
+            ::iim::record_cuda_error(e_, #call, __FILE__, __LINE__);      \
+            return IIM_ERR_CUDA;                                          \
+        }                                                                 \
+    } while (0)
+
+#define IIM_LAUNCHED()                                                    \
+    do {                                                                  \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) {                                          \
+            ::iim::record_cuda_error(e_, "kernel launch", __FILE__, __LINE__); \
+            return IIM_ERR_CUDA;                                          \
+        }                                                                 \
+    } while (0)
+
+#define IIM_CHECK(st)                 \
+    do {                              \
+        iim_status s_ = (st);         \
+        if (s_ != IIM_OK) return s_;  \
+    } while (0)
+
+// ------------------------------------------------------------------------- complex
+template <typename T>
+struct cpx {
+    T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cpx<T> cmul(cpx<T> a, cpx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+
+// ------------------------------------------------------------------------- twiddles
+// exp(-i pi k / 4096), k = 0..4095, in both precisions.  The DST of length n - 1 (n a power
+// of two <= 4096) uses entry k * (4096 / n).  Filled once per device from host cos/sin.
+constexpr int kTwLog = 12;
+constexpr int kTwN = 1 << kTwLog;
+iim_status ensure_twiddles();                 // for the current device
+const cpx<double>* twiddles64();              // device address, current device
+const cpx<float>* twiddles32();
+
+// ------------------------------------------------------------------------- node classes
+enum : uint8_t { CLS_FLUID = 0, CLS_PLUS = 1, CLS_MINUS = 2, CLS_SOLID = 3 };
+
+inline int ilog2(int n) {
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+inline bool is_pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+template <typename T>
+struct DevBuf {
+    T* p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace iim
+
+// Geometry handle: everything iim_setup_geometry builds, plus the solver workspace.
+struct iim_geometry_s {
+    int device = 0;
+    iim_grid grid{};
+    int nx = 0, ny = 0, NX = 0, NY = 0;  // cells and interior sizes
+    double h = 0.0;
+    int nb = 0, ncirc = 0;
+    std::vector<iim_region> regions;
+    std::vector<int> modes;
+    std::vector<int> circ_ids;  // body index of each circulation-mode body
+    int ncp = 0, na = 0, nminus = 0;
+    int ja0 = 0, ja1 = -1;      // interior rows holding affected points (inclusive)
+    int jo0 = 0, jo1 = -1;      // interior rows the gather stencils read (inclusive)
+
+    // control points (canonical order)
+    double *cp_x = nullptr, *cp_y = nullptr, *cp_t = nullptr;
+    int *cp_body = nullptr, *cp_axis = nullptr, *cp_ei = nullptr, *cp_ej = nullptr;
+    // affected points (row-major order)
+    int *aff_node = nullptr, *aff_body = nullptr, *aff_row_ptr = nullptr;
+    uint8_t* aff_solid = nullptr;
+    // gamma = A psi + B bc as CSR over affected points; idx >= 0: interior node, idx < 0:
+    // control point (-idx - 1)
+    int *gop_ptr = nullptr, *gop_idx = nullptr;
+    double* gop_w = nullptr;
+    // fourth-order ghost values at A- nodes (velocity, residual)
+    int *minus_node = nullptr, *gh_ptr = nullptr, *gh_idx = nullptr;
+    double* gh_w = nullptr;
+    uint8_t* node_class = nullptr;       // NY*NX
+    int* body_circ = nullptr;            // per body: index among circulation bodies or -1
+    iim_region* d_regions = nullptr;
+    // eigenvalues of the 1D three-point operators, x modes (NX) and y modes (NY)
+    double *lam_x64 = nullptr, *lam_y64 = nullptr;
+    float *lam_x32 = nullptr, *lam_y32 = nullptr;
+
+    // ---- solver workspace
+    double* psi_ext = nullptr;   // NY*NX FP64: fluid values, ghosts at A-, 0 elsewhere
+    double* res = nullptr;       // NY*NX FP64 residual (correction right-hand side)
+    void* tbuf = nullptr;        // NY*NX of T: transform buffer
+    void* psiT = nullptr;        // NY*NX of T: rectangular-solve output for gathers
+    double* partial = nullptr;   // reduction partials
+    double* small = nullptr;     // small per-solve vectors (see solve.cu)
+    int krylov_m = 0;            // restart length the Krylov buffers were sized for
+    double* V = nullptr;         // (m+1) * ns Krylov basis
+    double* H = nullptr;         // small Hessenberg / Givens storage
+    double* xsol = nullptr;      // ns
+    double* bvec = nullptr;      // ns
+    int* d_int = nullptr;        // device counters / flags
+    double* h_pinned = nullptr;  // pinned host scalars
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};

@@ -1,0 +1,840 @@
+// IIM Poisson solve (Sec. 4.2) on the device.
+//
+// Outer loop: FP64 iterative refinement of the un-reduced system.  The residual r of the
+// un-reduced equations (five-point Laplacian of the extended psi at fluid nodes, box data,
+// ghosts from psi_b + psibar_k; circulation rows / h^2) is evaluated in FP64; a correction
+// with homogeneous data solves L delta = r in Schur form:
+//   (I + A P E_a) dgamma - B sum_k dpsibar_k 1_k = A P r
+//   sum_{B_k} dgamma = sum_{R_k} r - rc_k            (rc_k: circulation row residual)
+//   delta = P (r - E_a dgamma)
+// where P = -nabla_h^-2 is the Dirichlet-box DST solve.  This is Eq. schur / psirecovery and
+// the augmented system of Sec. 4.2 with the sign derived from Eqs. discretepoisson and
+// poissoncorrections (P = -nabla_h^-2 turns the printed "+ A nabla^-2 E_a" into "+ A P E_a").
+// The Krylov solver is restarted GMRES with classical Gram-Schmidt applied twice; all Krylov
+// vectors and inner products are FP64.  In FP64 mode the rectangular solves use FP64
+// transforms; in mixed mode FP32 transforms (the refinement keeps the FP64 residual exact).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "dst.cuh"
+
+namespace iim {
+
+// ------------------------------------------------------------------------- errors, tables
+static thread_local char g_last_error[512];
+
+void record_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+}
+
+__device__ cpx<double> g_tw64[kTwN];
+__device__ cpx<float> g_tw32[kTwN];
+
+static std::mutex g_tw_mutex;
+static bool g_tw_ready[64];
+static const cpx<double>* g_tw64_addr[64];
+static const cpx<float>* g_tw32_addr[64];
+
+iim_status ensure_twiddles() {
+    int dev = 0;
+    IIM_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return IIM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tw_mutex);
+    if (g_tw_ready[dev]) return IIM_OK;
+    std::vector<cpx<double>> t64(kTwN);
+    std::vector<cpx<float>> t32(kTwN);
+    for (int k = 0; k < kTwN; ++k) {
+        const double a = M_PI * (double)k / (double)kTwN;
+        t64[k] = {std::cos(a), -std::sin(a)};
+        t32[k] = {(float)t64[k].x, (float)t64[k].y};
+    }
+    IIM_TRY(cudaMemcpyToSymbol(g_tw64, t64.data(), sizeof(cpx<double>) * kTwN));
+    IIM_TRY(cudaMemcpyToSymbol(g_tw32, t32.data(), sizeof(cpx<float>) * kTwN));
+    void* p64 = nullptr;
+    void* p32 = nullptr;
+    IIM_TRY(cudaGetSymbolAddress(&p64, g_tw64));
+    IIM_TRY(cudaGetSymbolAddress(&p32, g_tw32));
+    g_tw64_addr[dev] = (const cpx<double>*)p64;
+    g_tw32_addr[dev] = (const cpx<float>*)p32;
+    g_tw_ready[dev] = true;
+    return IIM_OK;
+}
+
+const cpx<double>* twiddles64() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_tw64_addr[dev];
+}
+const cpx<float>* twiddles32() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_tw32_addr[dev];
+}
+
+// ------------------------------------------------------------------------- transform plan
+template <typename T>
+struct Plan {
+    int NX, NY, nx, ny, lognx, logny;
+    const T* lam_x;
+    const T* lam_y;
+    const cpx<T>* tw;
+    T norm;
+};
+
+template <typename T>
+constexpr int cols_per_block() { return sizeof(T) == 8 ? 4 : 8; }
+constexpr int kRowWarps = 4;
+
+template <typename T>
+static size_t rows_smem(int n) { return (size_t)n * sizeof(cpx<T>) + (size_t)kRowWarps * 2 * n * sizeof(T); }
+template <typename T>
+static size_t cols_smem(int n) {
+    const int pad = sizeof(T) == 4 ? 4 : 2;
+    return (size_t)n * sizeof(cpx<T>) + (size_t)cols_per_block<T>() * (2 * n + pad) * sizeof(T);
+}
+
+// Raises a kernel's dynamic shared memory limit once per (device, kernel, size).
+static std::mutex g_attr_mutex;
+static std::vector<std::pair<std::pair<int, const void*>, size_t>> g_attr_done;
+
+template <typename KernelT>
+static void allow_smem(KernelT k, size_t bytes) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const void* key = (const void*)k;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    for (auto& e : g_attr_done)
+        if (e.first.first == dev && e.first.second == key && e.second >= bytes) return;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    g_attr_done.push_back({{dev, key}, bytes});
+}
+
+template <typename T>
+static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* dense, const double* ring, double ih2,
+                           const int* row_ptr, const int* aff_node, const double* gam, double gsign, T* out,
+                           cudaStream_t s) {
+    if (nrows <= 0) return IIM_OK;
+    const size_t sm = rows_smem<T>(p.nx);
+    allow_smem(k_rows_fwd<T, kRowWarps>, sm);
+    k_rows_fwd<T, kRowWarps><<<(nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s>>>(
+        p.NX, p.NY, p.nx, p.lognx, row0, nrows, dense, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+template <typename T>
+static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, cudaStream_t s) {
+    constexpr int C = cols_per_block<T>();
+    const size_t sm = cols_smem<T>(p.ny);
+    allow_smem(k_cols<T, C>, sm);
+    k_cols<T, C><<<(p.NX + C - 1) / C, C * 32, sm, s>>>(p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x,
+                                                      p.lam_y, p.norm, p.tw);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+template <typename T, int MODE>
+static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T* outT, double* out64,
+                           const uint8_t* cls, cudaStream_t s) {
+    if (nrows <= 0) return IIM_OK;
+    const size_t sm = rows_smem<T>(p.nx);
+    allow_smem(k_rows_inv<T, kRowWarps, MODE>, sm);
+    k_rows_inv<T, kRowWarps, MODE><<<(nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s>>>(
+        p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, cls, p.tw);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+template <typename T>
+static Plan<T> make_plan(iim_geometry g);
+template <>
+Plan<double> make_plan<double>(iim_geometry g) {
+    return Plan<double>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x64, g->lam_y64,
+                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny)};
+}
+template <>
+Plan<float> make_plan<float>(iim_geometry g) {
+    return Plan<float>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
+                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny))};
+}
+
+// ------------------------------------------------------------------------- reductions
+template <int BLOCK>
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[BLOCK / 32];
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = (l < BLOCK / 32) ? red[l] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) r += __shfl_down_sync(0xffffffffu, r, off);
+    }
+    return r;   // valid in thread 0
+}
+
+// ------------------------------------------------------------------------- IIM operators
+// out[a] = (v ? v[a] : 0) + sum_e w_e * (idx >= 0 ? psi[idx] : bc(control point))
+// with bc = -xc[body_circ[body]] for circulation bodies (the -B sum psibar 1_k column) when
+// xc is given, else 0.
+template <typename T>
+__global__ void k_gather(int na, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ w,
+                         const T* __restrict__ psi, const int* __restrict__ cp_body, const int* __restrict__ body_circ,
+                         const double* __restrict__ xc, const double* __restrict__ v, double* __restrict__ out) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= na) return;
+    double acc = 0.0;
+    for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+        const int q = idx[e];
+        if (q >= 0) {
+            acc += w[e] * (double)psi[q];
+        } else if (xc) {
+            const int bc = body_circ[cp_body[-q - 1]];
+            if (bc >= 0) acc -= w[e] * xc[bc];
+        }
+    }
+    out[a] = (v ? v[a] : 0.0) + acc;
+}
+
+// out[c] = sum over affected points of circulation body c of v
+template <int BLOCK>
+__global__ void k_circ_rows(int na, const int* __restrict__ aff_body, const int* __restrict__ body_circ,
+                            const double* __restrict__ v, double* __restrict__ out) {
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int a = threadIdx.x; a < na; a += BLOCK)
+        if (body_circ[aff_body[a]] == c) acc += v[a];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) out[c] = acc;
+}
+
+// Ghost values at A- nodes from fluid values and psi_b + psibar (Sec. 2.1, 2.2).
+__global__ void k_ghost(int nm, const int* __restrict__ minus_node, const int* __restrict__ ptr, const int* __restrict__ idx,
+                        const double* __restrict__ w, const double* __restrict__ psi_b, const double* __restrict__ psibar,
+                        const int* __restrict__ cp_body, double* __restrict__ psi) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= nm) return;
+    double acc = 0.0;
+    for (int e = ptr[m]; e < ptr[m + 1]; ++e) {
+        const int q = idx[e];
+        if (q >= 0) acc += w[e] * psi[q];
+        else {
+            const int c = -q - 1;
+            acc += w[e] * ((psi_b ? psi_b[c] : 0.0) + psibar[cp_body[c]]);
+        }
+    }
+    psi[minus_node[m]] = acc;
+}
+
+// Un-reduced FP64 residual at interior nodes: r = omega + nabla_h^2 psi_ext at fluid nodes,
+// 0 in the solid; per-block partial sums of r^2.
+template <int BLOCK>
+__global__ void k_residual(int NX, int NY, double ih2, const double* __restrict__ psi, const double* __restrict__ omega,
+                           const uint8_t* __restrict__ cls, const double* __restrict__ ring, double* __restrict__ res,
+                           double* __restrict__ partial) {
+    const long n = (long)NX * NY;
+    double acc = 0.0;
+    for (long k = (long)blockIdx.x * BLOCK + threadIdx.x; k < n; k += (long)gridDim.x * BLOCK) {
+        const int i = (int)(k % NX), j = (int)(k / NX);
+        double r = 0.0;
+        if (cls[k] <= CLS_PLUS) {
+            const double c = psi[k];
+            const double wv = i > 0 ? psi[k - 1] : (ring ? ring[2 * (NX + 2) + j] : 0.0);
+            const double ev = i < NX - 1 ? psi[k + 1] : (ring ? ring[2 * (NX + 2) + NY + j] : 0.0);
+            const double sv = j > 0 ? psi[k - NX] : (ring ? ring[i + 1] : 0.0);
+            const double nv = j < NY - 1 ? psi[k + NX] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
+            r = omega[k] - (4.0 * c - wv - ev - sv - nv) * ih2;
+            acc += r * r;
+        }
+        res[k] = r;
+    }
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Sum of an interior field over region R_k of each circulation body; grid (ncirc, S).
+template <int BLOCK>
+__global__ void k_region_sums(int NX, const double* __restrict__ f, const iim_region* __restrict__ R,
+                              const int* __restrict__ circ_ids, double* __restrict__ partial) {
+    const int c = blockIdx.x, part = blockIdx.y, S = gridDim.y;
+    const iim_region r = R[circ_ids[c]];
+    const int w = r.rx - r.lx + 1, hgt = r.ry - r.ly + 1;
+    const long n = (long)w * hgt;
+    double acc = 0.0;
+    for (long t = (long)part * BLOCK + threadIdx.x; t < n; t += (long)S * BLOCK) {
+        const int i = r.lx + (int)(t % w), j = r.ly + (int)(t / w);
+        acc += f[(long)(j - 1) * NX + (i - 1)];
+    }
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) partial[c * S + part] = acc;
+}
+
+// Discrete circulation -h sum_{dR}(grad_h psi).n (Eq. discretecircconstraint) of each circulation
+// body, from the fluid values of psi on the faces of R_k.
+template <int BLOCK>
+__global__ void k_circ_measure(int NX, const double* __restrict__ psi, const iim_region* __restrict__ R,
+                               const int* __restrict__ circ_ids, double* __restrict__ out) {
+    const int c = blockIdx.x;
+    const iim_region r = R[circ_ids[c]];
+    auto P = [&](int i, int j) { return psi[(long)(j - 1) * NX + (i - 1)]; };
+    double acc = 0.0;
+    for (int j = r.ly + threadIdx.x; j <= r.ry; j += BLOCK)
+        acc += (P(r.rx + 1, j) - P(r.rx, j)) - (P(r.lx, j) - P(r.lx - 1, j));
+    for (int i = r.lx + threadIdx.x; i <= r.rx; i += BLOCK)
+        acc += (P(i, r.ry + 1) - P(i, r.ry)) - (P(i, r.ly) - P(i, r.ly - 1));
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) out[c] = -acc;
+}
+
+// small[] layout
+enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_BNORM2 = 2, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048 };
+constexpr int kRegionParts = 16;
+
+// Combines the partial sums: res2 = sum r^2 + sum rc^2, bcirc[c] = sum_{R_k} r - rc_c,
+// rc_c = (Gamma_k - circ_k) / h^2.
+__global__ void k_finish_residual(int nparts, const double* __restrict__ partial, int ncirc,
+                                  const int* __restrict__ circ_ids, const double* __restrict__ gamma, double ih2,
+                                  double* __restrict__ small, const double* __restrict__ regpart, double* __restrict__ bcirc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[b];
+    double cerr = 0.0;
+    for (int c = 0; c < ncirc; ++c) {
+        const double gk = gamma ? gamma[circ_ids[c]] : 0.0;
+        const double diff = gk - small[SM_CIRC + c];
+        cerr = fmax(cerr, fabs(diff));
+        const double rc = diff * ih2;
+        small[SM_RC + c] = rc;
+        s += rc * rc;
+        double reg = 0.0;
+        for (int p = 0; p < kRegionParts; ++p) reg += regpart[c * kRegionParts + p];
+        if (bcirc) bcirc[c] = reg - rc;
+    }
+    small[SM_RES2] = s;
+    small[SM_CIRC_ERR] = cerr;
+}
+
+__global__ void k_init_psi(long n, const double* __restrict__ guess, const uint8_t* __restrict__ cls, double* __restrict__ psi) {
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    psi[k] = (guess && cls[k] <= CLS_PLUS) ? guess[k] : 0.0;
+}
+
+__global__ void k_init_psibar(int nb, const int* __restrict__ body_circ, const double* __restrict__ in, int keep_circ,
+                              double* __restrict__ out) {
+    const int k = threadIdx.x;
+    if (k >= nb) return;
+    const double v = in ? in[k] : 0.0;
+    out[k] = (body_circ[k] >= 0 && !keep_circ) ? 0.0 : v;
+}
+
+__global__ void k_add_psibar(int ncirc, const int* __restrict__ circ_ids, const double* __restrict__ x, double* __restrict__ psibar) {
+    const int c = threadIdx.x;
+    if (c < ncirc) psibar[circ_ids[c]] += x[c];
+}
+
+// Velocity u = (d_y psi, -d_x psi) by centered differences of psi_ext at fluid nodes (Sec. 4.2,
+// end); psi_out = psi at fluid nodes, 0 in the solid.
+__global__ void k_velocity(int NX, int NY, double inv2h, const double* __restrict__ psi, const uint8_t* __restrict__ cls,
+                           const double* __restrict__ ring, double* __restrict__ psi_out, double* __restrict__ ux,
+                           double* __restrict__ uy) {
+    const long n = (long)NX * NY;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)(k % NX), j = (int)(k / NX);
+    const bool fl = cls[k] <= CLS_PLUS;
+    if (psi_out) psi_out[k] = fl ? psi[k] : 0.0;
+    if (!ux && !uy) return;
+    double vx = 0.0, vy = 0.0;
+    if (fl) {
+        const double wv = i > 0 ? psi[k - 1] : (ring ? ring[2 * (NX + 2) + j] : 0.0);
+        const double ev = i < NX - 1 ? psi[k + 1] : (ring ? ring[2 * (NX + 2) + NY + j] : 0.0);
+        const double sv = j > 0 ? psi[k - NX] : (ring ? ring[i + 1] : 0.0);
+        const double nv = j < NY - 1 ? psi[k + NX] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
+        vx = (nv - sv) * inv2h;
+        vy = -(ev - wv) * inv2h;
+    }
+    if (ux) ux[k] = vx;
+    if (uy) uy[k] = vy;
+}
+
+// ------------------------------------------------------------------------- GMRES kernels
+template <int BLOCK>
+__global__ void k_dots(int j, const double* __restrict__ V, long ld, const double* __restrict__ w, int ns,
+                       double* __restrict__ out) {
+    const int i = blockIdx.x;
+    if (i > j) return;
+    const double* vi = V + (long)i * ld;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) acc += vi[e] * w[e];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) out[i] = acc;
+}
+
+__global__ void k_update(int j, const double* __restrict__ V, long ld, const double* __restrict__ coef, int ns,
+                         double* __restrict__ w) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ns) return;
+    double s = 0.0;
+    for (int i = 0; i <= j; ++i) s += coef[i] * V[(long)i * ld + e];
+    w[e] -= s;
+}
+
+template <int BLOCK>
+__global__ void k_sumsq(const double* __restrict__ w, int ns, double* __restrict__ partial) {
+    double acc = 0.0;
+    for (int e = blockIdx.x * BLOCK + threadIdx.x; e < ns; e += gridDim.x * BLOCK) acc += w[e] * w[e];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Krylov small-storage layout inside g->H (m <= 64):
+//   H (m+1) x m column-major | cs[m] | sn[m] | gv[m+1] | hc1[m+1] | hc2[m+1] | y[m] | scal[8]
+struct KLayout {
+    int m;
+    __host__ __device__ long H() const { return 0; }
+    __host__ __device__ long cs() const { return (long)(m + 1) * m; }
+    __host__ __device__ long sn() const { return cs() + m; }
+    __host__ __device__ long gv() const { return sn() + m; }
+    __host__ __device__ long hc1() const { return gv() + m + 1; }
+    __host__ __device__ long hc2() const { return hc1() + m + 1; }
+    __host__ __device__ long y() const { return hc2() + m + 1; }
+    __host__ __device__ long scal() const { return y() + m; }
+    __host__ __device__ long total() const { return scal() + 8; }
+};
+enum { SC_INV = 0, SC_RESID = 1, SC_BETA = 2 };
+
+// Arnoldi step j finish: norm, Hessenberg column, Givens rotations, residual estimate.
+__global__ void k_arnoldi_tail(int j, KLayout L, int nparts, const double* __restrict__ partial, double* __restrict__ K) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[b];
+    const double nrm = sqrt(s);
+    double* H = K + L.H();
+    const int ldh = L.m + 1;
+    double* col = H + (long)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] = K[L.hc1() + i] + K[L.hc2() + i];
+    col[j + 1] = nrm;
+    double* cs = K + L.cs();
+    double* sn = K + L.sn();
+    double* gv = K + L.gv();
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double d = hypot(col[j], col[j + 1]);
+    const double c = d > 0.0 ? col[j] / d : 1.0, sgn = d > 0.0 ? col[j + 1] / d : 0.0;
+    cs[j] = c;
+    sn[j] = sgn;
+    col[j] = d;
+    col[j + 1] = 0.0;
+    gv[j + 1] = -sgn * gv[j];
+    gv[j] = c * gv[j];
+    K[L.scal() + SC_INV] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    K[L.scal() + SC_RESID] = fabs(gv[j + 1]);
+}
+
+__global__ void k_scale(double* __restrict__ w, int ns, const double* __restrict__ sc) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < ns) w[e] *= *sc;
+}
+
+__global__ void k_start_cycle(int ns, const double* __restrict__ r, double* __restrict__ v0, KLayout L, double* __restrict__ K,
+                              int nparts, const double* __restrict__ partial) {
+    // every block recomputes beta from the partials (cheap, keeps this a single launch)
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += partial[b];
+    const double beta = sqrt(s);
+    const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < ns) v0[e] = r[e] * inv;
+    if (e == 0) {
+        double* gv = K + L.gv();
+        gv[0] = beta;
+        for (int i = 1; i <= L.m; ++i) gv[i] = 0.0;
+        K[L.scal() + SC_BETA] = beta;
+    }
+}
+
+__global__ void k_backsolve(int k, KLayout L, double* __restrict__ K) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double* H = K + L.H();
+    const int ldh = L.m + 1;
+    const double* gv = K + L.gv();
+    double* y = K + L.y();
+    for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int l = i + 1; l < k; ++l) s -= H[(long)l * ldh + i] * y[l];
+        const double d = H[(long)i * ldh + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+__global__ void k_xupdate(int k, const double* __restrict__ V, long ld, const double* __restrict__ y, int ns,
+                          double* __restrict__ x) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ns) return;
+    double s = 0.0;
+    for (int i = 0; i < k; ++i) s += y[i] * V[(long)i * ld + e];
+    x[e] += s;
+}
+
+__global__ void k_axpby(int n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = a * x[e] + b * y[e];
+}
+
+// ------------------------------------------------------------------------- solver
+struct Solver {
+    iim_geometry g;
+    cudaStream_t s;
+    int prec;
+    const double* omega;
+    const double* psi_b;
+    const double* ring;
+    const double* gamma;
+    double* psibar;   // device, n_bodies
+    int ns;
+    int m;
+    KLayout L;
+    double fnorm2 = 0.0;
+    int iters = 0;
+    double last_gmres_rel = 0.0;
+    static constexpr int kResBlocks = 1024;
+    static constexpr int kNormBlocks = 64;
+
+    // ---- residual of the un-reduced system; fills g->res, small[], bvec circulation rows
+    iim_status residual(double* res2_out, double* circ_err_out) {
+        const long n = (long)g->NX * g->NY;
+        const double ih2 = 1.0 / (g->h * g->h);
+        if (g->nminus > 0) {
+            k_ghost<<<(g->nminus + 255) / 256, 256, 0, s>>>(g->nminus, g->minus_node, g->gh_ptr, g->gh_idx, g->gh_w, psi_b,
+                                                             psibar, g->cp_body, g->psi_ext);
+            IIM_LAUNCHED();
+        }
+        k_residual<256><<<kResBlocks, 256, 0, s>>>(g->NX, g->NY, ih2, g->psi_ext, omega, g->node_class, ring, g->res,
+                                                   g->partial);
+        IIM_LAUNCHED();
+        double* small = g->small;
+        int* circ_ids_d = g->d_int + 32;   // circulation body ids (filled at solve start)
+        if (g->ncirc > 0) {
+            k_circ_measure<256><<<g->ncirc, 256, 0, s>>>(g->NX, g->psi_ext, g->d_regions, circ_ids_d, small + SM_CIRC);
+            k_region_sums<256><<<dim3(g->ncirc, kRegionParts), 256, 0, s>>>(g->NX, g->res, g->d_regions, circ_ids_d,
+                                                                            small + SM_REG);
+            IIM_LAUNCHED();
+        }
+        k_finish_residual<<<1, 32, 0, s>>>(kResBlocks, g->partial, g->ncirc, circ_ids_d, gamma, ih2, small,
+                                           small + SM_REG, g->bvec ? g->bvec + g->na : nullptr);
+        IIM_LAUNCHED();
+        IIM_TRY(cudaMemcpyAsync(g->h_pinned, small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        (void)n;
+        *res2_out = g->h_pinned[SM_RES2];
+        *circ_err_out = g->h_pinned[SM_CIRC_ERR];
+        return IIM_OK;
+    }
+
+    // ---- Schur operator application vout = S_aug vin (precision T for the box solves)
+    template <typename T>
+    iim_status apply(const double* vin, double* vout) {
+        Plan<T> p = make_plan<T>(g);
+        T* tb = (T*)g->tbuf;
+        T* pt = (T*)g->psiT;
+        if (g->na > 0) {
+            IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, nullptr, 0.0, g->aff_row_ptr, g->aff_node, vin,
+                                  1.0, tb, s));
+            IIM_CHECK(cols<T>(p, g->ja0, g->ja1, g->jo0, g->jo1, tb, s));
+            IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, nullptr, s)));
+            k_gather<T><<<(g->na + 127) / 128, 128, 0, s>>>(g->na, g->gop_ptr, g->gop_idx, g->gop_w, pt, g->cp_body,
+                                                             g->body_circ, vin + g->na, vin, vout);
+            IIM_LAUNCHED();
+        }
+        if (g->ncirc > 0) {
+            k_circ_rows<256><<<g->ncirc, 256, 0, s>>>(g->na, g->aff_body, g->body_circ, vin, vout + g->na);
+            IIM_LAUNCHED();
+        }
+        return IIM_OK;
+    }
+
+    // ---- right-hand side b = [A P r ; sum_R r - rc] (circulation part filled by residual())
+    template <typename T>
+    iim_status rhs() {
+        Plan<T> p = make_plan<T>(g);
+        T* tb = (T*)g->tbuf;
+        T* pt = (T*)g->psiT;
+        if (g->na == 0) return IIM_OK;
+        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, nullptr, 0.0, nullptr, nullptr, nullptr, 0.0, tb, s));
+        IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->jo0, g->jo1, tb, s));
+        IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, nullptr, s)));
+        k_gather<T><<<(g->na + 127) / 128, 128, 0, s>>>(g->na, g->gop_ptr, g->gop_idx, g->gop_w, pt, g->cp_body,
+                                                         g->body_circ, nullptr, nullptr, g->bvec);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
+
+    // ---- psi_ext += P (r - E_a dgamma) at fluid nodes; psibar += dpsibar
+    template <typename T>
+    iim_status recover(const double* x) {
+        Plan<T> p = make_plan<T>(g);
+        T* tb = (T*)g->tbuf;
+        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, nullptr, 0.0, g->aff_row_ptr, g->aff_node, g->na ? x : nullptr, -1.0,
+                              tb, s));
+        IIM_CHECK(cols<T>(p, 0, g->NY - 1, 0, g->NY - 1, tb, s));
+        IIM_CHECK((rows_inv<T, INV_ACCUM_FLUID>(p, 0, g->NY, tb, nullptr, g->psi_ext, g->node_class, s)));
+        if (g->ncirc > 0) {
+            k_add_psibar<<<1, 64, 0, s>>>(g->ncirc, g->d_int + 32, x + g->na, psibar);
+            IIM_LAUNCHED();
+        }
+        return IIM_OK;
+    }
+
+    iim_status norm2(const double* v, int n, double* out) {
+        k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(v, n, g->partial);
+        IIM_LAUNCHED();
+        k_finish_residual<<<1, 32, 0, s>>>(kNormBlocks, g->partial, 0, nullptr, nullptr, 0.0, g->small + SM_NORM, nullptr,
+                                           nullptr);
+        IIM_LAUNCHED();
+        IIM_TRY(cudaMemcpyAsync(g->h_pinned + 8, g->small + SM_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        *out = g->h_pinned[8];
+        return IIM_OK;
+    }
+
+    // ---- restarted GMRES on S_aug x = b, x0 = 0; returns relative residual estimate
+    template <typename T>
+    iim_status gmres(double tol, int max_it, double* rel_out) {
+        const int ns_ = ns;
+        double* V = g->V;
+        double* K = g->H;
+        double* x = g->xsol;
+        const long ld = ns_;
+        const int eb = (ns_ + 255) / 256;
+        IIM_TRY(cudaMemsetAsync(x, 0, ns_ * sizeof(double), s));
+        double b2 = 0.0;
+        IIM_CHECK(norm2(g->bvec, ns_, &b2));
+        if (!std::isfinite(b2)) return IIM_ERR_NONFINITE;
+        const double bnorm = std::sqrt(b2);
+        *rel_out = 0.0;
+        if (bnorm == 0.0) return IIM_OK;
+        // r0 = b (x0 = 0)
+        k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(g->bvec, ns_, g->partial);
+        k_start_cycle<<<eb, 256, 0, s>>>(ns_, g->bvec, V, L, K, kNormBlocks, g->partial);
+        IIM_LAUNCHED();
+        int it_local = 0;
+        double resid = bnorm;
+        while (true) {
+            int k = 0;
+            for (int j = 0; j < m; ++j) {
+                double* vj = V + (long)j * ld;
+                double* w = V + (long)(j + 1) * ld;
+                IIM_CHECK(apply<T>(vj, w));
+                k_dots<256><<<j + 1, 256, 0, s>>>(j, V, ld, w, ns_, K + L.hc1());
+                k_update<<<eb, 256, 0, s>>>(j, V, ld, K + L.hc1(), ns_, w);
+                k_dots<256><<<j + 1, 256, 0, s>>>(j, V, ld, w, ns_, K + L.hc2());
+                k_update<<<eb, 256, 0, s>>>(j, V, ld, K + L.hc2(), ns_, w);
+                k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(w, ns_, g->partial);
+                k_arnoldi_tail<<<1, 32, 0, s>>>(j, L, kNormBlocks, g->partial, K);
+                k_scale<<<eb, 256, 0, s>>>(w, ns_, K + L.scal() + SC_INV);
+                IIM_LAUNCHED();
+                IIM_TRY(cudaMemcpyAsync(g->h_pinned + 9, K + L.scal() + SC_RESID, sizeof(double), cudaMemcpyDeviceToHost, s));
+                IIM_TRY(cudaStreamSynchronize(s));
+                resid = g->h_pinned[9];
+                ++it_local;
+                ++iters;
+                k = j + 1;
+                if (!std::isfinite(resid)) return IIM_ERR_NONFINITE;
+                if (resid <= tol * bnorm || it_local >= max_it) break;
+            }
+            k_backsolve<<<1, 32, 0, s>>>(k, L, K);
+            k_xupdate<<<eb, 256, 0, s>>>(k, V, ld, K + L.y(), ns_, x);
+            IIM_LAUNCHED();
+            if (resid <= tol * bnorm || it_local >= max_it) break;
+            // restart: r = b - S x into V_0
+            double* tmp = V + ld;
+            IIM_CHECK(apply<T>(x, tmp));
+            k_axpby<<<eb, 256, 0, s>>>(ns_, 1.0, g->bvec, -1.0, tmp, tmp);
+            k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(tmp, ns_, g->partial);
+            k_start_cycle<<<eb, 256, 0, s>>>(ns_, tmp, V, L, K, kNormBlocks, g->partial);
+            IIM_LAUNCHED();
+        }
+        *rel_out = resid / bnorm;
+        last_gmres_rel = *rel_out;
+        return IIM_OK;
+    }
+
+    template <typename T>
+    iim_status correction(double tol, int max_it) {
+        double rel = 0.0;
+        IIM_CHECK(rhs<T>());
+        IIM_CHECK(gmres<T>(tol, max_it, &rel));
+        IIM_CHECK(recover<T>(g->xsol));
+        return IIM_OK;
+    }
+};
+
+static iim_status ensure_krylov(iim_geometry g, int m) {
+    const int ns = g->na + g->ncirc;
+    if (g->V && g->krylov_m >= m) return IIM_OK;
+    cudaFree(g->V); cudaFree(g->H); cudaFree(g->xsol); cudaFree(g->bvec);
+    g->V = g->H = g->xsol = g->bvec = nullptr;
+    KLayout L{m};
+    IIM_TRY(cudaMalloc(&g->V, sizeof(double) * (size_t)(m + 1) * std::max(ns, 1)));
+    IIM_TRY(cudaMalloc(&g->H, sizeof(double) * (size_t)L.total()));
+    IIM_TRY(cudaMalloc(&g->xsol, sizeof(double) * (size_t)std::max(ns, 1)));
+    IIM_TRY(cudaMalloc(&g->bvec, sizeof(double) * (size_t)std::max(ns, 1)));
+    g->krylov_m = m;
+    return IIM_OK;
+}
+
+}  // namespace iim
+
+using namespace iim;
+
+extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
+                                        const double* gamma, double* psibar, double* psi_out, double* ux_out,
+                                        double* uy_out, const double* psi_guess, const iim_opts* opts_in,
+                                        iim_stats* stats, iim_stream stream) {
+    iim_opts opts{IIM_FP64, 1e-10, 2000, 40, 8, 0, 0.0};
+    if (opts_in) opts = *opts_in;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!g || !omega || !psi_out || (g->ncp > 0 && !psi_b) || (g->nb > 0 && !psibar)) return IIM_ERR_INVALID_ARG;
+    if (opts.prec != IIM_FP64 && opts.prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
+    if (opts.restart < 1 || opts.restart > 64 || !(opts.rtol > 0.0) || opts.max_iter < 1 || opts.max_refine < 1)
+        return IIM_ERR_INVALID_ARG;
+    if (opts.guess == 1 && !psi_guess) return IIM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    IIM_CHECK(ensure_twiddles());
+    IIM_CHECK(ensure_krylov(g, opts.restart));
+    if (g->ncirc > 0)
+        IIM_TRY(cudaMemcpyAsync(g->d_int + 32, g->circ_ids.data(), g->ncirc * sizeof(int), cudaMemcpyHostToDevice, s));
+    IIM_TRY(cudaEventRecord(g->ev0, s));
+
+    Solver S;
+    S.g = g; S.s = s; S.prec = opts.prec; S.omega = omega; S.psi_b = psi_b; S.ring = psi_box; S.gamma = gamma;
+    S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
+    const long n = (long)g->NX * g->NY;
+    const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 2e-5);
+
+    // ||f||: residual at psi = 0 (ghosts from the boundary data only)
+    double res2 = 0.0, cerr = 0.0;
+    int fallback = 0;
+    k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, g->node_class, g->psi_ext);
+    if (g->nb > 0) {
+        // fixed bodies keep their psibar, circulation bodies start from 0
+        k_init_psibar<<<1, 64, 0, s>>>(g->nb, g->body_circ, psibar, 0, psibar);
+    }
+    IIM_LAUNCHED();
+    IIM_CHECK(S.residual(&res2, &cerr));
+    if (!std::isfinite(res2)) return IIM_ERR_NONFINITE;
+    S.fnorm2 = res2;
+    const double fnorm = std::sqrt(res2);
+    if (opts.guess == 1) {
+        k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, psi_guess, g->node_class, g->psi_ext);
+        IIM_LAUNCHED();
+        double r2g = 0.0, cg = 0.0;
+        IIM_CHECK(S.residual(&r2g, &cg));
+        if (std::isfinite(r2g) && r2g < res2) {
+            res2 = r2g;
+            cerr = cg;
+        } else {
+            // the guess raised the residual: start again from zero
+            fallback = 1;
+            k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, g->node_class, g->psi_ext);
+            IIM_LAUNCHED();
+            IIM_CHECK(S.residual(&res2, &cerr));
+        }
+    }
+    double rel = fnorm > 0.0 ? std::sqrt(res2) / fnorm : 0.0;
+    int refinements = 0;
+    iim_status st = IIM_OK;
+    while (rel > opts.rtol) {
+        if (refinements >= opts.max_refine || S.iters >= opts.max_iter) { st = IIM_ERR_NOT_CONVERGED; break; }
+        const int budget = opts.max_iter - S.iters;
+        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget) : S.correction<float>(inner, budget);
+        if (cs != IIM_OK) { st = cs; break; }
+        ++refinements;
+        IIM_CHECK(S.residual(&res2, &cerr));
+        if (!std::isfinite(res2)) { st = IIM_ERR_NONFINITE; break; }
+        rel = std::sqrt(res2) / fnorm;
+    }
+    k_velocity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->NX, g->NY, 0.5 / g->h, g->psi_ext, g->node_class, psi_box,
+                                                          psi_out, ux_out, uy_out);
+    IIM_LAUNCHED();
+    IIM_TRY(cudaEventRecord(g->ev1, s));
+    IIM_TRY(cudaEventSynchronize(g->ev1));
+    if (stats) {
+        stats->iters = S.iters;
+        stats->refinements = refinements;
+        stats->fallback = fallback;
+        stats->status = st;
+        stats->rel_res = rel;
+        stats->gmres_rel_res = S.last_gmres_rel;
+        stats->circ_err_max = cerr;
+        cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
+    }
+    return st;
+}
+
+// Rectangular Dirichlet-box solve with caller workspace (Sec. 4.2 solution operator).
+extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box, double* u, int prec,
+                                      double* work, iim_stream stream) {
+    if (!grid || !f || !u || !work) return IIM_ERR_INVALID_ARG;
+    const int nx = grid->nx, ny = grid->ny;
+    if (!is_pow2_in(nx, 16, 2048) || !is_pow2_in(ny, 16, 2048)) return IIM_ERR_INVALID_ARG;
+    if (prec != IIM_FP64 && prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
+    const double h = (grid->x1 - grid->x0) / nx;
+    if (!(h > 0.0)) return IIM_ERR_INVALID_ARG;
+    IIM_CHECK(ensure_twiddles());
+    cudaStream_t s = (cudaStream_t)stream;
+    const int NX = nx - 1, NY = ny - 1;
+    // work: transform buffer (NX*NY) followed by the eigenvalue tables (NX + NY)
+    double* buf = work;
+    double* lam = work + (size_t)NX * NY;   // NX + NY doubles (FP64) or floats
+    std::vector<double> lx(NX + NY);
+    for (int k = 0; k < NX; ++k) lx[k] = (2.0 - 2.0 * std::cos(M_PI * (k + 1) / nx)) / (h * h);
+    for (int k = 0; k < NY; ++k) lx[NX + k] = (2.0 - 2.0 * std::cos(M_PI * (k + 1) / ny)) / (h * h);
+    const double ih2 = 1.0 / (h * h);
+    if (prec == IIM_FP64) {
+        IIM_TRY(cudaMemcpyAsync(lam, lx.data(), sizeof(double) * (NX + NY), cudaMemcpyHostToDevice, s));
+        Plan<double> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lam, lam + NX, twiddles64(), (2.0 / nx) * (2.0 / ny)};
+        IIM_CHECK(rows_fwd<double>(p, 0, NY, f, psi_box, ih2, nullptr, nullptr, nullptr, 0.0, buf, s));
+        IIM_CHECK(cols<double>(p, 0, NY - 1, 0, NY - 1, buf, s));
+        IIM_CHECK((rows_inv<double, INV_STORE_F64>(p, 0, NY, buf, nullptr, u, nullptr, s)));
+    } else {
+        std::vector<float> fl(NX + NY);
+        for (int k = 0; k < NX + NY; ++k) fl[k] = (float)lx[k];
+        float* lamf = (float*)lam;
+        IIM_TRY(cudaMemcpyAsync(lamf, fl.data(), sizeof(float) * (NX + NY), cudaMemcpyHostToDevice, s));
+        Plan<float> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lamf, lamf + NX, twiddles32(), (float)((2.0 / nx) * (2.0 / ny))};
+        float* fb = (float*)buf;
+        IIM_CHECK(rows_fwd<float>(p, 0, NY, f, psi_box, ih2, nullptr, nullptr, nullptr, 0.0, fb, s));
+        IIM_CHECK(cols<float>(p, 0, NY - 1, 0, NY - 1, fb, s));
+        IIM_CHECK((rows_inv<float, INV_STORE_F64>(p, 0, NY, fb, nullptr, u, nullptr, s)));
+    }
+    // pageable-memory copies are staged before cudaMemcpyAsync returns, so the host vectors
+    // may go out of scope here
+    return IIM_OK;
+}
+
+extern "C" const char* iim_last_error_message(void) { return g_last_error; }
+
+extern "C" const char* iim_status_string(iim_status st) {
+    switch (st) {
+        case IIM_OK: return "IIM_OK";
+        case IIM_ERR_INVALID_ARG: return "IIM_ERR_INVALID_ARG";
+        case IIM_ERR_UNDERRESOLVED: return "IIM_ERR_UNDERRESOLVED";
+        case IIM_ERR_BAD_REGION: return "IIM_ERR_BAD_REGION";
+        case IIM_ERR_NONFINITE: return "IIM_ERR_NONFINITE";
+        case IIM_ERR_NOT_CONVERGED: return "IIM_ERR_NOT_CONVERGED";
+        case IIM_ERR_TIMEOUT: return "IIM_ERR_TIMEOUT";
+        case IIM_ERR_CUDA: return "IIM_ERR_CUDA";
+        default: return "IIM_UNKNOWN_STATUS";
+    }
+}

@@ -1,0 +1,194 @@
+"""GPU parity of the IIM Poisson path (through the C ABI) against the CPU oracle.
+
+Tolerances: FP64 mode must match the oracle's exact discrete solution to a relative
+L-infinity error of 1e-10; mixed mode (FP32 transforms inside FP64 refinement) to 1e-8.
+Index work (control points, affected sets) must match exactly."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2109_13628_gb300 as iim
+from oracle import geometry as geom
+from oracle import poisson as op
+from paper_2109_13628_gb300 import inputs
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {iim.IIM_FP64: 1e-10, iim.IIM_MIXED: 1e-8}
+
+
+def rel_linf(a, b, mask):
+    return np.abs(a - b)[mask].max() / max(np.abs(b)[mask].max(), 1e-300)
+
+
+# ----------------------------------------------------------------------------- box solver
+@pytest.mark.parametrize("nx,ny", [(16, 16), (64, 32), (128, 256), (512, 512), (1024, 1024), (2048, 64)])
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_box_poisson_matches_oracle(nx, ny, prec):
+    rng = np.random.default_rng(nx * 7 + ny)
+    h = 1.0 / 64
+    g = iim.make_grid(0, nx * h, 0, ny * h, nx, ny)
+    f = rng.normal(size=(ny - 1, nx - 1))
+    ring = rng.normal(size=2 * (nx + ny))
+    ref = op.poisson_box(f, h, ring)
+    u = torch.empty((ny - 1) * (nx - 1), dtype=torch.float64, device=gu.dev())
+    work = torch.empty(2 * (nx - 1) * (ny - 1), dtype=torch.float64, device=gu.dev())
+    iim.iim_box_poisson(g, gu.T(f), gu.T(ring), u, prec, work)
+    out = u.cpu().numpy().reshape(ny - 1, nx - 1)
+    err = np.abs(out - ref).max() / np.abs(ref).max()
+    assert err < (1e-12 if prec == iim.IIM_FP64 else 2e-5), err
+
+
+def test_box_poisson_eigenmode_closed_form():
+    nx = ny = 256
+    h = 4.0 / nx
+    g = iim.make_grid(-2, 2, -2, 2, nx, ny)
+    i = np.arange(1, nx)
+    k, l = 37, 200
+    mode = np.outer(np.sin(np.pi * l * i / ny), np.sin(np.pi * k * i / nx))
+    lam = 4 * math.sin(math.pi * k / (2 * nx)) ** 2 / h**2 + 4 * math.sin(math.pi * l / (2 * ny)) ** 2 / h**2
+    u = torch.empty(mode.size, dtype=torch.float64, device=gu.dev())
+    work = torch.empty(2 * mode.size, dtype=torch.float64, device=gu.dev())
+    iim.iim_box_poisson(g, gu.T(lam * mode), None, u, iim.IIM_FP64, work)
+    assert np.abs(u.cpu().numpy().reshape(mode.shape) - mode).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- geometry
+@pytest.mark.parametrize("maker", [lambda: inputs.bicubic_bodies(64, seed=0), lambda: inputs.bicubic_bodies(128, seed=1),
+                                   lambda: inputs.c1_cylinder(256), lambda: inputs.ellipses_problem(256, 5)])
+def test_geometry_matches_oracle(maker):
+    P = maker()
+    geo = gu.setup(P)
+    ref = geom.process_geometry(P.grid, P.phi, P.regions)
+    cp = {k: v.cpu().numpy() for k, v in iim.iim_geometry_control_points(geo).items()}
+    rc = ref["cp"]
+    assert geo.n_control == len(rc["t"])
+    for k_gpu, k_ref in (("axis", "axis"), ("i", "i"), ("j", "j")):
+        assert np.array_equal(cp[k_gpu], rc[k_ref])
+    assert np.array_equal(cp["body"], ref["cp_body"])
+    assert np.abs(cp["t"] - rc["t"]).max() < 1e-12
+    assert np.abs(cp["x"] - rc["x"]).max() < 1e-12 and np.abs(cp["y"] - rc["y"]).max() < 1e-12
+    ap = {k: v.cpu().numpy() for k, v in iim.iim_geometry_affected_points(geo).items()}
+    assert np.array_equal(ap["i"], ref["aff_i"]) and np.array_equal(ap["j"], ref["aff_j"])
+    assert np.array_equal(ap["solid"].astype(bool), ref["aff_solid"])
+    assert np.array_equal(ap["body"], ref["aff_body"])
+    geo.close()
+
+
+def test_geometry_errors():
+    g = inputs.square_grid(128)
+    X, Y = g.nodes()
+    star = inputs.phi_star(X, Y, 0.0, 0.85, 0.5, 0.15, 5)
+    P = inputs.Problem(grid=g, phi=star, regions=[inputs.region_around(g, star)], modes=[0], omega=None, psi_box=None,
+                       psi_b_fn=None, psibar=None, gamma=None, exact=None)
+    with pytest.raises(iim.IIMError) as e:
+        gu.setup(P)
+    assert e.value.status == iim.IIM_ERR_UNDERRESOLVED
+    a = inputs.phi_circle(X, Y, -0.6, 0, 0.4)
+    ra = inputs.region_around(g, a)
+    P2 = inputs.Problem(grid=g, phi=a, regions=[(ra[0] + 4, ra[1], ra[2], ra[3])], modes=[0], omega=None, psi_box=None,
+                        psi_b_fn=None, psibar=None, gamma=None, exact=None)
+    with pytest.raises(iim.IIMError) as e:
+        gu.setup(P2)
+    assert e.value.status == iim.IIM_ERR_BAD_REGION
+
+
+# ----------------------------------------------------------------------------- whole solve
+@pytest.mark.parametrize("n", [64, 128, 256])
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+@pytest.mark.parametrize("circulation", [True, False])
+def test_solve_matches_oracle_vortex_field(n, prec, circulation):
+    P = inputs.bicubic_bodies(n, seed=n + 3, circulation=circulation)
+    w = inputs.vortex_field(P.grid, 21, count=20, sigma=0.2)
+    P.omega = np.where(P.phi >= 0, w, 0.0)[1:-1, 1:-1]
+    S = op.Setup(P)
+    gam = op.gamma_from_regions(P) + np.array([0.05, -0.1, 0.02])
+    pb_in = None if circulation else P.psibar
+    ref, pb_ref = op.solve_unreduced(S, gamma=gam, psibar=pb_in)
+    geo = gu.setup(P)
+    out = gu.solve(P, geo, gamma=gam, psibar=pb_in, prec=prec, rtol=1e-13, velocity=True)
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    assert rel_linf(out["psi"], ref[1:-1, 1:-1], fl) < TOL[prec], out["stats"]
+    assert np.abs(out["psi"][~fl]).max() == 0.0
+    assert np.allclose(out["psibar"], pb_ref, rtol=TOL[prec], atol=TOL[prec] * np.abs(ref).max())
+    ux, uy = op.velocity(S, ref, pb_ref)
+    umax = max(np.abs(ux).max(), np.abs(uy).max())
+    assert np.abs(out["ux"] - ux).max() < 10 * TOL[prec] * umax
+    assert np.abs(out["uy"] - uy).max() < 10 * TOL[prec] * umax
+    # the residual the library reports agrees with the oracle's residual of its output
+    r_or = op.residual(S, gu.nodes_from_interior(P, out["psi"]), out["psibar"], gamma=gam)
+    assert r_or < 1e-12 and out["stats"]["rel_res"] < 1e-12
+    if circulation:
+        assert out["stats"]["circ_err_max"] < 1e-10
+    geo.close()
+
+
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_polynomial_exactness_full_size(prec, n):
+    """Any size: a bicubic psi* is reproduced exactly by the discrete IIM problem."""
+    P = inputs.bicubic_bodies(n, seed=7, circulation=True)
+    gam = np.array([op.discrete_circulation(P.exact, r) for r in P.regions])
+    geo = gu.setup(P)
+    out = gu.solve(P, geo, gamma=gam, prec=prec, rtol=1e-12)
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    assert rel_linf(out["psi"], P.exact[1:-1, 1:-1], fl) < TOL[prec], out["stats"]
+    assert np.allclose(out["psibar"], P.psibar, atol=TOL[prec] * 10)
+    geo.close()
+
+
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_c1_cylinder_1024_residual_and_accuracy(prec):
+    """The timed workload: the single-cylinder manufactured case at 1024^2 to 1e-10; the oracle
+    evaluates the un-reduced residual of the output (a property at any size) and the error
+    against the continuous solution is second-order small."""
+    P = inputs.c1_cylinder(1024)
+    S = op.Setup(P)
+    geo = gu.setup(P)
+    out = gu.solve(P, geo, prec=prec, rtol=1e-10)
+    nodes = gu.nodes_from_interior(P, out["psi"])
+    assert op.residual(S, nodes, out["psibar"]) < 1e-10
+    fl = P.phi >= 0
+    assert np.abs(nodes - P.exact)[fl].max() < 2e-5
+    geo.close()
+
+
+def test_solve_is_deterministic():
+    P = inputs.bicubic_bodies(128, seed=2, circulation=True)
+    gam = op.gamma_from_regions(P)
+    geo = gu.setup(P)
+    a = gu.solve(P, geo, gamma=gam, prec=iim.IIM_MIXED, rtol=1e-11)
+    b = gu.solve(P, geo, gamma=gam, prec=iim.IIM_MIXED, rtol=1e-11)
+    assert np.array_equal(a["psi"], b["psi"]) and np.array_equal(a["psibar"], b["psibar"])
+    geo.close()
+
+
+def test_solve_error_statuses():
+    P = inputs.bicubic_bodies(64, seed=4, circulation=True)
+    geo = gu.setup(P)
+    gam = op.gamma_from_regions(P)
+    out = gu.solve(P, geo, gamma=gam, rtol=1e-14, max_iter=2, check=False)
+    assert out["stats"]["status"] == iim.IIM_ERR_NOT_CONVERGED
+    bad = P.omega.copy()
+    bad[10, 10] = np.nan
+    out = gu.solve(P, geo, gamma=gam, omega=bad, check=False)
+    assert out["stats"]["status"] == iim.IIM_ERR_NONFINITE
+    geo.close()
+
+
+def test_guess_fallback_and_benefit():
+    P = inputs.bicubic_bodies(128, seed=5, circulation=False)
+    S = op.Setup(P)
+    ref, _ = op.solve_unreduced(S, psibar=P.psibar)
+    geo = gu.setup(P)
+    base = gu.solve(P, geo, psibar=P.psibar, rtol=1e-11)
+    good = gu.solve(P, geo, psibar=P.psibar, rtol=1e-11, guess=ref[1:-1, 1:-1] * (1 + 1e-6))
+    assert good["stats"]["fallback"] == 0 and good["stats"]["iters"] <= base["stats"]["iters"]
+    bad = gu.solve(P, geo, psibar=P.psibar, rtol=1e-11, guess=np.full_like(ref[1:-1, 1:-1], 1e6))
+    assert bad["stats"]["fallback"] == 1
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    assert rel_linf(bad["psi"], ref[1:-1, 1:-1], fl) < 1e-10
+    geo.close()
