@@ -151,6 +151,20 @@ iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* 
 iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box,
                            double* u, int prec, double* work, iim_stream stream);
 
+/* Number of kernels the library has launched in this process (all threads, all devices);
+ * monotonic.  Lets a caller count the launches inside a timed region. */
+long long iim_launch_count(void);
+
+/* Opt-in per-kernel timing (instrumentation, not part of the method): between
+ * iim_profile_begin and iim_profile_end, every kernel the calling thread launches is bracketed
+ * by CUDA events on its stream.  iim_profile_end waits for those events and writes one record
+ * per kernel name (launch count, summed milliseconds, summed algorithmic bytes and flops) into
+ * `out` (host, `capacity` entries; the names are static strings) and returns the number of
+ * distinct names (which may exceed `capacity`). */
+typedef struct { const char* name; long long launches; double ms; double bytes; double flops; } iim_kernel_stat;
+iim_status iim_profile_begin(void);
+int iim_profile_end(iim_kernel_stat* out, int capacity);
+
 /* Text of the last CUDA failure recorded by this thread (empty when none). */
 const char* iim_last_error_message(void);
 

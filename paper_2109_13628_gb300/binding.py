@@ -47,6 +47,10 @@ class iim_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class iim_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_longlong), ("ms", _d), ("bytes", _d), ("flops", _d)]
+
+
 SIGNATURES = [
     ("iim_setup_geometry", _i, [ctypes.POINTER(iim_grid), _vp, _i, ctypes.POINTER(iim_region), _ip, _vp,
                                 ctypes.POINTER(_vp)]),
@@ -57,6 +61,9 @@ SIGNATURES = [
                                ctypes.POINTER(iim_stats), _vp]),
     ("iim_box_poisson", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp, _vp]),
     ("iim_last_error_message", ctypes.c_char_p, []),
+    ("iim_launch_count", ctypes.c_longlong, []),
+    ("iim_profile_begin", _i, []),
+    ("iim_profile_end", _i, [ctypes.POINTER(iim_kernel_stat), _i]),
     ("iim_destroy_geometry", None, [_vp]),
     ("iim_status_string", ctypes.c_char_p, [_i]),
 ]
@@ -186,7 +193,7 @@ def iim_geometry_affected_points(g: Geometry, stream=None):
     return out
 
 
-def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=40, max_refine=8, guess=0, inner_rtol=0.0):
+def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=64, max_refine=12, guess=0, inner_rtol=0.0):
     return iim_opts(int(prec), float(rtol), int(max_iter), int(restart), int(max_refine), int(guess), float(inner_rtol))
 
 
@@ -226,3 +233,19 @@ def iim_status_string(st: int) -> str:
 
 def iim_destroy_geometry(g: Geometry):
     g.close()
+
+
+def iim_launch_count() -> int:
+    return int(load().iim_launch_count())
+
+
+def iim_profile_begin():
+    _check(load().iim_profile_begin(), "iim_profile_begin")
+
+
+def iim_profile_end(capacity: int = 128):
+    """Per-kernel records [{name, launches, ms, bytes, flops}] since iim_profile_begin."""
+    buf = (iim_kernel_stat * capacity)()
+    n = load().iim_profile_end(buf, capacity)
+    return [{"name": buf[k].name.decode(), "launches": buf[k].launches, "ms": buf[k].ms, "bytes": buf[k].bytes,
+             "flops": buf[k].flops} for k in range(min(n, capacity))]

@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <utility>
 #include <vector>
 
 #include "../../include/iim.h"
@@ -69,11 +70,30 @@ inline int ilog2(int n) {
 }
 inline bool is_pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
-template <typename T>
-struct DevBuf {
-    T* p = nullptr;
-    size_t n = 0;
+// Counts every kernel launch of the library; while profiling is on (iim_profile_begin) it
+// also records CUDA events around the launch on its stream, tagged with the kernel's name and
+// its algorithmic bytes / flops.
+struct KTrace {
+    KTrace(const char* name, cudaStream_t s, double bytes = 0.0, double flops = 0.0);
+    ~KTrace();
+    bool active;
+    cudaStream_t stream;
+    int idx;
 };
+
+// While a stream capture is being recorded, launches are neither counted nor timed (the
+// replays of the captured graph are counted by the caller through count_launches).
+void set_capture(bool on);
+bool profiling_active();
+void count_launches(long long n);
+
+// k<<<grid, block, smem, s>>>(args...) with launch accounting.
+template <typename... KArgs, typename... Args>
+inline void launch(const char* name, double bytes, double flops, void (*k)(KArgs...), dim3 grid, dim3 block,
+                   size_t smem, cudaStream_t s, Args&&... args) {
+    KTrace t(name, s, bytes, flops);
+    k<<<grid, block, smem, s>>>(std::forward<Args>(args)...);
+}
 
 }  // namespace iim
 
@@ -126,4 +146,11 @@ struct iim_geometry_s {
     int* d_int = nullptr;        // device counters / flags
     double* h_pinned = nullptr;  // pinned host scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
+    void* graph64 = nullptr;     // captured GMRES iteration (FP64 transforms)
+    void* graph32 = nullptr;     // captured GMRES iteration (FP32 transforms)
 };
+
+namespace iim {
+void destroy_graphs(iim_geometry g);
+}

@@ -200,7 +200,7 @@ __global__ void k_classify(int nx, int ny, const double* __restrict__ phi, uint8
             gop += 4 * __popc(usable_dirs(phi, nx, ny, qi, qj, nullptr));
         }
     }
-    cls[node] = c;
+    cls[(long)(gj - 1) * nx + gi] = c;   // padded layout
     aff_flag[node] = (c == CLS_PLUS || c == CLS_MINUS);
     minus_flag[node] = (c == CLS_MINUS);
     gop_cnt[node] = gop;
@@ -245,7 +245,7 @@ __device__ int emit_ghost(int nx, int ny, const double* phi, const int* pos, con
         ++o;
         for (int m = 2; m <= 4; ++m) {
             const int qi = gi + m * c_dir_i[d], qj = gj + m * c_dir_j[d];
-            idx[o] = (qj - 1) * NX + (qi - 1);
+            idx[o] = (qj - 1) * nx + qi;   // padded layout
             w[o] = wt[m - 1] * s;
             ++o;
         }
@@ -262,12 +262,13 @@ __global__ void k_fill(int nx, int ny, double h, const double* __restrict__ phi,
     const int NX = nx - 1, NY = ny - 1;
     const long node = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= (long)NX * NY) return;
-    const uint8_t c = cls[node];
-    if (c != CLS_PLUS && c != CLS_MINUS) return;
     const int gi = (int)(node % NX) + 1, gj = (int)(node / NX) + 1;
+    const long pnode = (long)(gj - 1) * nx + gi;   // padded layout
+    const uint8_t c = cls[pnode];
+    if (c != CLS_PLUS && c != CLS_MINUS) return;
     const int W = nx + 1;
     const int a = aff_pos[node];
-    aff_node[a] = (int)node;
+    aff_node[a] = (int)pnode;
     aff_solid[a] = (c == CLS_MINUS);
     const int b = body_of(gi, gj, nb, R);
     aff_body[a] = b;
@@ -279,12 +280,12 @@ __global__ void k_fill(int nx, int ny, double h, const double* __restrict__ phi,
         for (int d = 0; d < 4; ++d) {
             const int qi = gi + c_dir_i[d], qj = gj + c_dir_j[d];
             if (solid_at(phi, W, qi, qj)) continue;
-            gop_idx[o] = (qj - 1) * NX + (qi - 1);
+            gop_idx[o] = (qj - 1) * nx + qi;
             gop_w[o] = ih2;
             ++o;
         }
         const int m = minus_pos[node];
-        minus_node[m] = (int)node;
+        minus_node[m] = (int)pnode;
         emit_ghost(nx, ny, phi, edge_pos, tval, gi, gj, 1.0, gh_idx + gh_off[node], gh_w + gh_off[node]);
     } else {
         // gamma_p = -(1/h^2) sum of the ghost values of the solid neighbours
@@ -324,7 +325,7 @@ __global__ void k_check_regions(int nx, int nb, const iim_region* __restrict__ R
         const int i = r.lx - 1 + t % w, j = r.ly - 1 + t / w;
         const bool inner = (i > r.lx && i < r.rx && j > r.ly && j < r.ry);
         if (inner) continue;
-        if (cls[(long)(j - 1) * NX + (i - 1)] != CLS_FLUID) atomicOr(err, ERR_FACES);
+        if (cls[(long)(j - 1) * nx + i] != CLS_FLUID) atomicOr(err, ERR_FACES);
     }
 }
 
@@ -334,9 +335,15 @@ __global__ void k_row_ptr(int NX, int NY, int na, const int* __restrict__ aff_po
     if (r == NY) row_ptr[NY] = na;
 }
 
-__global__ void k_ptr_from_offsets(int n, const int* __restrict__ nodes, const int* __restrict__ off, int total, int* ptr) {
+// ptr[a] = offset of node a (nodes in the padded layout, offsets over the unpadded one)
+__global__ void k_ptr_from_offsets(int n, int nx, const int* __restrict__ nodes, const int* __restrict__ off, int total,
+                                   int* ptr) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a < n) ptr[a] = off[nodes[a]];
+    if (a < n) {
+        const int p = nodes[a];
+        const int r = p / nx, i = p - r * nx - 1;
+        ptr[a] = off[(long)r * (nx - 1) + i];
+    }
     if (a == n) ptr[n] = total;
 }
 
@@ -459,7 +466,9 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
                                                             g->cp_axis, g->cp_ei, g->cp_ej, err);
     SETUP_CUDA(cudaGetLastError());
 
-    SETUP_TRY(dalloc(&g->node_class, nnode));
+    const long npad = (long)nx * NY;   // padded layout: row r at [r*nx, r*nx + nx), slot 0 a pad
+    SETUP_TRY(dalloc(&g->node_class, npad));
+    SETUP_CUDA(cudaMemsetAsync(g->node_class, CLS_SOLID, npad, s));
     SETUP_TRY(dalloc(&aff_flag, nnode)); SETUP_TRY(dalloc(&aff_pos, nnode));
     SETUP_TRY(dalloc(&minus_flag, nnode)); SETUP_TRY(dalloc(&minus_pos, nnode));
     SETUP_TRY(dalloc(&gop_cnt, nnode)); SETUP_TRY(dalloc(&gop_off, nnode));
@@ -485,8 +494,8 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
                                                          epos, tval, n_bodies, g->d_regions, g->aff_node, g->aff_body,
                                                          g->aff_solid, g->gop_idx, g->gop_w, g->minus_node, g->gh_idx,
                                                          g->gh_w, err);
-    k_ptr_from_offsets<<<(na + 256) / 256, 256, 0, s>>>(na, g->aff_node, gop_off, gop_total, g->gop_ptr);
-    k_ptr_from_offsets<<<(nm + 256) / 256, 256, 0, s>>>(nm, g->minus_node, gh_off, gh_total, g->gh_ptr);
+    k_ptr_from_offsets<<<(na + 256) / 256, 256, 0, s>>>(na, nx, g->aff_node, gop_off, gop_total, g->gop_ptr);
+    k_ptr_from_offsets<<<(nm + 256) / 256, 256, 0, s>>>(nm, nx, g->minus_node, gh_off, gh_total, g->gh_ptr);
     k_row_ptr<<<(NY + 256) / 256, 256, 0, s>>>(NX, NY, na, aff_pos, g->aff_row_ptr);
     if (n_bodies) k_check_regions<<<n_bodies, 256, 0, s>>>(nx, n_bodies, g->d_regions, g->node_class, err);
     SETUP_CUDA(cudaGetLastError());
@@ -499,7 +508,7 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
     SETUP_CUDA(cudaStreamSynchronize(s));
     if (herr & (ERR_REGION | ERR_FACES)) return fail(IIM_ERR_BAD_REGION);
     if (na > 0) {
-        g->ja0 = first / NX; g->ja1 = last / NX;
+        g->ja0 = first / nx; g->ja1 = last / nx;
         g->jo0 = std::max(0, g->ja0 - 4); g->jo1 = std::min(NY - 1, g->ja1 + 4);
     } else {
         g->ja0 = 0; g->ja1 = -1; g->jo0 = 0; g->jo1 = -1;
@@ -518,14 +527,17 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
         SETUP_CUDA(cudaMemcpy(g->lam_y32, fy.data(), NY * sizeof(float), cudaMemcpyHostToDevice));
     }
     // solver workspace
-    SETUP_TRY(dalloc(&g->psi_ext, nnode));
-    SETUP_TRY(dalloc(&g->res, nnode));
-    SETUP_TRY(dalloc((double**)&g->tbuf, nnode));   // sized for FP64, reused for FP32
-    SETUP_TRY(dalloc((double**)&g->psiT, nnode));
+    SETUP_TRY(dalloc(&g->psi_ext, npad));
+    SETUP_TRY(dalloc(&g->res, npad));
+    SETUP_TRY(dalloc((double**)&g->tbuf, npad));   // sized for FP64, reused for FP32
+    SETUP_TRY(dalloc((double**)&g->psiT, npad));
+    SETUP_CUDA(cudaMemsetAsync(g->psi_ext, 0, npad * sizeof(double), s));
+    SETUP_CUDA(cudaMemsetAsync(g->psiT, 0, npad * sizeof(double), s));
     SETUP_TRY(dalloc(&g->partial, 4096 * 72));
     SETUP_TRY(dalloc(&g->small, 4096));
     SETUP_TRY(dalloc(&g->d_int, 256));   // [32, 96): circulation body ids
     SETUP_CUDA(cudaMallocHost(&g->h_pinned, 64 * sizeof(double)));
+    SETUP_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     SETUP_CUDA(cudaEventCreate(&g->ev0));
     SETUP_CUDA(cudaEventCreate(&g->ev1));
 #undef SETUP_TRY
@@ -541,6 +553,7 @@ void free_geometry(iim_geometry g) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(g->device);
+    destroy_graphs(g);
     void* ptrs[] = {g->cp_x, g->cp_y, g->cp_t, g->cp_body, g->cp_axis, g->cp_ei, g->cp_ej, g->aff_node, g->aff_body,
                     g->aff_row_ptr, g->aff_solid, g->gop_ptr, g->gop_idx, g->gop_w, g->minus_node, g->gh_ptr,
                     g->gh_idx, g->gh_w, g->node_class, g->body_circ, g->d_regions, g->lam_x64, g->lam_y64,
@@ -550,6 +563,7 @@ void free_geometry(iim_geometry g) {
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     delete g;
     cudaSetDevice(cur);
 }
@@ -570,9 +584,10 @@ __global__ void k_export_aff(int na, int NX, const int* __restrict__ node, const
                              const int* __restrict__ body, int* oi, int* oj, int* os, int* ob) {
     const int a = blockIdx.x * blockDim.x + threadIdx.x;
     if (a >= na) return;
-    const int n = node[a];
-    if (oi) oi[a] = n % NX + 1;
-    if (oj) oj[a] = n / NX + 1;
+    const int n = node[a];   // padded layout
+    const int nx = NX + 1;
+    if (oi) oi[a] = n % nx;
+    if (oj) oj[a] = n / nx + 1;
     if (os) os[a] = solid[a];
     if (ob) ob[a] = body[a];
 }

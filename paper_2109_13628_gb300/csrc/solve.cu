@@ -13,10 +13,15 @@
 // The Krylov solver is restarted GMRES with classical Gram-Schmidt applied twice; all Krylov
 // vectors and inner products are FP64.  In FP64 mode the rectangular solves use FP64
 // transforms; in mixed mode FP32 transforms (the refinement keeps the FP64 residual exact).
+//
+// One GMRES iteration is a fixed sequence of kernels that read the iteration index from
+// device memory and become no-ops once a device stop flag is set, so the sequence is captured
+// once as a CUDA graph and replayed; the host reads the convergence state once per batch.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 #include "dst.cuh"
@@ -84,8 +89,12 @@ struct Plan {
     T norm;
 };
 
+// Algorithmic flops of one DST-I of n - 1 points through an n/2-point complex FFT
+// (2.5 n log2(2n): the half-length FFT plus the packing and split steps).
+static inline double dst_flops(int n) { return 2.5 * n * std::log2(2.0 * n); }
+
 template <typename T>
-constexpr int cols_per_block() { return sizeof(T) == 8 ? 4 : 8; }
+constexpr int cols_per_block() { return 4; }
 constexpr int kRowWarps = 4;
 
 template <typename T>
@@ -112,38 +121,45 @@ static void allow_smem(KernelT k, size_t bytes) {
     g_attr_done.push_back({{dev, key}, bytes});
 }
 
+static const VecArg kNoVec{nullptr, nullptr, 0, 0};
+
 template <typename T>
-static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* dense, const double* ring, double ih2,
-                           const int* row_ptr, const int* aff_node, const double* gam, double gsign, T* out,
-                           cudaStream_t s) {
+static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* dense, int dld, int doff,
+                           const double* ring, double ih2, const int* row_ptr, const int* aff_node, VecArg gam,
+                           double gsign, T* out, const int* stop, cudaStream_t s) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
     allow_smem(k_rows_fwd<T, kRowWarps>, sm);
-    k_rows_fwd<T, kRowWarps><<<(nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s>>>(
-        p.NX, p.NY, p.nx, p.lognx, row0, nrows, dense, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out);
+    launch(sizeof(T) == 8 ? "dst_rows_fwd_f64" : "dst_rows_fwd_f32",
+           (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx),
+           k_rows_fwd<T, kRowWarps>, (nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s, p.NX, p.NY, p.nx,
+           p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
     IIM_LAUNCHED();
     return IIM_OK;
 }
 
 template <typename T>
-static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, cudaStream_t s) {
+static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s) {
     constexpr int C = cols_per_block<T>();
     const size_t sm = cols_smem<T>(p.ny);
     allow_smem(k_cols<T, C>, sm);
-    k_cols<T, C><<<(p.NX + C - 1) / C, C * 32, sm, s>>>(p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x,
-                                                      p.lam_y, p.norm, p.tw);
+    launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32", (double)(in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
+           (double)p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), k_cols<T, C>, p.nx / C, C * 32, sm, s, p.NX, p.NY, p.ny,
+           p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop);
     IIM_LAUNCHED();
     return IIM_OK;
 }
 
 template <typename T, int MODE>
-static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T* outT, double* out64,
-                           const uint8_t* cls, cudaStream_t s) {
+static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T* outT, double* out64, int old,
+                           int ooff, const uint8_t* cls, const int* stop, cudaStream_t s) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
     allow_smem(k_rows_inv<T, kRowWarps, MODE>, sm);
-    k_rows_inv<T, kRowWarps, MODE><<<(nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s>>>(
-        p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, cls, p.tw);
+    launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
+           (double)nrows * p.NX * (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
+           (double)nrows * dst_flops(p.nx), k_rows_inv<T, kRowWarps, MODE>, (nrows + kRowWarps - 1) / kRowWarps,
+           kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw, stop);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -178,39 +194,49 @@ __device__ __forceinline__ double block_sum(double v) {
     return r;   // valid in thread 0
 }
 
-// ------------------------------------------------------------------------- IIM operators
-// out[a] = (v ? v[a] : 0) + sum_e w_e * (idx >= 0 ? psi[idx] : bc(control point))
-// with bc = -xc[body_circ[body]] for circulation bodies (the -B sum psibar 1_k column) when
-// xc is given, else 0.
-template <typename T>
-__global__ void k_gather(int na, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ w,
-                         const T* __restrict__ psi, const int* __restrict__ cp_body, const int* __restrict__ body_circ,
-                         const double* __restrict__ xc, const double* __restrict__ v, double* __restrict__ out) {
-    const int a = blockIdx.x * blockDim.x + threadIdx.x;
-    if (a >= na) return;
-    double acc = 0.0;
-    for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
-        const int q = idx[e];
-        if (q >= 0) {
-            acc += w[e] * (double)psi[q];
-        } else if (xc) {
-            const int bc = body_circ[cp_body[-q - 1]];
-            if (bc >= 0) acc -= w[e] * xc[bc];
-        }
-    }
-    out[a] = (v ? v[a] : 0.0) + acc;
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
 }
 
-// out[c] = sum over affected points of circulation body c of v
-template <int BLOCK>
-__global__ void k_circ_rows(int na, const int* __restrict__ aff_body, const int* __restrict__ body_circ,
-                            const double* __restrict__ v, double* __restrict__ out) {
-    const int c = blockIdx.x;
-    double acc = 0.0;
-    for (int a = threadIdx.x; a < na; a += BLOCK)
-        if (body_circ[aff_body[a]] == c) acc += v[a];
-    acc = block_sum<BLOCK>(acc);
-    if (threadIdx.x == 0) out[c] = acc;
+// ------------------------------------------------------------------------- IIM operators
+// Blocks [0, nga): out[a] = (v ? v[a] : 0) + sum_e w_e * (idx >= 0 ? psi[idx] : bc(cp)),
+// bc = -xc[body_circ[body]] for circulation bodies (the -B sum psibar 1_k column) when xc is
+// given, else 0.  Blocks [nga, nga + ncirc): out[na + c] = sum of v over body c's affected
+// points (the circulation rows), when v is given.
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_gather(int na, int nga, const int* __restrict__ ptr, const int* __restrict__ idx, const double* __restrict__ w,
+         const T* __restrict__ psi, const int* __restrict__ cp_body, const int* __restrict__ body_circ,
+         const int* __restrict__ aff_body, VecArg vin, int use_xc, double* __restrict__ outb, const int* __restrict__ jidx,
+         long stride, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    const double* v = vin.base ? vin.get() : nullptr;
+    double* out = jidx ? outb + (long)(*jidx + 1) * stride : outb;
+    if ((int)blockIdx.x < nga) {
+        const int a = blockIdx.x * BLOCK + threadIdx.x;
+        if (a >= na) return;
+        const double* xc = (use_xc && v) ? v + na : nullptr;
+        double acc = 0.0;
+        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+            const int q = idx[e];
+            if (q >= 0) {
+                acc += w[e] * (double)psi[q];
+            } else if (xc) {
+                const int bc = body_circ[cp_body[-q - 1]];
+                if (bc >= 0) acc -= w[e] * xc[bc];
+            }
+        }
+        out[a] = (v ? v[a] : 0.0) + acc;
+    } else {
+        if (!v) return;
+        const int c = blockIdx.x - nga;
+        double acc = 0.0;
+        for (int a = threadIdx.x; a < na; a += BLOCK)
+            if (body_circ[aff_body[a]] == c) acc += v[a];
+        acc = block_sum<BLOCK>(acc);
+        if (threadIdx.x == 0) out[na + c] = acc;
+    }
 }
 
 // Ghost values at A- nodes from fluid values and psi_b + psibar (Sec. 2.1, 2.2).
@@ -231,24 +257,25 @@ __global__ void k_ghost(int nm, const int* __restrict__ minus_node, const int* _
     psi[minus_node[m]] = acc;
 }
 
-// Un-reduced FP64 residual at interior nodes: r = omega + nabla_h^2 psi_ext at fluid nodes,
-// 0 in the solid; per-block partial sums of r^2.
+// Un-reduced FP64 residual: r = omega + nabla_h^2 psi_ext at fluid nodes, 0 in the solid and
+// in the pads (padded layout); per-block partial sums of r^2.
 template <int BLOCK>
 __global__ void k_residual(int NX, int NY, double ih2, const double* __restrict__ psi, const double* __restrict__ omega,
                            const uint8_t* __restrict__ cls, const double* __restrict__ ring, double* __restrict__ res,
                            double* __restrict__ partial) {
-    const long n = (long)NX * NY;
+    const int nx = NX + 1;
+    const long n = (long)nx * NY;
     double acc = 0.0;
     for (long k = (long)blockIdx.x * BLOCK + threadIdx.x; k < n; k += (long)gridDim.x * BLOCK) {
-        const int i = (int)(k % NX), j = (int)(k / NX);
+        const int j = (int)(k / nx), i = (int)(k - (long)j * nx) - 1;
         double r = 0.0;
-        if (cls[k] <= CLS_PLUS) {
+        if (i >= 0 && cls[k] <= CLS_PLUS) {
             const double c = psi[k];
             const double wv = i > 0 ? psi[k - 1] : (ring ? ring[2 * (NX + 2) + j] : 0.0);
             const double ev = i < NX - 1 ? psi[k + 1] : (ring ? ring[2 * (NX + 2) + NY + j] : 0.0);
-            const double sv = j > 0 ? psi[k - NX] : (ring ? ring[i + 1] : 0.0);
-            const double nv = j < NY - 1 ? psi[k + NX] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
-            r = omega[k] - (4.0 * c - wv - ev - sv - nv) * ih2;
+            const double sv = j > 0 ? psi[k - nx] : (ring ? ring[i + 1] : 0.0);
+            const double nv = j < NY - 1 ? psi[k + nx] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
+            r = omega[(long)j * NX + i] - (4.0 * c - wv - ev - sv - nv) * ih2;
             acc += r * r;
         }
         res[k] = r;
@@ -257,9 +284,9 @@ __global__ void k_residual(int NX, int NY, double ih2, const double* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-// Sum of an interior field over region R_k of each circulation body; grid (ncirc, S).
+// Sum of a padded field over region R_k of each circulation body; grid (ncirc, S).
 template <int BLOCK>
-__global__ void k_region_sums(int NX, const double* __restrict__ f, const iim_region* __restrict__ R,
+__global__ void k_region_sums(int nx, const double* __restrict__ f, const iim_region* __restrict__ R,
                               const int* __restrict__ circ_ids, double* __restrict__ partial) {
     const int c = blockIdx.x, part = blockIdx.y, S = gridDim.y;
     const iim_region r = R[circ_ids[c]];
@@ -268,7 +295,7 @@ __global__ void k_region_sums(int NX, const double* __restrict__ f, const iim_re
     double acc = 0.0;
     for (long t = (long)part * BLOCK + threadIdx.x; t < n; t += (long)S * BLOCK) {
         const int i = r.lx + (int)(t % w), j = r.ly + (int)(t / w);
-        acc += f[(long)(j - 1) * NX + (i - 1)];
+        acc += f[(long)(j - 1) * nx + i];
     }
     acc = block_sum<BLOCK>(acc);
     if (threadIdx.x == 0) partial[c * S + part] = acc;
@@ -277,11 +304,11 @@ __global__ void k_region_sums(int NX, const double* __restrict__ f, const iim_re
 // Discrete circulation -h sum_{dR}(grad_h psi).n (Eq. discretecircconstraint) of each circulation
 // body, from the fluid values of psi on the faces of R_k.
 template <int BLOCK>
-__global__ void k_circ_measure(int NX, const double* __restrict__ psi, const iim_region* __restrict__ R,
+__global__ void k_circ_measure(int nx, const double* __restrict__ psi, const iim_region* __restrict__ R,
                                const int* __restrict__ circ_ids, double* __restrict__ out) {
     const int c = blockIdx.x;
     const iim_region r = R[circ_ids[c]];
-    auto P = [&](int i, int j) { return psi[(long)(j - 1) * NX + (i - 1)]; };
+    auto P = [&](int i, int j) { return psi[(long)(j - 1) * nx + i]; };
     double acc = 0.0;
     for (int j = r.ly + threadIdx.x; j <= r.ry; j += BLOCK)
         acc += (P(r.rx + 1, j) - P(r.rx, j)) - (P(r.lx, j) - P(r.lx - 1, j));
@@ -292,17 +319,21 @@ __global__ void k_circ_measure(int NX, const double* __restrict__ psi, const iim
 }
 
 // small[] layout
-enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_BNORM2 = 2, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048 };
+enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048 };
 constexpr int kRegionParts = 16;
 
-// Combines the partial sums: res2 = sum r^2 + sum rc^2, bcirc[c] = sum_{R_k} r - rc_c,
-// rc_c = (Gamma_k - circ_k) / h^2.
+// Combines partial sums into *out_res2 = sum partial + sum rc^2 and, for circulation bodies,
+// bcirc[c] = sum_{R_k} r - rc_c with rc_c = (Gamma_k - circ_k) / h^2; max |Gamma_k - circ_k|
+// goes to small[SM_CIRC_ERR] when ncirc > 0 or out_res2 is small[SM_RES2].
+template <int BLOCK>
 __global__ void k_finish_residual(int nparts, const double* __restrict__ partial, int ncirc,
                                   const int* __restrict__ circ_ids, const double* __restrict__ gamma, double ih2,
-                                  double* __restrict__ small, const double* __restrict__ regpart, double* __restrict__ bcirc) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+                                  double* __restrict__ small, const double* __restrict__ regpart,
+                                  double* __restrict__ bcirc, double* __restrict__ out_res2) {
     double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += partial[b];
+    for (int b = threadIdx.x; b < nparts; b += BLOCK) s += partial[b];
+    s = block_sum<BLOCK>(s);
+    if (threadIdx.x != 0) return;
     double cerr = 0.0;
     for (int c = 0; c < ncirc; ++c) {
         const double gk = gamma ? gamma[circ_ids[c]] : 0.0;
@@ -315,14 +346,17 @@ __global__ void k_finish_residual(int nparts, const double* __restrict__ partial
         for (int p = 0; p < kRegionParts; ++p) reg += regpart[c * kRegionParts + p];
         if (bcirc) bcirc[c] = reg - rc;
     }
-    small[SM_RES2] = s;
-    small[SM_CIRC_ERR] = cerr;
+    out_res2[0] = s;
+    if (out_res2 == small + SM_RES2) small[SM_CIRC_ERR] = cerr;
 }
 
-__global__ void k_init_psi(long n, const double* __restrict__ guess, const uint8_t* __restrict__ cls, double* __restrict__ psi) {
+__global__ void k_init_psi(int NX, int NY, const double* __restrict__ guess, const uint8_t* __restrict__ cls,
+                           double* __restrict__ psi) {
+    const int nx = NX + 1;
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    psi[k] = (guess && cls[k] <= CLS_PLUS) ? guess[k] : 0.0;
+    if (k >= (long)nx * NY) return;
+    const int j = (int)(k / nx), i = (int)(k - (long)j * nx) - 1;
+    psi[k] = (guess && i >= 0 && cls[k] <= CLS_PLUS) ? guess[(long)j * NX + i] : 0.0;
 }
 
 __global__ void k_init_psibar(int nb, const int* __restrict__ body_circ, const double* __restrict__ in, int keep_circ,
@@ -339,23 +373,25 @@ __global__ void k_add_psibar(int ncirc, const int* __restrict__ circ_ids, const 
 }
 
 // Velocity u = (d_y psi, -d_x psi) by centered differences of psi_ext at fluid nodes (Sec. 4.2,
-// end); psi_out = psi at fluid nodes, 0 in the solid.
+// end); psi_out = psi at fluid nodes, 0 in the solid.  Outputs in the caller's layout.
 __global__ void k_velocity(int NX, int NY, double inv2h, const double* __restrict__ psi, const uint8_t* __restrict__ cls,
                            const double* __restrict__ ring, double* __restrict__ psi_out, double* __restrict__ ux,
                            double* __restrict__ uy) {
     const long n = (long)NX * NY;
     const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
+    const int nx = NX + 1;
     const int i = (int)(k % NX), j = (int)(k / NX);
-    const bool fl = cls[k] <= CLS_PLUS;
-    if (psi_out) psi_out[k] = fl ? psi[k] : 0.0;
+    const long p = (long)j * nx + 1 + i;
+    const bool fl = cls[p] <= CLS_PLUS;
+    if (psi_out) psi_out[k] = fl ? psi[p] : 0.0;
     if (!ux && !uy) return;
     double vx = 0.0, vy = 0.0;
     if (fl) {
-        const double wv = i > 0 ? psi[k - 1] : (ring ? ring[2 * (NX + 2) + j] : 0.0);
-        const double ev = i < NX - 1 ? psi[k + 1] : (ring ? ring[2 * (NX + 2) + NY + j] : 0.0);
-        const double sv = j > 0 ? psi[k - NX] : (ring ? ring[i + 1] : 0.0);
-        const double nv = j < NY - 1 ? psi[k + NX] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
+        const double wv = i > 0 ? psi[p - 1] : (ring ? ring[2 * (NX + 2) + j] : 0.0);
+        const double ev = i < NX - 1 ? psi[p + 1] : (ring ? ring[2 * (NX + 2) + NY + j] : 0.0);
+        const double sv = j > 0 ? psi[p - nx] : (ring ? ring[i + 1] : 0.0);
+        const double nv = j < NY - 1 ? psi[p + nx] : (ring ? ring[(NX + 2) + i + 1] : 0.0);
         vx = (nv - sv) * inv2h;
         vy = -(ev - wv) * inv2h;
     }
@@ -364,34 +400,10 @@ __global__ void k_velocity(int NX, int NY, double inv2h, const double* __restric
 }
 
 // ------------------------------------------------------------------------- GMRES kernels
-template <int BLOCK>
-__global__ void k_dots(int j, const double* __restrict__ V, long ld, const double* __restrict__ w, int ns,
-                       double* __restrict__ out) {
-    const int i = blockIdx.x;
-    if (i > j) return;
-    const double* vi = V + (long)i * ld;
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < ns; e += BLOCK) acc += vi[e] * w[e];
-    acc = block_sum<BLOCK>(acc);
-    if (threadIdx.x == 0) out[i] = acc;
-}
-
-__global__ void k_update(int j, const double* __restrict__ V, long ld, const double* __restrict__ coef, int ns,
-                         double* __restrict__ w) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ns) return;
-    double s = 0.0;
-    for (int i = 0; i <= j; ++i) s += coef[i] * V[(long)i * ld + e];
-    w[e] -= s;
-}
-
-template <int BLOCK>
-__global__ void k_sumsq(const double* __restrict__ w, int ns, double* __restrict__ partial) {
-    double acc = 0.0;
-    for (int e = blockIdx.x * BLOCK + threadIdx.x; e < ns; e += gridDim.x * BLOCK) acc += w[e] * w[e];
-    acc = block_sum<BLOCK>(acc);
-    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-}
+// Device state (int): [0] j (column of the current cycle), [1] stop, [2] iterations of this
+// call, [3] max iterations of this call, [4] converged, [5] scratch column index,
+// [32, 96) circulation body ids
+enum { DI_J = 0, DI_STOP = 1, DI_IT = 2, DI_MAXIT = 3, DI_CONV = 4, DI_TMPJ = 5, DI_CIRC = 32 };
 
 // Krylov small-storage layout inside g->H (m <= 64):
 //   H (m+1) x m column-major | cs[m] | sn[m] | gv[m+1] | hc1[m+1] | hc2[m+1] | y[m] | scal[8]
@@ -407,13 +419,62 @@ struct KLayout {
     __host__ __device__ long scal() const { return y() + m; }
     __host__ __device__ long total() const { return scal() + 8; }
 };
-enum { SC_INV = 0, SC_RESID = 1, SC_BETA = 2 };
+enum { SC_INV = 0, SC_RESID = 1, SC_BETA = 2, SC_TOL = 3 };
 
-// Arnoldi step j finish: norm, Hessenberg column, Givens rotations, residual estimate.
-__global__ void k_arnoldi_tail(int j, KLayout L, int nparts, const double* __restrict__ partial, double* __restrict__ K) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// h[i] = <V_i, V_{j+1}> for i <= j (one block per i)
+template <int BLOCK>
+__global__ void k_dots(const int* __restrict__ di, const double* __restrict__ V, long ld, int ns, double* __restrict__ out) {
+    if (di[DI_STOP]) return;
+    const int j = di[DI_J];
+    const int i = blockIdx.x;
+    if (i > j) return;
+    const double* vi = V + (long)i * ld;
+    const double* w = V + (long)(j + 1) * ld;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) acc += vi[e] * w[e];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) out[i] = acc;
+}
+
+// V_{j+1} -= sum_{i<=j} coef[i] V_i; with `partial`, per-block sums of squares of the result.
+template <int BLOCK>
+__global__ void k_update(const int* __restrict__ di, double* __restrict__ V, long ld, const double* __restrict__ coef,
+                         int ns, double* __restrict__ partial) {
+    if (di[DI_STOP]) return;
+    const int j = di[DI_J];
+    const int e = blockIdx.x * BLOCK + threadIdx.x;
+    double* w = V + (long)(j + 1) * ld;
+    double val = 0.0;
+    if (e < ns) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += coef[i] * V[(long)i * ld + e];
+        val = w[e] - s;
+        w[e] = val;
+    }
+    if (partial) {
+        const double sq = block_sum<BLOCK>(val * val);
+        if (threadIdx.x == 0) partial[blockIdx.x] = sq;
+    }
+}
+
+template <int BLOCK>
+__global__ void k_sumsq(const double* __restrict__ w, int ns, double* __restrict__ partial) {
+    double acc = 0.0;
+    for (int e = blockIdx.x * BLOCK + threadIdx.x; e < ns; e += gridDim.x * BLOCK) acc += w[e] * w[e];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// Arnoldi step finish: norm, Hessenberg column, Givens rotations, residual estimate, stop test.
+__global__ void k_arnoldi_tail(int* __restrict__ di, KLayout L, int nparts, const double* __restrict__ partial,
+                               double* __restrict__ K) {
+    if (di[DI_STOP]) return;
+    const int lane = threadIdx.x;
     double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += partial[b];
+    for (int b = lane; b < nparts; b += 32) s += partial[b];
+    s = warp_sum(s);
+    if (lane != 0) return;
+    const int j = di[DI_J];
     const double nrm = sqrt(s);
     double* H = K + L.H();
     const int ldh = L.m + 1;
@@ -429,25 +490,34 @@ __global__ void k_arnoldi_tail(int j, KLayout L, int nparts, const double* __res
         col[i] = t;
     }
     const double d = hypot(col[j], col[j + 1]);
-    const double c = d > 0.0 ? col[j] / d : 1.0, sgn = d > 0.0 ? col[j + 1] / d : 0.0;
+    const double c = d > 0.0 ? col[j] / d : 1.0, sg = d > 0.0 ? col[j + 1] / d : 0.0;
     cs[j] = c;
-    sn[j] = sgn;
+    sn[j] = sg;
     col[j] = d;
     col[j + 1] = 0.0;
-    gv[j + 1] = -sgn * gv[j];
+    gv[j + 1] = -sg * gv[j];
     gv[j] = c * gv[j];
+    const double resid = fabs(gv[j + 1]);
     K[L.scal() + SC_INV] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    K[L.scal() + SC_RESID] = fabs(gv[j + 1]);
+    K[L.scal() + SC_RESID] = resid;
+    const int jn = j + 1;
+    di[DI_J] = jn;
+    di[DI_IT] += 1;
+    const bool conv = !(resid > K[L.scal() + SC_TOL]);   // also stops on NaN
+    if (conv) di[DI_CONV] = 1;
+    if (conv || jn >= L.m || di[DI_IT] >= di[DI_MAXIT] || nrm == 0.0) di[DI_STOP] = 1;
 }
 
-__global__ void k_scale(double* __restrict__ w, int ns, const double* __restrict__ sc) {
+// V_j *= 1 / ||V_j|| (j already advanced by the tail)
+__global__ void k_scale(const int* __restrict__ di, double* __restrict__ V, long ld, int ns, const double* __restrict__ sc) {
+    if (di[DI_STOP]) return;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < ns) w[e] *= *sc;
+    if (e < ns) V[(long)di[DI_J] * ld + e] *= *sc;
 }
 
+// V_0 = r / ||r||, g = (beta, 0, ...), j = 0, stop unless there is work left
 __global__ void k_start_cycle(int ns, const double* __restrict__ r, double* __restrict__ v0, KLayout L, double* __restrict__ K,
-                              int nparts, const double* __restrict__ partial) {
-    // every block recomputes beta from the partials (cheap, keeps this a single launch)
+                              int nparts, const double* __restrict__ partial, int* __restrict__ di) {
     double s = 0.0;
     for (int b = 0; b < nparts; ++b) s += partial[b];
     const double beta = sqrt(s);
@@ -459,27 +529,38 @@ __global__ void k_start_cycle(int ns, const double* __restrict__ r, double* __re
         gv[0] = beta;
         for (int i = 1; i <= L.m; ++i) gv[i] = 0.0;
         K[L.scal() + SC_BETA] = beta;
+        K[L.scal() + SC_RESID] = beta;
+        di[DI_J] = 0;
+        di[DI_STOP] = (di[DI_IT] >= di[DI_MAXIT]) ? 1 : 0;
+        if (!(beta > K[L.scal() + SC_TOL])) { di[DI_CONV] = 1; di[DI_STOP] = 1; }
     }
 }
 
-__global__ void k_backsolve(int k, KLayout L, double* __restrict__ K) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// y = H^{-1} g over the first k = j columns (one warp)
+__global__ void k_backsolve(const int* __restrict__ di, KLayout L, double* __restrict__ K) {
+    const int lane = threadIdx.x;
+    const int k = di[DI_J];
     const double* H = K + L.H();
     const int ldh = L.m + 1;
     const double* gv = K + L.gv();
     double* y = K + L.y();
     for (int i = k - 1; i >= 0; --i) {
-        double s = gv[i];
-        for (int l = i + 1; l < k; ++l) s -= H[(long)l * ldh + i] * y[l];
-        const double d = H[(long)i * ldh + i];
-        y[i] = d != 0.0 ? s / d : 0.0;
+        double s = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) s += H[(long)l * ldh + i] * y[l];
+        s = warp_sum(s);
+        if (lane == 0) {
+            const double d = H[(long)i * ldh + i];
+            y[i] = d != 0.0 ? (gv[i] - s) / d : 0.0;
+        }
+        __syncwarp();
     }
 }
 
-__global__ void k_xupdate(int k, const double* __restrict__ V, long ld, const double* __restrict__ y, int ns,
-                          double* __restrict__ x) {
+__global__ void k_xupdate(const int* __restrict__ di, const double* __restrict__ V, long ld, const double* __restrict__ y,
+                          int ns, double* __restrict__ x) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ns) return;
+    const int k = di[DI_J];
     double s = 0.0;
     for (int i = 0; i < k; ++i) s += y[i] * V[(long)i * ld + e];
     x[e] += s;
@@ -491,7 +572,27 @@ __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b,
     if (e < n) out[e] = a * x[e] + b * y[e];
 }
 
+__global__ void k_set_int(int* __restrict__ p, int v) { *p = v; }
+
+__global__ void k_gmres_init(int* __restrict__ di, int maxit, double* __restrict__ K, KLayout L, const double* __restrict__ b2,
+                             double tol) {
+    di[DI_J] = 0;
+    di[DI_STOP] = 0;
+    di[DI_IT] = 0;
+    di[DI_MAXIT] = maxit;
+    di[DI_CONV] = 0;
+    di[DI_TMPJ] = 0;
+    K[L.scal() + SC_TOL] = tol * sqrt(*b2);
+}
+
 // ------------------------------------------------------------------------- solver
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    int prec = -1, m = 0;
+    cudaStream_t stream = nullptr;
+    int nodes = 0;
+};
+
 struct Solver {
     iim_geometry g;
     cudaStream_t s;
@@ -504,62 +605,120 @@ struct Solver {
     int ns;
     int m;
     KLayout L;
-    double fnorm2 = 0.0;
     int iters = 0;
     double last_gmres_rel = 0.0;
+    bool use_graph = true;
     static constexpr int kResBlocks = 1024;
     static constexpr int kNormBlocks = 64;
+    static constexpr int kBatch = 6;   // graph replays between host convergence checks
+
+    int* di() const { return g->d_int; }
 
     // ---- residual of the un-reduced system; fills g->res, small[], bvec circulation rows
     iim_status residual(double* res2_out, double* circ_err_out) {
-        const long n = (long)g->NX * g->NY;
         const double ih2 = 1.0 / (g->h * g->h);
         if (g->nminus > 0) {
-            k_ghost<<<(g->nminus + 255) / 256, 256, 0, s>>>(g->nminus, g->minus_node, g->gh_ptr, g->gh_idx, g->gh_w, psi_b,
-                                                             psibar, g->cp_body, g->psi_ext);
+            launch("ghost_f64", 0.0, 0.0, k_ghost, (g->nminus + 255) / 256, 256, 0, s, g->nminus, g->minus_node, g->gh_ptr,
+                   g->gh_idx, g->gh_w, psi_b, psibar, g->cp_body, g->psi_ext);
             IIM_LAUNCHED();
         }
-        k_residual<256><<<kResBlocks, 256, 0, s>>>(g->NX, g->NY, ih2, g->psi_ext, omega, g->node_class, ring, g->res,
-                                                   g->partial);
+        launch("residual_f64", 25.0 * (double)g->NX * g->NY, 8.0 * (double)g->NX * g->NY, k_residual<256>, kResBlocks,
+               256, 0, s, g->NX, g->NY, ih2, g->psi_ext, omega, g->node_class, ring, g->res, g->partial);
         IIM_LAUNCHED();
         double* small = g->small;
-        int* circ_ids_d = g->d_int + 32;   // circulation body ids (filled at solve start)
+        const int* circ_ids_d = g->d_int + DI_CIRC;
         if (g->ncirc > 0) {
-            k_circ_measure<256><<<g->ncirc, 256, 0, s>>>(g->NX, g->psi_ext, g->d_regions, circ_ids_d, small + SM_CIRC);
-            k_region_sums<256><<<dim3(g->ncirc, kRegionParts), 256, 0, s>>>(g->NX, g->res, g->d_regions, circ_ids_d,
-                                                                            small + SM_REG);
+            launch("circ_measure", 0.0, 0.0, k_circ_measure<256>, g->ncirc, 256, 0, s, g->nx, g->psi_ext, g->d_regions,
+                   circ_ids_d, small + SM_CIRC);
+            launch("region_sums", 0.0, 0.0, k_region_sums<256>, dim3(g->ncirc, kRegionParts), 256, 0, s, g->nx, g->res,
+                   g->d_regions, circ_ids_d, small + SM_REG);
             IIM_LAUNCHED();
         }
-        k_finish_residual<<<1, 32, 0, s>>>(kResBlocks, g->partial, g->ncirc, circ_ids_d, gamma, ih2, small,
-                                           small + SM_REG, g->bvec ? g->bvec + g->na : nullptr);
+        launch("finish_residual", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kResBlocks, g->partial, g->ncirc,
+               circ_ids_d, gamma, ih2, small, small + SM_REG, g->bvec ? g->bvec + g->na : nullptr, small + SM_RES2);
         IIM_LAUNCHED();
         IIM_TRY(cudaMemcpyAsync(g->h_pinned, small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         IIM_TRY(cudaStreamSynchronize(s));
-        (void)n;
         *res2_out = g->h_pinned[SM_RES2];
         *circ_err_out = g->h_pinned[SM_CIRC_ERR];
         return IIM_OK;
     }
 
-    // ---- Schur operator application vout = S_aug vin (precision T for the box solves)
+    // ---- Schur operator application V_{jd+1} = S_aug V_jd, jd = di[jslot] (device)
     template <typename T>
-    iim_status apply(const double* vin, double* vout) {
+    iim_status apply_at(int jslot, const int* stop) {
         Plan<T> p = make_plan<T>(g);
         T* tb = (T*)g->tbuf;
         T* pt = (T*)g->psiT;
+        const long ld = ns;
+        const VecArg vj{g->V, di() + jslot, 0, ld};
         if (g->na > 0) {
-            IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, nullptr, 0.0, g->aff_row_ptr, g->aff_node, vin,
-                                  1.0, tb, s));
-            IIM_CHECK(cols<T>(p, g->ja0, g->ja1, g->jo0, g->jo1, tb, s));
-            IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, nullptr, s)));
-            k_gather<T><<<(g->na + 127) / 128, 128, 0, s>>>(g->na, g->gop_ptr, g->gop_idx, g->gop_w, pt, g->cp_body,
-                                                             g->body_circ, vin + g->na, vin, vout);
-            IIM_LAUNCHED();
+            IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, 0, 0, nullptr, 0.0, g->aff_row_ptr,
+                                  g->aff_node, vj, 1.0, tb, stop, s));
+            IIM_CHECK(cols<T>(p, g->ja0, g->ja1, g->jo0, g->jo1, tb, stop, s));
+            IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, stop, s)));
         }
-        if (g->ncirc > 0) {
-            k_circ_rows<256><<<g->ncirc, 256, 0, s>>>(g->na, g->aff_body, g->body_circ, vin, vout + g->na);
-            IIM_LAUNCHED();
+        const int nga = (g->na + 127) / 128;
+        launch("gather", 0.0, 0.0, k_gather<T, 128>, nga + g->ncirc, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx,
+               g->gop_w, pt, g->cp_body, g->body_circ, g->aff_body, vj, 1, g->V, di() + jslot, ld, stop);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
+
+    // ---- one Arnoldi step after the operator application
+    iim_status ortho_iter() {
+        const long ld = ns;
+        double* K = g->H;
+        const int eb = (ns + 255) / 256;
+        launch("gmres_dots", 0.0, 0.0, k_dots<256>, m, 256, 0, s, di(), g->V, ld, ns, K + L.hc1());
+        launch("gmres_update", 0.0, 0.0, k_update<256>, eb, 256, 0, s, di(), g->V, ld, K + L.hc1(), ns, nullptr);
+        launch("gmres_dots", 0.0, 0.0, k_dots<256>, m, 256, 0, s, di(), g->V, ld, ns, K + L.hc2());
+        launch("gmres_update", 0.0, 0.0, k_update<256>, eb, 256, 0, s, di(), g->V, ld, K + L.hc2(), ns, g->partial);
+        launch("gmres_tail", 0.0, 0.0, k_arnoldi_tail, 1, 32, 0, s, di(), L, eb, g->partial, K);
+        launch("gmres_scale", 0.0, 0.0, k_scale, eb, 256, 0, s, di(), g->V, ld, ns, K + L.scal() + SC_INV);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
+
+    template <typename T>
+    iim_status iteration() {
+        IIM_CHECK(apply_at<T>(DI_J, di() + DI_STOP));
+        return ortho_iter();
+    }
+
+    template <typename T>
+    iim_status ensure_graph(IterGraph& G) {
+        if (G.exec && G.prec == (int)sizeof(T) && G.m == m) return IIM_OK;
+        if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+        // capture on the geometry's private stream (the caller's may be the legacy stream,
+        // which cannot be captured); the graph is then launched on the caller's stream
+        cudaGraph_t graph = nullptr;
+        const cudaStream_t user = s;
+        IIM_TRY(cudaStreamSynchronize(user));
+        s = g->cap_stream;
+        set_capture(true);
+        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            set_capture(false);
+            s = user;
+            record_cuda_error(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+            return IIM_ERR_CUDA;
         }
+        iim_status st = iteration<T>();
+        e = cudaStreamEndCapture(s, &graph);
+        set_capture(false);
+        s = user;
+        if (st != IIM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+        if (e != cudaSuccess) { record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return IIM_ERR_CUDA; }
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) { G.exec = nullptr; record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); return IIM_ERR_CUDA; }
+        G.prec = (int)sizeof(T);
+        G.m = m;
+        G.stream = s;
+        G.nodes = (int)nn;
         return IIM_OK;
     }
 
@@ -570,11 +729,12 @@ struct Solver {
         T* tb = (T*)g->tbuf;
         T* pt = (T*)g->psiT;
         if (g->na == 0) return IIM_OK;
-        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, nullptr, 0.0, nullptr, nullptr, nullptr, 0.0, tb, s));
-        IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->jo0, g->jo1, tb, s));
-        IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, nullptr, s)));
-        k_gather<T><<<(g->na + 127) / 128, 128, 0, s>>>(g->na, g->gop_ptr, g->gop_idx, g->gop_w, pt, g->cp_body,
-                                                         g->body_circ, nullptr, nullptr, g->bvec);
+        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, g->nx, 1, nullptr, 0.0, nullptr, nullptr, kNoVec, 0.0, tb, nullptr, s));
+        IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->jo0, g->jo1, tb, nullptr, s));
+        IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
+        const int nga = (g->na + 127) / 128;
+        launch("gather", 0.0, 0.0, k_gather<T, 128>, nga, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx, g->gop_w, pt,
+               g->cp_body, g->body_circ, g->aff_body, kNoVec, 0, g->bvec, nullptr, 0L, nullptr);
         IIM_LAUNCHED();
         return IIM_OK;
     }
@@ -584,96 +744,104 @@ struct Solver {
     iim_status recover(const double* x) {
         Plan<T> p = make_plan<T>(g);
         T* tb = (T*)g->tbuf;
-        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, nullptr, 0.0, g->aff_row_ptr, g->aff_node, g->na ? x : nullptr, -1.0,
-                              tb, s));
-        IIM_CHECK(cols<T>(p, 0, g->NY - 1, 0, g->NY - 1, tb, s));
-        IIM_CHECK((rows_inv<T, INV_ACCUM_FLUID>(p, 0, g->NY, tb, nullptr, g->psi_ext, g->node_class, s)));
+        const VecArg xg{g->na ? x : nullptr, nullptr, 0, 0};
+        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, g->nx, 1, nullptr, 0.0, g->aff_row_ptr, g->aff_node, xg, -1.0, tb,
+                              nullptr, s));
+        IIM_CHECK(cols<T>(p, 0, g->NY - 1, 0, g->NY - 1, tb, nullptr, s));
+        IIM_CHECK((rows_inv<T, INV_ACCUM_FLUID>(p, 0, g->NY, tb, nullptr, g->psi_ext, 0, 0, g->node_class, nullptr, s)));
         if (g->ncirc > 0) {
-            k_add_psibar<<<1, 64, 0, s>>>(g->ncirc, g->d_int + 32, x + g->na, psibar);
+            launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, g->ncirc, di() + DI_CIRC, x + g->na, psibar);
             IIM_LAUNCHED();
         }
         return IIM_OK;
     }
 
-    iim_status norm2(const double* v, int n, double* out) {
-        k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(v, n, g->partial);
-        IIM_LAUNCHED();
-        k_finish_residual<<<1, 32, 0, s>>>(kNormBlocks, g->partial, 0, nullptr, nullptr, 0.0, g->small + SM_NORM, nullptr,
-                                           nullptr);
-        IIM_LAUNCHED();
-        IIM_TRY(cudaMemcpyAsync(g->h_pinned + 8, g->small + SM_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
+    iim_status read_state(int* out8) {
+        IIM_TRY(cudaMemcpyAsync(g->h_pinned + 16, di(), 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         IIM_TRY(cudaStreamSynchronize(s));
-        *out = g->h_pinned[8];
+        std::memcpy(out8, g->h_pinned + 16, 8 * sizeof(int));
         return IIM_OK;
     }
 
-    // ---- restarted GMRES on S_aug x = b, x0 = 0; returns relative residual estimate
+    // ---- restarted GMRES on S_aug x = b, x0 = 0
     template <typename T>
-    iim_status gmres(double tol, int max_it, double* rel_out) {
+    iim_status gmres(double tol, int max_it) {
         const int ns_ = ns;
         double* V = g->V;
         double* K = g->H;
         double* x = g->xsol;
         const long ld = ns_;
         const int eb = (ns_ + 255) / 256;
-        IIM_TRY(cudaMemsetAsync(x, 0, ns_ * sizeof(double), s));
-        double b2 = 0.0;
-        IIM_CHECK(norm2(g->bvec, ns_, &b2));
-        if (!std::isfinite(b2)) return IIM_ERR_NONFINITE;
-        const double bnorm = std::sqrt(b2);
-        *rel_out = 0.0;
-        if (bnorm == 0.0) return IIM_OK;
-        // r0 = b (x0 = 0)
-        k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(g->bvec, ns_, g->partial);
-        k_start_cycle<<<eb, 256, 0, s>>>(ns_, g->bvec, V, L, K, kNormBlocks, g->partial);
+        IIM_TRY(cudaMemsetAsync(x, 0, (size_t)ns_ * sizeof(double), s));
+        launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
+        launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0, nullptr,
+               nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
+        launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), max_it, K, L, g->small + SM_NORM, tol);
+        // V_0 = b / ||b|| (x0 = 0)
+        launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns_, g->bvec, V, L, K, kNormBlocks, g->partial, di());
         IIM_LAUNCHED();
-        int it_local = 0;
-        double resid = bnorm;
-        while (true) {
-            int k = 0;
-            for (int j = 0; j < m; ++j) {
-                double* vj = V + (long)j * ld;
-                double* w = V + (long)(j + 1) * ld;
-                IIM_CHECK(apply<T>(vj, w));
-                k_dots<256><<<j + 1, 256, 0, s>>>(j, V, ld, w, ns_, K + L.hc1());
-                k_update<<<eb, 256, 0, s>>>(j, V, ld, K + L.hc1(), ns_, w);
-                k_dots<256><<<j + 1, 256, 0, s>>>(j, V, ld, w, ns_, K + L.hc2());
-                k_update<<<eb, 256, 0, s>>>(j, V, ld, K + L.hc2(), ns_, w);
-                k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(w, ns_, g->partial);
-                k_arnoldi_tail<<<1, 32, 0, s>>>(j, L, kNormBlocks, g->partial, K);
-                k_scale<<<eb, 256, 0, s>>>(w, ns_, K + L.scal() + SC_INV);
-                IIM_LAUNCHED();
-                IIM_TRY(cudaMemcpyAsync(g->h_pinned + 9, K + L.scal() + SC_RESID, sizeof(double), cudaMemcpyDeviceToHost, s));
-                IIM_TRY(cudaStreamSynchronize(s));
-                resid = g->h_pinned[9];
-                ++it_local;
-                ++iters;
-                k = j + 1;
-                if (!std::isfinite(resid)) return IIM_ERR_NONFINITE;
-                if (resid <= tol * bnorm || it_local >= max_it) break;
+        IterGraph* G = nullptr;
+        if (use_graph && !profiling_active()) {
+            G = (IterGraph*)(sizeof(T) == 8 ? g->graph64 : g->graph32);
+            if (!G) {
+                G = new IterGraph();
+                if (sizeof(T) == 8) g->graph64 = G; else g->graph32 = G;
             }
-            k_backsolve<<<1, 32, 0, s>>>(k, L, K);
-            k_xupdate<<<eb, 256, 0, s>>>(k, V, ld, K + L.y(), ns_, x);
-            IIM_LAUNCHED();
-            if (resid <= tol * bnorm || it_local >= max_it) break;
-            // restart: r = b - S x into V_0
-            double* tmp = V + ld;
-            IIM_CHECK(apply<T>(x, tmp));
-            k_axpby<<<eb, 256, 0, s>>>(ns_, 1.0, g->bvec, -1.0, tmp, tmp);
-            k_sumsq<256><<<kNormBlocks, 256, 0, s>>>(tmp, ns_, g->partial);
-            k_start_cycle<<<eb, 256, 0, s>>>(ns_, tmp, V, L, K, kNormBlocks, g->partial);
-            IIM_LAUNCHED();
+            IIM_CHECK(ensure_graph<T>(*G));
         }
-        *rel_out = resid / bnorm;
-        last_gmres_rel = *rel_out;
+        int st[8] = {0};
+        IIM_CHECK(read_state(st));
+        while (!st[DI_STOP] || !st[DI_CONV]) {
+            // one cycle: iterate until the device stop flag is set
+            while (!st[DI_STOP]) {
+                if (G) {
+                    for (int b = 0; b < kBatch; ++b) {
+                        IIM_TRY(cudaGraphLaunch(G->exec, s));
+                        count_launches(G->nodes);
+                    }
+                } else {
+                    IIM_CHECK(iteration<T>());
+                }
+                IIM_CHECK(read_state(st));
+            }
+            launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
+            launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, x);
+            IIM_LAUNCHED();
+            if (st[DI_CONV] || st[DI_IT] >= max_it) break;
+            // restart: V_1 = x, V_2 = S V_1, V_0 = (b - V_2) / ||b - V_2||
+            IIM_TRY(cudaMemcpyAsync(V + ld, x, (size_t)ns_ * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            IIM_CHECK(restart_residual<T>());
+            IIM_CHECK(read_state(st));
+        }
+        IIM_TRY(cudaMemcpyAsync(g->h_pinned + 12, K + L.scal(), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        iters += st[DI_IT];
+        const double bnorm = g->h_pinned[12 + SC_TOL] / std::max(tol, 1e-300);
+        last_gmres_rel = bnorm > 0.0 ? g->h_pinned[12 + SC_RESID] / bnorm : 0.0;
+        return IIM_OK;
+    }
+
+    // V_2 = S V_1 (V_1 holds x), then V_0 = (b - V_2) / ||b - V_2||
+    template <typename T>
+    iim_status restart_residual() {
+        const long ld = ns;
+        double* V = g->V;
+        double* K = g->H;
+        const int eb = (ns + 255) / 256;
+        launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 1);
+        IIM_CHECK(apply_at<T>(DI_TMPJ, nullptr));
+        launch("gmres_axpby", 0.0, 0.0, k_axpby, eb, 256, 0, s, ns, 1.0, g->bvec, -1.0, V + 2 * ld, V + 2 * ld);
+        launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, V + 2 * ld, ns, g->partial);
+        launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns, V + 2 * ld, V, L, K, kNormBlocks, g->partial,
+               di());
+        IIM_LAUNCHED();
         return IIM_OK;
     }
 
     template <typename T>
     iim_status correction(double tol, int max_it) {
-        double rel = 0.0;
         IIM_CHECK(rhs<T>());
-        IIM_CHECK(gmres<T>(tol, max_it, &rel));
+        IIM_CHECK(gmres<T>(tol, max_it));
         IIM_CHECK(recover<T>(g->xsol));
         return IIM_OK;
     }
@@ -690,7 +858,23 @@ static iim_status ensure_krylov(iim_geometry g, int m) {
     IIM_TRY(cudaMalloc(&g->xsol, sizeof(double) * (size_t)std::max(ns, 1)));
     IIM_TRY(cudaMalloc(&g->bvec, sizeof(double) * (size_t)std::max(ns, 1)));
     g->krylov_m = m;
+    // the captured iteration graphs refer to the old buffers
+    for (void** gp : {&g->graph64, &g->graph32}) {
+        IterGraph* G = (IterGraph*)*gp;
+        if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+    }
     return IIM_OK;
+}
+
+void destroy_graphs(iim_geometry g) {
+    for (void** gp : {&g->graph64, &g->graph32}) {
+        IterGraph* G = (IterGraph*)*gp;
+        if (G) {
+            if (G->exec) cudaGraphExecDestroy(G->exec);
+            delete G;
+            *gp = nullptr;
+        }
+    }
 }
 
 }  // namespace iim
@@ -701,7 +885,7 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
                                         const double* gamma, double* psibar, double* psi_out, double* ux_out,
                                         double* uy_out, const double* psi_guess, const iim_opts* opts_in,
                                         iim_stats* stats, iim_stream stream) {
-    iim_opts opts{IIM_FP64, 1e-10, 2000, 40, 8, 0, 0.0};
+    iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0};
     if (opts_in) opts = *opts_in;
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (!g || !omega || !psi_out || (g->ncp > 0 && !psi_b) || (g->nb > 0 && !psibar)) return IIM_ERR_INVALID_ARG;
@@ -713,30 +897,28 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
     if (g->ncirc > 0)
-        IIM_TRY(cudaMemcpyAsync(g->d_int + 32, g->circ_ids.data(), g->ncirc * sizeof(int), cudaMemcpyHostToDevice, s));
+        IIM_TRY(cudaMemcpyAsync(g->d_int + DI_CIRC, g->circ_ids.data(), g->ncirc * sizeof(int), cudaMemcpyHostToDevice, s));
     IIM_TRY(cudaEventRecord(g->ev0, s));
 
     Solver S;
     S.g = g; S.s = s; S.prec = opts.prec; S.omega = omega; S.psi_b = psi_b; S.ring = psi_box; S.gamma = gamma;
     S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
-    const long n = (long)g->NX * g->NY;
-    const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 2e-5);
+    const long npad = (long)g->nx * g->NY;
+    const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 1e-5);
 
     // ||f||: residual at psi = 0 (ghosts from the boundary data only)
     double res2 = 0.0, cerr = 0.0;
     int fallback = 0;
-    k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, g->node_class, g->psi_ext);
-    if (g->nb > 0) {
-        // fixed bodies keep their psibar, circulation bodies start from 0
-        k_init_psibar<<<1, 64, 0, s>>>(g->nb, g->body_circ, psibar, 0, psibar);
-    }
+    launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, nullptr,
+           g->node_class, g->psi_ext);
+    if (g->nb > 0) launch("init_psibar", 0.0, 0.0, k_init_psibar, 1, 64, 0, s, g->nb, g->body_circ, psibar, 0, psibar);
     IIM_LAUNCHED();
     IIM_CHECK(S.residual(&res2, &cerr));
     if (!std::isfinite(res2)) return IIM_ERR_NONFINITE;
-    S.fnorm2 = res2;
     const double fnorm = std::sqrt(res2);
     if (opts.guess == 1) {
-        k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, psi_guess, g->node_class, g->psi_ext);
+        launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, psi_guess,
+               g->node_class, g->psi_ext);
         IIM_LAUNCHED();
         double r2g = 0.0, cg = 0.0;
         IIM_CHECK(S.residual(&r2g, &cg));
@@ -746,7 +928,8 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         } else {
             // the guess raised the residual: start again from zero
             fallback = 1;
-            k_init_psi<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, nullptr, g->node_class, g->psi_ext);
+            launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, nullptr,
+                   g->node_class, g->psi_ext);
             IIM_LAUNCHED();
             IIM_CHECK(S.residual(&res2, &cerr));
         }
@@ -764,8 +947,10 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         if (!std::isfinite(res2)) { st = IIM_ERR_NONFINITE; break; }
         rel = std::sqrt(res2) / fnorm;
     }
-    k_velocity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g->NX, g->NY, 0.5 / g->h, g->psi_ext, g->node_class, psi_box,
-                                                          psi_out, ux_out, uy_out);
+    const long n = (long)g->NX * g->NY;
+    launch("velocity_f64", (double)n * (9.0 + 8.0 + (ux_out ? 8.0 : 0.0) + (uy_out ? 8.0 : 0.0)), 0.0, k_velocity,
+           (unsigned)((n + 255) / 256), 256, 0, s, g->NX, g->NY, 0.5 / g->h, g->psi_ext, g->node_class, psi_box, psi_out,
+           ux_out, uy_out);
     IIM_LAUNCHED();
     IIM_TRY(cudaEventRecord(g->ev1, s));
     IIM_TRY(cudaEventSynchronize(g->ev1));
@@ -794,9 +979,9 @@ extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, con
     IIM_CHECK(ensure_twiddles());
     cudaStream_t s = (cudaStream_t)stream;
     const int NX = nx - 1, NY = ny - 1;
-    // work: transform buffer (NX*NY) followed by the eigenvalue tables (NX + NY)
+    // work: padded transform buffer (nx*NY) followed by the eigenvalue tables (NX + NY)
     double* buf = work;
-    double* lam = work + (size_t)NX * NY;   // NX + NY doubles (FP64) or floats
+    double* lam = work + (size_t)nx * NY;
     std::vector<double> lx(NX + NY);
     for (int k = 0; k < NX; ++k) lx[k] = (2.0 - 2.0 * std::cos(M_PI * (k + 1) / nx)) / (h * h);
     for (int k = 0; k < NY; ++k) lx[NX + k] = (2.0 - 2.0 * std::cos(M_PI * (k + 1) / ny)) / (h * h);
@@ -804,9 +989,9 @@ extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, con
     if (prec == IIM_FP64) {
         IIM_TRY(cudaMemcpyAsync(lam, lx.data(), sizeof(double) * (NX + NY), cudaMemcpyHostToDevice, s));
         Plan<double> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lam, lam + NX, twiddles64(), (2.0 / nx) * (2.0 / ny)};
-        IIM_CHECK(rows_fwd<double>(p, 0, NY, f, psi_box, ih2, nullptr, nullptr, nullptr, 0.0, buf, s));
-        IIM_CHECK(cols<double>(p, 0, NY - 1, 0, NY - 1, buf, s));
-        IIM_CHECK((rows_inv<double, INV_STORE_F64>(p, 0, NY, buf, nullptr, u, nullptr, s)));
+        IIM_CHECK(rows_fwd<double>(p, 0, NY, f, NX, 0, psi_box, ih2, nullptr, nullptr, kNoVec, 0.0, buf, nullptr, s));
+        IIM_CHECK(cols<double>(p, 0, NY - 1, 0, NY - 1, buf, nullptr, s));
+        IIM_CHECK((rows_inv<double, INV_STORE_F64>(p, 0, NY, buf, nullptr, u, NX, 0, nullptr, nullptr, s)));
     } else {
         std::vector<float> fl(NX + NY);
         for (int k = 0; k < NX + NY; ++k) fl[k] = (float)lx[k];
@@ -814,9 +999,9 @@ extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, con
         IIM_TRY(cudaMemcpyAsync(lamf, fl.data(), sizeof(float) * (NX + NY), cudaMemcpyHostToDevice, s));
         Plan<float> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lamf, lamf + NX, twiddles32(), (float)((2.0 / nx) * (2.0 / ny))};
         float* fb = (float*)buf;
-        IIM_CHECK(rows_fwd<float>(p, 0, NY, f, psi_box, ih2, nullptr, nullptr, nullptr, 0.0, fb, s));
-        IIM_CHECK(cols<float>(p, 0, NY - 1, 0, NY - 1, fb, s));
-        IIM_CHECK((rows_inv<float, INV_STORE_F64>(p, 0, NY, fb, nullptr, u, nullptr, s)));
+        IIM_CHECK(rows_fwd<float>(p, 0, NY, f, NX, 0, psi_box, ih2, nullptr, nullptr, kNoVec, 0.0, fb, nullptr, s));
+        IIM_CHECK(cols<float>(p, 0, NY - 1, 0, NY - 1, fb, nullptr, s));
+        IIM_CHECK((rows_inv<float, INV_STORE_F64>(p, 0, NY, fb, nullptr, u, NX, 0, nullptr, nullptr, s)));
     }
     // pageable-memory copies are staged before cudaMemcpyAsync returns, so the host vectors
     // may go out of scope here

@@ -27,7 +27,7 @@ def psi_b_for(P, geo):
     return P.psi_b_fn(cp["x"].cpu().numpy(), cp["y"].cpu().numpy(), cp["body"].cpu().numpy())
 
 
-def solve(P, geo, gamma=None, psibar=None, prec=iim.IIM_FP64, rtol=1e-12, velocity=False, guess=None, restart=40,
+def solve(P, geo, gamma=None, psibar=None, prec=iim.IIM_FP64, rtol=1e-12, velocity=False, guess=None, restart=64,
           max_iter=3000, inner_rtol=0.0, check=True, omega=None):
     g = P.grid
     NXY = (g.nx - 1) * (g.ny - 1)
