@@ -278,3 +278,19 @@ def ellipses_problem(n: int, seed: int) -> Problem:
                    omega=_mask_interior(g, phi, w_nodes), psi_box=np.zeros(2 * (g.nx + g.ny)),
                    psi_b_fn=lambda x, y, body: np.zeros_like(x), psibar=np.zeros(nb), gamma=None,
                    exact=None, name=f"ellipses_{n}_s{seed}")
+
+
+def c2_cylinder_flow(nx: int = 1024, ny: int = 512, seed: int = 0) -> Problem:
+    """Flow past one cylinder (R = 0.5 at (-1, 0)) on [-2,6]x[-2,2], uniform inflow U = 1,
+    Re = U D / nu = 200 (nu = 0.005): initial vorticity of the potential flow (zero) plus
+    seeded Gaussian noise of amplitude 1e-3 at every fluid node; box streamfunction U y."""
+    h = 8.0 / nx
+    g = Grid(-2.0, 6.0, -2.0, -2.0 + h * ny, nx, ny)
+    X, Y = g.nodes()
+    phi = phi_circle(X, Y, -1.0, 0.0, 0.5)
+    rng = np.random.default_rng(seed)
+    noise = 1e-3 * rng.normal(size=(ny + 1, nx + 1))
+    omega = _mask_interior(g, phi, noise)
+    return Problem(grid=g, phi=phi, regions=[region_around(g, phi)], modes=[1], omega=omega,
+                   psi_box=box_ring(g, 1.0 * Y), psi_b_fn=lambda x, y, body: np.zeros_like(x),
+                   psibar=np.zeros(1), gamma=None, exact=None, name=f"c2_cylinder_flow_{nx}x{ny}")
