@@ -151,6 +151,49 @@ iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* 
 iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box,
                            double* u, int prec, double* work, iim_stream stream);
 
+/* Conservative vorticity transport right-hand side with the IIM boundary treatment (Sec. 3:
+ * Eqs. upwind, 2dshuconserve, Sec. 3.2) and the Kelvin ODE (Sec. 5.1, Eq. discreteKelvinChoice)
+ * for a given velocity; omega_b from the velocity by the local vorticity boundary condition of
+ * Sec. 5.3 (its stencil figure is missing from the paper; the library's reading is a
+ * three-node quadratic along the grid line and a one-sided second-order difference across it
+ * that uses u_b).
+ *   omega, ux, uy  interior arrays (values at solid nodes ignored)
+ *   u_b            2 |C| values: u_x at the control points, then u_y (NULL: no-slip, zero)
+ *   Uinf           host, 2 values: velocity at and beyond the box
+ *   nu             viscosity (>= 0)
+ *   omega_b_in     |C| values of a prescribed wall vorticity, or NULL to derive omega_b from
+ *                  the velocity (Sec. 5.3)
+ *   omega_b_out    |C| values or NULL (the omega_b used)
+ *   rhs_out        interior array: d omega / dt (0 in the solid)
+ *   dgamma_out     n_bodies values: -h sum_{dR_k}(f + q).n, or NULL
+ * Box: vorticity 0 at and beyond the box except the right edge (outflow), which copies the
+ * last interior column.  Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA.  Asynchronous. */
+iim_status iim_transport_rhs(iim_geometry g, const double* omega, const double* ux, const double* uy,
+                             const double* u_b, const double Uinf[2], double nu, const double* omega_b_in,
+                             double* omega_b_out, double* rhs_out, double* dgamma_out, iim_stream stream);
+
+/* One time step of the full algorithm (Sec. 5.5): three stages of the low-storage RK3 of
+ * Williamson (1980) (A = 0, -5/9, -153/128; B = 1/3, 15/16, 8/15) on (omega, Gamma_k); each stage
+ * reconstructs psi and u with iim_poisson_solve (Gamma as given), evaluates omega_b, the
+ * transport right-hand side and the Kelvin ODE, then updates.
+ *   omega          interior array, in/out (kept 0 in the solid)
+ *   gamma          n_bodies, in/out (device)
+ *   psibar         n_bodies, in/out (device): fixed values / last solved values
+ *   u_b            2 |C| values (u_x then u_y) or NULL (no-slip)
+ *   psi_b          |C| values or NULL (zero)
+ *   psi_box        box ring or NULL (zero)
+ *   Uinf, nu       as in iim_transport_rhs
+ *   c_stab, dt_inout  host: if *dt_inout <= 0 the step is c_stab times the stable step of the
+ *                  RK3 polygon (App. B): 1/dt_max = max(|u_x|+|u_y|)/(1.620 h) + nu/(0.314 h^2),
+ *                  from the velocity of the first stage; the step used is written back
+ *   opts           Poisson solve options (NULL: defaults of iim_poisson_solve)
+ *   per_stage      host, 3 entries or NULL
+ * Errors: those of iim_poisson_solve, IIM_ERR_INVALID_ARG.  Synchronizes `stream`. */
+iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma, double* psibar, const double* u_b,
+                        const double* psi_b, const double* psi_box, const double Uinf[2], double nu,
+                        double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
+                        iim_stream stream);
+
 /* Number of kernels the library has launched in this process (all threads, all devices);
  * monotonic.  Lets a caller count the launches inside a timed region. */
 long long iim_launch_count(void);

@@ -60,6 +60,9 @@ SIGNATURES = [
     ("iim_poisson_solve", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
                                ctypes.POINTER(iim_stats), _vp]),
     ("iim_box_poisson", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp, _vp]),
+    ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
+    ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
+                          ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
     ("iim_last_error_message", ctypes.c_char_p, []),
     ("iim_launch_count", ctypes.c_longlong, []),
     ("iim_profile_begin", _i, []),
@@ -249,3 +252,35 @@ def iim_profile_end(capacity: int = 128):
     n = load().iim_profile_end(buf, capacity)
     return [{"name": buf[k].name.decode(), "launches": buf[k].launches, "ms": buf[k].ms, "bytes": buf[k].bytes,
              "flops": buf[k].flops} for k in range(min(n, capacity))]
+
+
+def iim_transport_rhs(g: Geometry, omega, ux, uy, u_b, Uinf, nu, rhs_out, omega_b_in=None, omega_b_out=None,
+                      dgamma_out=None, stream=None):
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
+    st = load().iim_transport_rhs(g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(ux, f64, NXY, "ux"),
+                                  _ptr(uy, f64, NXY, "uy"), _ptr(u_b, f64, 2 * g.n_control, "u_b"), U, float(nu),
+                                  _ptr(omega_b_in, f64, g.n_control, "omega_b_in"),
+                                  _ptr(omega_b_out, f64, g.n_control, "omega_b_out"), _ptr(rhs_out, f64, NXY, "rhs_out"),
+                                  _ptr(dgamma_out, f64, g.n_bodies, "dgamma_out"), _stream(stream))
+    _check(st, "iim_transport_rhs")
+
+
+def iim_rk3_step(g: Geometry, omega, gamma, psibar, u_b, psi_b, psi_box, Uinf, nu, c_stab, dt=0.0,
+                 opts: iim_opts | None = None, stream=None, check=True):
+    """One RK3 step in place on omega, gamma, psibar; returns (dt used, [stats per stage])."""
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
+    dtc = _d(float(dt))
+    stats = (iim_stats * 3)()
+    o = opts if opts is not None else default_opts()
+    st = load().iim_rk3_step(g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(gamma, f64, g.n_bodies, "gamma"),
+                             _ptr(psibar, f64, g.n_bodies, "psibar"), _ptr(u_b, f64, 2 * g.n_control, "u_b"),
+                             _ptr(psi_b, f64, g.n_control, "psi_b"),
+                             _ptr(psi_box, f64, 2 * (g.grid.nx + g.grid.ny), "psi_box"), U, float(nu), float(c_stab),
+                             ctypes.byref(dtc), ctypes.byref(o), stats, _stream(stream))
+    if check:
+        _check(st, "iim_rk3_step")
+    return dtc.value, [stats[k].as_dict() for k in range(3)], st

@@ -124,7 +124,11 @@ struct iim_geometry_s {
     // fourth-order ghost values at A- nodes (velocity, residual)
     int *minus_node = nullptr, *gh_ptr = nullptr, *gh_idx = nullptr;
     double* gh_w = nullptr;
-    uint8_t* node_class = nullptr;       // NY*NX
+    int* minus_cp = nullptr;             // 4 per A- node: control point per direction or -1
+    uint8_t* minus_mask = nullptr;       // per A- node: bit d fourth-order usable, bit 4+d third-order
+    int* minus_map = nullptr;            // padded node -> A- index or -1
+    double* tr_buf = nullptr;            // transport workspace (allocated on first use)
+    uint8_t* node_class = nullptr;       // padded layout
     int* body_circ = nullptr;            // per body: index among circulation bodies or -1
     iim_region* d_regions = nullptr;
     // eigenvalues of the 1D three-point operators, x modes (NX) and y modes (NY)

@@ -258,7 +258,8 @@ __global__ void k_fill(int nx, int ny, double h, const double* __restrict__ phi,
                        const int* __restrict__ gop_off, const int* __restrict__ gh_off,
                        const int* __restrict__ edge_pos, const double* __restrict__ tval, int nb,
                        const iim_region* __restrict__ R, int* aff_node, int* aff_body, uint8_t* aff_solid,
-                       int* gop_idx, double* gop_w, int* minus_node, int* gh_idx, double* gh_w, int* err) {
+                       int* gop_idx, double* gop_w, int* minus_node, int* gh_idx, double* gh_w, int* minus_cp,
+                       uint8_t* minus_mask, int* minus_map, int* err) {
     const int NX = nx - 1, NY = ny - 1;
     const long node = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= (long)NX * NY) return;
@@ -286,6 +287,22 @@ __global__ void k_fill(int nx, int ny, double h, const double* __restrict__ phi,
         }
         const int m = minus_pos[node];
         minus_node[m] = (int)pnode;
+        minus_map[pnode] = m;
+        // per direction: control point index (or -1) and validity of the fourth-order (bit d)
+        // and third-order (bit 4 + d) extrapolations
+        uint8_t mask = (uint8_t)usable_dirs(phi, nx, ny, gi, gj, nullptr);
+        for (int d = 0; d < 4; ++d) {
+            const int qi = gi + c_dir_i[d], qj = gj + c_dir_j[d];
+            if (solid_at(phi, W, qi, qj)) { minus_cp[4 * m + d] = -1; continue; }
+            minus_cp[4 * m + d] = edge_pos[edge_index(nx, ny, gi, gj, d)];
+            bool ok3 = true;
+            for (int k = 2; k <= 3; ++k) {
+                const int ri = gi + k * c_dir_i[d], rj = gj + k * c_dir_j[d];
+                if (ri < 1 || ri > nx - 1 || rj < 1 || rj > ny - 1 || solid_at(phi, W, ri, rj)) ok3 = false;
+            }
+            if (ok3) mask |= (uint8_t)(16 << d);
+        }
+        minus_mask[m] = mask;
         emit_ghost(nx, ny, phi, edge_pos, tval, gi, gj, 1.0, gh_idx + gh_off[node], gh_w + gh_off[node]);
     } else {
         // gamma_p = -(1/h^2) sum of the ghost values of the solid neighbours
@@ -490,10 +507,13 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
     SETUP_TRY(dalloc(&g->gop_ptr, na + 1)); SETUP_TRY(dalloc(&g->gop_idx, gop_total)); SETUP_TRY(dalloc(&g->gop_w, gop_total));
     SETUP_TRY(dalloc(&g->minus_node, nm)); SETUP_TRY(dalloc(&g->gh_ptr, nm + 1));
     SETUP_TRY(dalloc(&g->gh_idx, gh_total)); SETUP_TRY(dalloc(&g->gh_w, gh_total));
+    SETUP_TRY(dalloc(&g->minus_cp, 4 * (size_t)nm)); SETUP_TRY(dalloc(&g->minus_mask, nm));
+    SETUP_TRY(dalloc(&g->minus_map, npad));
+    SETUP_CUDA(cudaMemsetAsync(g->minus_map, 0xff, npad * sizeof(int), s));
     k_fill<<<(unsigned)((nnode + 255) / 256), 256, 0, s>>>(nx, ny, h, phi, g->node_class, aff_pos, minus_pos, gop_off, gh_off,
                                                          epos, tval, n_bodies, g->d_regions, g->aff_node, g->aff_body,
                                                          g->aff_solid, g->gop_idx, g->gop_w, g->minus_node, g->gh_idx,
-                                                         g->gh_w, err);
+                                                         g->gh_w, g->minus_cp, g->minus_mask, g->minus_map, err);
     k_ptr_from_offsets<<<(na + 256) / 256, 256, 0, s>>>(na, nx, g->aff_node, gop_off, gop_total, g->gop_ptr);
     k_ptr_from_offsets<<<(nm + 256) / 256, 256, 0, s>>>(nm, nx, g->minus_node, gh_off, gh_total, g->gh_ptr);
     k_row_ptr<<<(NY + 256) / 256, 256, 0, s>>>(NX, NY, na, aff_pos, g->aff_row_ptr);
@@ -558,7 +578,7 @@ void free_geometry(iim_geometry g) {
                     g->aff_row_ptr, g->aff_solid, g->gop_ptr, g->gop_idx, g->gop_w, g->minus_node, g->gh_ptr,
                     g->gh_idx, g->gh_w, g->node_class, g->body_circ, g->d_regions, g->lam_x64, g->lam_y64,
                     g->lam_x32, g->lam_y32, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
-                    g->xsol, g->bvec, g->d_int};
+                    g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf};
     for (void* p : ptrs) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);
