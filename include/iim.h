@@ -151,6 +151,24 @@ iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* 
 iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box,
                            double* u, int prec, double* work, iim_stream stream);
 
+/* Allocation-free variant of iim_box_poisson.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- code running while a CUDA graph is
+ * being captured (where cudaMalloc would break the capture), real-time loops and embedded or
+ * foreign-language hosts that must not touch the device allocator, and applications whose
+ * memory pool already owns all free device memory.  Same arguments and results as
+ * iim_box_poisson without `work`: the scratch is a static device array of the library of
+ * 1024 * 1026 doubles (8.4 MB), held by every GPU that loads the library until the process
+ * exits.  Limits: nx, ny <= 1024 (larger grids return IIM_ERR_INVALID_ARG and a message in
+ * iim_last_error_message).  The first call on a device performs a one-time set-up on that
+ * device (twiddle tables, the scratch address, kernel attributes); make that first call
+ * before any stream capture.  Afterwards calls allocate nothing on the device or the host;
+ * every call shares the one scratch array, so calls that overlap on the GPU (different
+ * streams, or other threads) race -- serialize them.  The per-kernel profiler
+ * (iim_profile_begin) records events with allocation; keep it off around this call.
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA.  Asynchronous on `stream`. */
+iim_status iim_box_poisson_noalloc(const iim_grid* grid, const double* f, const double* psi_box, double* u,
+                                   int prec, iim_stream stream);
+
 /* Conservative vorticity transport right-hand side with the IIM boundary treatment (Sec. 3:
  * Eqs. upwind, 2dshuconserve, Sec. 3.2) and the Kelvin ODE (Sec. 5.1, Eq. discreteKelvinChoice)
  * for a given velocity; omega_b from the velocity by the local vorticity boundary condition of

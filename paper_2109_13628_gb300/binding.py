@@ -60,6 +60,7 @@ SIGNATURES = [
     ("iim_poisson_solve", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
                                ctypes.POINTER(iim_stats), _vp]),
     ("iim_box_poisson", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp, _vp]),
+    ("iim_box_poisson_noalloc", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp]),
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
     ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
                           ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
@@ -228,6 +229,17 @@ def iim_box_poisson(grid: iim_grid, f, psi_box, u, prec, work, stream=None):
                                 _ptr(u, torch.float64, NXY, "u"), int(prec), _ptr(work, torch.float64, None, "work"),
                                 _stream(stream))
     _check(st, "iim_box_poisson")
+
+
+def iim_box_poisson_noalloc(grid: iim_grid, f, psi_box, u, prec, stream=None):
+    """iim_box_poisson without a workspace argument: the library's static device scratch is
+    used, for callers that cannot allocate device memory (nx, ny <= 1024; calls that overlap
+    on the GPU race)."""
+    NXY = (grid.nx - 1) * (grid.ny - 1)
+    st = load().iim_box_poisson_noalloc(ctypes.byref(grid), _ptr(f, torch.float64, NXY, "f"),
+                                        _ptr(psi_box, torch.float64, 2 * (grid.nx + grid.ny), "psi_box"),
+                                        _ptr(u, torch.float64, NXY, "u"), int(prec), _stream(stream))
+    _check(st, "iim_box_poisson_noalloc")
 
 
 def iim_status_string(st: int) -> str:

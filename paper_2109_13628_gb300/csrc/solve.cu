@@ -1008,6 +1008,96 @@ extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, con
     return IIM_OK;
 }
 
+// ------------------------------------------------------------------------- allocation-free box solve
+// The same Dirichlet-box solve as iim_box_poisson, for callers that cannot allocate device
+// memory.  Its scratch (the padded transform buffer followed by the eigenvalue tables) is the
+// file-scope array below, which every GPU that loads the library keeps until the process
+// exits.  All calls share it: calls that overlap on the GPU race.  Every call overwrites the
+// whole region it uses before reading it, so no clearing is needed between calls.
+namespace iim {
+constexpr int kNoAllocMaxN = 1024;                                    // nx, ny <= 1024
+constexpr size_t kNoAllocDoubles = (size_t)kNoAllocMaxN * (kNoAllocMaxN + 2);   // 8.4 MB
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+static std::mutex g_noalloc_mutex;
+static double* g_noalloc_ptr[64];
+
+// Eigenvalues of the 1D three-point operators (x modes, then y modes), in FP64 or FP32.
+__global__ void k_box_eigs(int NX, int NY, int nx, int ny, double h, int as_float, double* lam) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= NX + NY) return;
+    const double v = k < NX ? (2.0 - 2.0 * cospi((double)(k + 1) / nx)) / (h * h)
+                            : (2.0 - 2.0 * cospi((double)(k - NX + 1) / ny)) / (h * h);
+    if (as_float) reinterpret_cast<float*>(lam)[k] = (float)v;
+    else lam[k] = v;
+}
+
+// Once per device, with that device current: twiddle tables, the device address of the
+// static scratch, and the shared-memory limits of the transform kernels for the largest
+// supported line, so that later calls touch nothing but their stream.
+static iim_status noalloc_setup(double** out) {
+    int dev = 0;
+    IIM_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return IIM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        IIM_CHECK(ensure_twiddles());
+        void* p = nullptr;
+        IIM_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        allow_smem(k_rows_fwd<double, kRowWarps>, rows_smem<double>(kNoAllocMaxN));
+        allow_smem(k_rows_fwd<float, kRowWarps>, rows_smem<float>(kNoAllocMaxN));
+        allow_smem(k_cols<double, cols_per_block<double>()>, cols_smem<double>(kNoAllocMaxN));
+        allow_smem(k_cols<float, cols_per_block<float>()>, cols_smem<float>(kNoAllocMaxN));
+        allow_smem(k_rows_inv<double, kRowWarps, INV_STORE_F64>, rows_smem<double>(kNoAllocMaxN));
+        allow_smem(k_rows_inv<float, kRowWarps, INV_STORE_F64>, rows_smem<float>(kNoAllocMaxN));
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return IIM_OK;
+}
+}  // namespace iim
+
+extern "C" iim_status iim_box_poisson_noalloc(const iim_grid* grid, const double* f, const double* psi_box, double* u,
+                                              int prec, iim_stream stream) {
+    if (!grid || !f || !u) return IIM_ERR_INVALID_ARG;
+    const int nx = grid->nx, ny = grid->ny;
+    if (!is_pow2_in(nx, 16, 2048) || !is_pow2_in(ny, 16, 2048)) return IIM_ERR_INVALID_ARG;
+    if (nx > kNoAllocMaxN || ny > kNoAllocMaxN) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "iim_box_poisson_noalloc: %d x %d cells exceed its static scratch (nx, ny <= %d)", nx, ny,
+                 kNoAllocMaxN);
+        return IIM_ERR_INVALID_ARG;
+    }
+    if (prec != IIM_FP64 && prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
+    const double h = (grid->x1 - grid->x0) / nx;
+    if (!(h > 0.0)) return IIM_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    IIM_CHECK(noalloc_setup(&scratch));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int NX = nx - 1, NY = ny - 1;
+    double* buf = scratch;                          // padded transform buffer, nx * NY
+    double* lam = scratch + (size_t)nx * NY;        // NX + NY eigenvalues
+    const double ih2 = 1.0 / (h * h);
+    const int as_float = prec == IIM_MIXED;
+    launch("box_eigs", 0.0, 0.0, k_box_eigs, (NX + NY + 255) / 256, 256, 0, s, NX, NY, nx, ny, h, as_float, lam);
+    IIM_LAUNCHED();
+    if (prec == IIM_FP64) {
+        Plan<double> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lam, lam + NX, twiddles64(), (2.0 / nx) * (2.0 / ny)};
+        IIM_CHECK(rows_fwd<double>(p, 0, NY, f, NX, 0, psi_box, ih2, nullptr, nullptr, kNoVec, 0.0, buf, nullptr, s));
+        IIM_CHECK(cols<double>(p, 0, NY - 1, 0, NY - 1, buf, nullptr, s));
+        IIM_CHECK((rows_inv<double, INV_STORE_F64>(p, 0, NY, buf, nullptr, u, NX, 0, nullptr, nullptr, s)));
+    } else {
+        const float* lamf = reinterpret_cast<const float*>(lam);
+        Plan<float> p{NX, NY, nx, ny, ilog2(nx), ilog2(ny), lamf, lamf + NX, twiddles32(),
+                      (float)((2.0 / nx) * (2.0 / ny))};
+        float* fb = reinterpret_cast<float*>(buf);
+        IIM_CHECK(rows_fwd<float>(p, 0, NY, f, NX, 0, psi_box, ih2, nullptr, nullptr, kNoVec, 0.0, fb, nullptr, s));
+        IIM_CHECK(cols<float>(p, 0, NY - 1, 0, NY - 1, fb, nullptr, s));
+        IIM_CHECK((rows_inv<float, INV_STORE_F64>(p, 0, NY, fb, nullptr, u, NX, 0, nullptr, nullptr, s)));
+    }
+    return IIM_OK;
+}
+
 extern "C" const char* iim_last_error_message(void) { return g_last_error; }
 
 extern "C" const char* iim_status_string(iim_status st) {
