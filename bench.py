@@ -46,7 +46,7 @@ def kernel_source_hash():
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N_CELLS)
@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--inner-rtol", type=float, default=0.0, help="mixed-mode Krylov tolerance (0: library default)")
     ap.add_argument("--restart", type=int, default=64)
     ap.add_argument("--sweep", action="store_true", help="print iterations/time for a grid of inner tolerances and exit")
+    ap.add_argument("--no-precond", action="store_true", help="chosen form without the dense Schur preconditioner")
+    ap.add_argument("--batch", type=int, default=8, help="independent problems in flight per step")
+    ap.add_argument("--no-c4", action="store_true", help="skip the mixed-size batched workload")
+    ap.add_argument("--c4-count", type=int, default=96)
     return ap.parse_args()
 
 
@@ -82,7 +86,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -179,6 +183,48 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def c4_batch(iim, inputs, T, dev, count, seed, precond):
+    """The mixed-size batched workload: geometries, inputs, outputs (under-resolved draws skipped)."""
+    import numpy as np
+    import torch
+    probs = inputs.batched_c4(count=count, seed=seed)
+    geos, om, pb, gm, pbar, out, kept = [], [], [], [], [], [], []
+    for P in probs:
+        g = P.grid
+        try:
+            geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions, P.modes)
+        except iim.IIMError:
+            continue
+        cp = iim.iim_geometry_control_points(geo)
+        geos.append(geo)
+        kept.append(P)
+        om.append(T(P.omega.ravel()))
+        pb.append(T(np.zeros(geo.n_control)))
+        h = g.h
+        gm.append(T(np.array([h * h * P.omega[r[2] - 1:r[3], r[0] - 1:r[1]].sum() for r in P.regions])))
+        pbar.append(torch.zeros(len(P.regions), dtype=torch.float64, device=dev))
+        out.append(torch.empty(P.omega.size, dtype=torch.float64, device=dev))
+        del cp
+    t0 = time.perf_counter()
+    if precond:
+        # one-time per-geometry set-up, built concurrently on worker streams (ctypes releases the GIL)
+        import concurrent.futures as cf
+        order = sorted(range(len(geos)), key=lambda k: -kept[k].grid.nx)
+
+        def build(ks):
+            torch.cuda.set_device(dev)
+            st = torch.cuda.Stream(device=dev)
+            for k in ks:
+                iim.iim_build_preconditioner(geos[k], stream=st)
+            st.synchronize()
+
+        nw = 8
+        with cf.ThreadPoolExecutor(nw) as ex:
+            list(ex.map(build, [order[w::nw] for w in range(nw)]))
+    torch.cuda.synchronize()
+    return kept, geos, om, pb, gm, pbar, out, time.perf_counter() - t0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -195,82 +241,114 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     import paper_2109_13628_gb300 as iim
-    from paper_2109_13628_gb300 import inputs
+    from paper_2109_13628_gb300 import autotune, inputs
 
     P = inputs.c1_cylinder(args.n)
     g = P.grid
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     grid = iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny)
-    t_setup = time.perf_counter()
-    geo = iim.iim_setup_geometry(grid, T(P.phi), P.regions, P.modes)
-    t_setup = time.perf_counter() - t_setup
-    cp = iim.iim_geometry_control_points(geo)
-    psi_b_h = P.psi_b_fn(cp["x"].cpu().numpy(), cp["y"].cpu().numpy(), None)
+    precond = 0 if args.no_precond else 1
     NXY = (g.nx - 1) * (g.ny - 1)
+    B = max(1, args.batch)
+    # B independent problems (each its own geometry workspace) on the same cylinder workload
+    t_setup = time.perf_counter()
+    geos = [iim.iim_setup_geometry(grid, T(P.phi), P.regions, P.modes) for _ in range(B)]
+    t_setup = (time.perf_counter() - t_setup) / B
+    cp = iim.iim_geometry_control_points(geos[0])
+    psi_b_h = P.psi_b_fn(cp["x"].cpu().numpy(), cp["y"].cpu().numpy(), None)
     omega, psi_b, ring = T(P.omega.ravel()), T(psi_b_h), T(P.psi_box)
-    psibar = torch.zeros(1, dtype=torch.float64, device=dev)
-    psi = torch.empty(NXY, dtype=torch.float64, device=dev)
-    ux, uy = torch.empty_like(psi), torch.empty_like(psi)
+    psibars = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(B)]
+    psis = [torch.empty(NXY, dtype=torch.float64, device=dev) for _ in range(B)]
+    uxs = [torch.empty(NXY, dtype=torch.float64, device=dev) for _ in range(B)]
+    uys = [torch.empty(NXY, dtype=torch.float64, device=dev) for _ in range(B)]
+    t_pc = time.perf_counter()
+    pc_ms = [iim.iim_build_preconditioner(geo) if precond else 0.0 for geo in geos][0]
+    t_pc = (time.perf_counter() - t_pc) / B
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     stream = torch.cuda.current_stream()
+    geo = geos[0]
 
-    def solve(prec, inner=None):
-        return iim.iim_poisson_solve(geo, omega, psi_b, ring, None, psibar, psi, ux, uy,
-                                     opts=iim.default_opts(prec=prec, rtol=RTOL, restart=args.restart,
-                                                           inner_rtol=args.inner_rtol if inner is None else inner))
+    def opts_for(prec, inner=None, pc=None):
+        use_pc = (precond if prec == iim.IIM_MIXED else 0) if pc is None else pc
+        return iim.default_opts(prec=prec, rtol=RTOL, restart=args.restart, precond=use_pc,
+                                inner_rtol=args.inner_rtol if inner is None else inner)
+
+    def solve(prec, inner=None, pc=None):
+        # the plain FP64 comparator is the unpreconditioned paper iteration
+        return iim.iim_poisson_solve(geo, omega, psi_b, ring, None, psibars[0], psis[0], uxs[0], uys[0],
+                                     opts=opts_for(prec, inner, pc))
+
+    def solve_batch(n_streams):
+        return iim.iim_poisson_solve_batched(geos, [omega] * B, [psi_b] * B, [ring] * B, None, psibars, psis, uxs, uys,
+                                             opts=opts_for(iim.IIM_MIXED), n_streams=n_streams)
 
     if args.sweep:
-        for prec in (iim.IIM_MIXED, iim.IIM_FP64):
-            for inner in ((3e-3, 1e-3, 3e-4, 1e-4, 3e-5, 1e-5) if prec == iim.IIM_MIXED else (5e-12, 1e-11, 5e-11)):
+        for prec, pc in ((iim.IIM_MIXED, 1), (iim.IIM_FP64, 1), (iim.IIM_MIXED, 0), (iim.IIM_FP64, 0)):
+            if pc and not precond:
+                continue
+            for inner in ((1e-3, 1e-4, 1e-5) if prec == iim.IIM_MIXED else (5e-12, 5e-11)):
                 for _ in range(2):
-                    solve(prec, inner)
+                    solve(prec, inner, pc)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 for _ in range(5):
-                    st = solve(prec, inner)
+                    st = solve(prec, inner, pc)
                 torch.cuda.synchronize()
-                print(json.dumps({"prec": prec, "inner": inner, "ms": (time.perf_counter() - t0) / 5 * 1e3,
-                                  "iters": st["iters"], "refinements": st["refinements"], "rel_res": st["rel_res"]}))
+                print(json.dumps({"prec": prec, "precond": pc, "inner": inner,
+                                  "ms": (time.perf_counter() - t0) / 5 * 1e3, "iters": st["iters"],
+                                  "refinements": st["refinements"], "rel_res": st["rel_res"]}))
         return
 
-    def timed(prec, k, warm):
+    def timed(step, k, warm):
         for _ in range(warm):
-            solve(prec)
+            step()
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
-        ms, stats = [], []
+        ms, outs = [], []
         for _ in range(k):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            st = solve(prec)
+            outs.append(step())
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
-            stats.append(st)
         torch.cuda.synchronize()
         if ws > 1:
             torch.distributed.barrier()
-        return ms, stats
+        return ms, outs
 
-    # ---- chosen form (timed region), with clocks sampled and launches counted
+    def max_over_ranks(x):
+        if ws > 1:
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return x
+
+    # ---- concurrency autotuning of the batched form (untimed)
+    n_streams = B
+    tuned = None
+    if B > 1:
+        n_streams, tuned = autotune.tune_streams(solve_batch, tuple(c for c in (1, 2, 4, 8, 12, 16) if c <= B))
+    # ---- chosen form: B problems per step in flight (the timed region), clocks sampled
     with ClockSampler(local) as clk:
         l0 = iim.iim_launch_count()
-        ms, stats = timed(iim.IIM_MIXED, args.steps, args.warmup)
+        ms, outs = timed(lambda: solve_batch(n_streams)[1] if B > 1 else [solve(iim.IIM_MIXED)], args.steps,
+                         args.warmup)
         launches = iim.iim_launch_count() - l0
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * args.steps / (total_ms * 1e-3)
-    # ---- plain FP64 iteration (the comparator)
+    stats = [s for step_stats in outs for s in step_stats]
+    total_ms = max_over_ranks(sum(ms))
+    value = ws * B * args.steps / (total_ms * 1e-3)
+    # ---- the same form one problem at a time (latency view)
+    ms1, outs1 = timed(lambda: solve(iim.IIM_MIXED), args.steps, 2)
+    single = args.steps / (sum(ms1) * 1e-3)
+    # ---- plain FP64 iteration (the comparator: unpreconditioned, one problem at a time)
     k64 = max(3, args.steps // 5)
-    ms64, stats64 = timed(iim.IIM_FP64, k64, max(3, args.warmup // 2))
+    ms64, stats64 = timed(lambda: solve(iim.IIM_FP64), k64, 2)
     plain = k64 / (sum(ms64) * 1e-3)
-    # ---- per-kernel timing of the same step (a second pass with CUDA events around kernels)
+    # ---- per-kernel timing of the single-problem step (second pass, CUDA events around kernels)
     kprof = min(args.steps, 10)
     iim.iim_profile_begin()
     for _ in range(kprof):
@@ -291,64 +369,81 @@ def main():
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
                 "alg_bytes_per_launch": dom["bytes"] / dom["launches"], "avg_launch_us": per_launch_s * 1e6,
-                "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None}
-    # ---- end to end through the C ABI with host buffers
+                "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None,
+                "timing": "single-problem step, CUDA events around each launch on its stream"}
+    # ---- end to end through the C ABI with host buffers (B problems per step)
     e2e = None
     if not args.no_e2e:
-        h_omega = torch.empty(NXY, dtype=torch.float64).pin_memory()
-        h_omega.copy_(torch.from_numpy(np.ascontiguousarray(P.omega).ravel()))
+        h_omega = torch.from_numpy(np.ascontiguousarray(P.omega).ravel()).pin_memory()
         h_psib = torch.from_numpy(np.ascontiguousarray(psi_b_h)).pin_memory()
         h_ring = torch.from_numpy(np.ascontiguousarray(P.psi_box)).pin_memory()
-        h_out = [torch.empty(NXY, dtype=torch.float64).pin_memory() for _ in range(3)]
-        d_omega, d_psib, d_ring = torch.empty_like(omega), torch.empty_like(psi_b), torch.empty_like(ring)
+        h_out = [[torch.empty(NXY, dtype=torch.float64).pin_memory() for _ in range(3)] for _ in range(B)]
+        d_in = [(torch.empty_like(omega), torch.empty_like(psi_b), torch.empty_like(ring)) for _ in range(B)]
 
         def e2e_step():
-            d_omega.copy_(h_omega, non_blocking=True)
-            d_psib.copy_(h_psib, non_blocking=True)
-            d_ring.copy_(h_ring, non_blocking=True)
-            iim.iim_poisson_solve(geo, d_omega, d_psib, d_ring, None, psibar, psi, ux, uy,
-                                  opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=RTOL))
-            for h, d in zip(h_out, (psi, ux, uy)):
-                h.copy_(d, non_blocking=True)
+            for d in d_in:
+                d[0].copy_(h_omega, non_blocking=True)
+                d[1].copy_(h_psib, non_blocking=True)
+                d[2].copy_(h_ring, non_blocking=True)
+            if B > 1:
+                iim.iim_poisson_solve_batched(geos, [d[0] for d in d_in], [d[1] for d in d_in], [d[2] for d in d_in],
+                                              None, psibars, psis, uxs, uys, opts=opts_for(iim.IIM_MIXED),
+                                              n_streams=n_streams)
+            else:
+                iim.iim_poisson_solve(geo, d_in[0][0], d_in[0][1], d_in[0][2], None, psibars[0], psis[0], uxs[0],
+                                      uys[0], opts=opts_for(iim.IIM_MIXED))
+            for k in range(B):
+                for h, d in zip(h_out[k], (psis[k], uxs[k], uys[k])):
+                    h.copy_(d, non_blocking=True)
 
-        for _ in range(args.warmup):
-            e2e_step()
-        torch.cuda.synchronize()
-        ems = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
-            b.synchronize()
-            ems.append(a.elapsed_time(b))
-        e_total = sum(ems)
-        if ws > 1:
-            t = torch.tensor([e_total], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_total = float(t.item())
-        h2d = 8 * (NXY + psi_b.numel() + ring.numel())
-        d2h = 8 * 3 * NXY
-        e2e = {"value": ws * args.steps / (e_total * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+        ems, _ = timed(e2e_step, args.steps, args.warmup)
+        e_total = max_over_ranks(sum(ems))
+        e2e = {"value": ws * B * args.steps / (e_total * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": B * 8 * (NXY + psi_b.numel() + ring.numel()), "d2h_bytes_per_step": B * 8 * 3 * NXY}
+    # ---- mixed-size batched workload (96 problems, 128^2 .. 1024^2)
+    c4 = None
+    if not args.no_c4:
+        kept, cgeos, om, pbv, gm, pbar, cout, c4_pc = c4_batch(iim, inputs, T, dev, args.c4_count, 2, precond)
+        tiles = autotune.tune_tiles(cgeos, lambda k: iim.iim_poisson_solve(
+            cgeos[k], om[k], pbv[k], None, gm[k], pbar[k], cout[k], opts=opts_for(iim.IIM_MIXED)))
+
+        def c4_run(nst):
+            return iim.iim_poisson_solve_batched(cgeos, om, pbv, None, gm, pbar, cout, opts=opts_for(iim.IIM_MIXED),
+                                                 n_streams=nst)
+
+        c4_streams, c4_tuned = autotune.tune_streams(c4_run, (4, 8, 16, 24))
+        cms, couts = timed(lambda: c4_run(c4_streams)[1], max(2, args.steps // 10), 1)
+        unknowns = sum((P.grid.nx - 1) * (P.grid.ny - 1) for P in kept)
+        c4 = {"problems": len(kept), "solves_per_s": len(kept) * len(cms) / (sum(cms) * 1e-3),
+              "unknown_solves_per_s": unknowns * len(cms) / (sum(cms) * 1e-3), "ms_per_batch": sum(cms) / len(cms),
+              "streams": c4_streams, "tiles_by_size": {f"{k[0]}x{k[1]}": v for k, v in tiles.items()},
+              "precond_setup_s": c4_pc, "max_rel_res": max(s["rel_res"] for o in couts for s in o),
+              "krylov_iters_mean": statistics.mean(s["iters"] for o in couts for s in o)}
+        for gg in cgeos:
+            gg.close()
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.n)
-    it = [s["iters"] for s in stats]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 transforms + f64 refinement", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "flushed before every timed step (256 MiB write, outside the events)",
-                   "form": f"mixed: FP32 DST-I box solves inside FP64 iterative refinement, GMRES({args.restart}) FP64 Krylov",
+        "config": {"workload": WORKLOAD, "batch": f"{B} independent problems of this workload per step, in flight "
+                                                   f"together on {n_streams} streams",
+                   "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                   "form": ("mixed: FP32 DST-I box solves inside FP64 iterative refinement, GMRES("
+                            f"{args.restart}) FP64 Krylov" + (", right-preconditioned by the dense FP32 inverse of the"
+                                                             " Schur matrix" if precond else "")),
                    "parallelism": f"replicas x{ws}"},
+        "single_problem": {"value": single, "unit": UNIT, "ms_per_solve": sum(ms1) / len(ms1)},
         "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": sum(ms64) / k64,
                        "krylov_iters": statistics.mean(s["iters"] for s in stats64),
                        "final_rel_res": max(s["rel_res"] for s in stats64)},
         "speedup_vs_plain_fp64": value / plain / ws,
-        "solver": {"krylov_iters": statistics.mean(it), "refinements": statistics.mean(s["refinements"] for s in stats),
+        "solver": {"krylov_iters": statistics.mean(s["iters"] for s in stats),
+                   "refinements": statistics.mean(s["refinements"] for s in stats),
                    "final_rel_res_max": max(s["rel_res"] for s in stats), "setup_s": t_setup,
+                   "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms, "streams_tuning_ms": tuned,
                    "n_control": geo.n_control, "n_affected": geo.n_affected},
         "roofline": roof,
         "kernels": [{"name": r["name"], "launches_per_step": r["launches"] / kprof, "ms_per_step": r["ms"] / kprof,
@@ -356,11 +451,13 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "e2e": e2e,
+        "batched_c4": c4,
         "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line))
-    geo.close()
+    for gg in geos:
+        gg.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
 

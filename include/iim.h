@@ -74,7 +74,9 @@ typedef struct {
     int max_refine;    /* cap on outer refinement steps */
     int guess;         /* 0: start from psi = 0; 1: start from psi_guess */
     double inner_rtol; /* Krylov tolerance of each correction solve (<= 0: library default,
-                          rtol/20 in FP64 mode, 2e-5 in mixed mode) */
+                          rtol/20 in FP64 mode, 1e-4 in mixed mode) */
+    int precond;       /* 1: right-precondition GMRES with the dense inverse of the Schur matrix
+                          (built on first use, see iim_build_preconditioner); 0: plain GMRES */
 } iim_opts;
 
 typedef struct {
@@ -140,6 +142,37 @@ iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* 
                              double* psi_out, double* ux_out, double* uy_out,
                              const double* psi_guess, const iim_opts* opts, iim_stats* stats,
                              iim_stream stream);
+
+/* Many independent IIM Poisson solves in flight at once (batched workloads of mixed grid sizes
+ * and geometries).  Problem k uses geoms[k] (all distinct: each geometry owns the workspace
+ * of its solve) and the k-th pointer of every array argument, with the meaning of
+ * iim_poisson_solve; psi_box, gamma, ux_out, uy_out may be NULL arrays (then NULL for every
+ * problem).  n_streams worker threads, each on its own stream, take the problems largest
+ * first; every solve replays its GMRES iterations as a CUDA graph.  The work is ordered after
+ * prior work on `stream` and `stream` waits for all of it.  stats: host, n entries or NULL.
+ * Returns the first non-OK status of any problem (all problems are attempted).  The paper
+ * solves one problem at a time; batching is this library's throughput mode. */
+iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const double* const* omega,
+                                     const double* const* psi_b, const double* const* psi_box,
+                                     const double* const* gamma, double* const* psibar,
+                                     double* const* psi_out, double* const* ux_out, double* const* uy_out,
+                                     const iim_opts* opts, iim_stats* stats, int n_streams,
+                                     iim_stream stream);
+
+/* Tile width of the column pass of the geometry's rectangular solves: 2, 4 or 8 columns per
+ * block (FP32 transforms use 4 or 8, FP64 transforms 2 or 4; the nearest supported width is
+ * taken).  Chosen per grid size by the autotuner of the Python package.  Errors:
+ * IIM_ERR_INVALID_ARG. */
+iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
+
+/* Builds the dense Schur-complement preconditioner of a geometry: the matrix S of the augmented
+ * system of Sec. 4.2 (gamma plus circulation unknowns), one column per FP32 operator
+ * application, and its inverse by Gauss-Jordan elimination with partial pivoting in FP32,
+ * kept as an (ns x 2ns) FP32 array on the device (ns = |A| + circulation bodies).  The paper
+ * solves with plain GMRes; this is a one-time cost per geometry that pays when many solves
+ * share the geometry (time stepping).  Its milliseconds go to *setup_ms (host, may be NULL).
+ * Errors: IIM_ERR_NOT_CONVERGED (singular pivot), IIM_ERR_CUDA.  Synchronizes `stream`. */
+iim_status iim_build_preconditioner(iim_geometry g, float* setup_ms, iim_stream stream);
 
 /* Rectangular Dirichlet-box solve u = -nabla_h^{-2} f (Sec. 4.2: the FFT solution operator,
  * here a 2D DST-I for the Dirichlet box): -nabla_h^2 u = f on the interior nodes with box data.

@@ -1,0 +1,48 @@
+"""Autotuner of the batched solver: the column-pass tile width per grid-size bucket, then the
+number of concurrent worker streams, each chosen by timing real solves of the caller's own
+problems on the device (CUDA events), keeping the fastest."""
+from __future__ import annotations
+
+import collections
+
+import torch
+
+from . import binding as B
+
+
+def _time(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_tiles(geoms, solve_one, widths=(2, 4, 8), reps=2):
+    """For each grid-size bucket, the tile width with the fastest solve of the bucket's first
+    problem; `solve_one(k)` solves problem k.  Applies the choice to every geometry and returns
+    {(nx, ny): width}."""
+    buckets = collections.defaultdict(list)
+    for k, g in enumerate(geoms):
+        buckets[(g.grid.nx, g.grid.ny)].append(k)
+    best = {}
+    for key, ks in buckets.items():
+        k0 = ks[0]
+        times = {}
+        for w in widths:
+            B.iim_geometry_set_tiles(geoms[k0], w)
+            times[w] = _time(lambda: solve_one(k0), reps)
+        best[key] = min(times, key=times.get)
+        for k in ks:
+            B.iim_geometry_set_tiles(geoms[k], best[key])
+    return best
+
+
+def tune_streams(run_batch, candidates=(1, 2, 4, 8, 12, 16, 24)):
+    """The number of worker streams for which `run_batch(n_streams)` is fastest."""
+    times = {c: _time(lambda: run_batch(c), 1) for c in candidates}
+    return min(times, key=times.get), times

@@ -36,7 +36,7 @@ class iim_region(ctypes.Structure):
 
 class iim_opts(ctypes.Structure):
     _fields_ = [("prec", _i), ("rtol", _d), ("max_iter", _i), ("restart", _i), ("max_refine", _i),
-                ("guess", _i), ("inner_rtol", _d)]
+                ("guess", _i), ("inner_rtol", _d), ("precond", _i)]
 
 
 class iim_stats(ctypes.Structure):
@@ -61,6 +61,10 @@ SIGNATURES = [
                                ctypes.POINTER(iim_stats), _vp]),
     ("iim_box_poisson", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp, _vp]),
     ("iim_box_poisson_noalloc", _i, [ctypes.POINTER(iim_grid), _vp, _vp, _vp, _i, _vp]),
+    ("iim_build_preconditioner", _i, [_vp, ctypes.POINTER(ctypes.c_float), _vp]),
+    ("iim_poisson_solve_batched", _i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
+                                       _vp, _i, _vp]),
+    ("iim_geometry_set_tiles", _i, [_vp, _i]),
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
     ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
                           ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
@@ -197,8 +201,54 @@ def iim_geometry_affected_points(g: Geometry, stream=None):
     return out
 
 
-def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=64, max_refine=12, guess=0, inner_rtol=0.0):
-    return iim_opts(int(prec), float(rtol), int(max_iter), int(restart), int(max_refine), int(guess), float(inner_rtol))
+def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=64, max_refine=12, guess=0, inner_rtol=0.0,
+                 precond=0):
+    return iim_opts(int(prec), float(rtol), int(max_iter), int(restart), int(max_refine), int(guess), float(inner_rtol),
+                    int(precond))
+
+
+def iim_geometry_set_tiles(g: "Geometry", cols_per_block: int):
+    _check(load().iim_geometry_set_tiles(g.handle, int(cols_per_block)), "iim_geometry_set_tiles")
+
+
+def _ptr_array(tensors, dtype, sizes, name):
+    """Host array of device pointers (NULL entries allowed) or None when every entry is None."""
+    if tensors is None or all(t is None for t in tensors):
+        return None
+    arr = (_vp * len(tensors))()
+    for k, (t, n) in enumerate(zip(tensors, sizes)):
+        p = _ptr(t, dtype, n, f"{name}[{k}]")
+        arr[k] = p.value if p is not None else None
+    return arr
+
+
+def iim_poisson_solve_batched(geoms, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out=None, uy_out=None,
+                              opts: "iim_opts | None" = None, n_streams=8, stream=None, check=True):
+    """Solves len(geoms) independent problems concurrently; returns (status, [stats dicts])."""
+    n = len(geoms)
+    f64 = torch.float64
+    nxy = [(g.grid.nx - 1) * (g.grid.ny - 1) for g in geoms]
+    G = (_vp * n)(*[g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle for g in geoms])
+    stats = (iim_stats * n)()
+    o = opts if opts is not None else default_opts()
+    none = [None] * n
+    st = load().iim_poisson_solve_batched(
+        n, G, _ptr_array(omega, f64, nxy, "omega"), _ptr_array(psi_b, f64, [g.n_control for g in geoms], "psi_b"),
+        _ptr_array(psi_box or none, f64, [2 * (g.grid.nx + g.grid.ny) for g in geoms], "psi_box"),
+        _ptr_array(gamma or none, f64, [g.n_bodies for g in geoms], "gamma"),
+        _ptr_array(psibar, f64, [g.n_bodies for g in geoms], "psibar"), _ptr_array(psi_out, f64, nxy, "psi_out"),
+        _ptr_array(ux_out or none, f64, nxy, "ux_out"), _ptr_array(uy_out or none, f64, nxy, "uy_out"),
+        ctypes.byref(o), stats, int(n_streams), _stream(stream))
+    if check:
+        _check(st, "iim_poisson_solve_batched")
+    return st, [stats[k].as_dict() for k in range(n)]
+
+
+def iim_build_preconditioner(g: "Geometry", stream=None) -> float:
+    """Builds the dense Schur-complement preconditioner; returns its set-up milliseconds."""
+    ms = ctypes.c_float()
+    _check(load().iim_build_preconditioner(g.handle, ctypes.byref(ms), _stream(stream)), "iim_build_preconditioner")
+    return ms.value
 
 
 def iim_poisson_solve(g: Geometry, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out=None, uy_out=None,

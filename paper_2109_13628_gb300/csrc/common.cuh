@@ -150,6 +150,14 @@ struct iim_geometry_s {
     int* d_int = nullptr;        // device counters / flags
     double* h_pinned = nullptr;  // pinned host scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // dense Schur-complement preconditioner: [S | S^-1] row-major ns x 2ns (FP32), scratch
+    float* pc_aug = nullptr;
+    float* pc_f = nullptr;
+    int* pc_info = nullptr;
+    double* pc_z = nullptr;      // 2 ns
+    int pc_ready = 0;
+    float pc_setup_ms = 0.f;
+    int cols_c = 4;              // column-pass tile width (autotuned per size bucket)
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     void* graph64 = nullptr;     // captured GMRES iteration (FP64 transforms)
     void* graph32 = nullptr;     // captured GMRES iteration (FP32 transforms)
@@ -157,4 +165,10 @@ struct iim_geometry_s {
 
 namespace iim {
 void destroy_graphs(iim_geometry g);
+// dense Schur-complement preconditioner (precond.cu)
+iim_status gj_invert_aug(float* A, int n, float* f, int* info, cudaStream_t s);
+iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
+                        int accumulate, const int* stop, cudaStream_t s);
+__global__ void k_unit_vector(int n, int j, double* v);
+__global__ void k_store_column(int n, int j, const double* v, float* A);
 }

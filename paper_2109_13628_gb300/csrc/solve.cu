@@ -87,6 +87,7 @@ struct Plan {
     const T* lam_y;
     const cpx<T>* tw;
     T norm;
+    int cols_c = 4;   // columns per block of the column pass (tile width)
 };
 
 // Algorithmic flops of one DST-I of n - 1 points through an n/2-point complex FFT
@@ -100,9 +101,16 @@ constexpr int kRowWarps = 4;
 template <typename T>
 static size_t rows_smem(int n) { return (size_t)n * sizeof(cpx<T>) + (size_t)kRowWarps * 2 * n * sizeof(T); }
 template <typename T>
-static size_t cols_smem(int n) {
+static size_t cols_smem(int n, int C = cols_per_block<T>()) {
     const int pad = sizeof(T) == 4 ? 4 : 2;
-    return (size_t)n * sizeof(cpx<T>) + (size_t)cols_per_block<T>() * (2 * n + pad) * sizeof(T);
+    return (size_t)n * sizeof(cpx<T>) + (size_t)C * (2 * n + pad) * sizeof(T);
+}
+
+// Tile widths the column pass supports: FP32 4 or 8 columns, FP64 2 or 4 (16-byte row segments).
+template <typename T>
+static int tile_width(int requested) {
+    if (sizeof(T) == 4) return requested >= 8 ? 8 : 4;
+    return requested <= 2 ? 2 : 4;
 }
 
 // Raises a kernel's dynamic shared memory limit once per (device, kernel, size).
@@ -138,10 +146,22 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
     return IIM_OK;
 }
 
+template <typename T, int C>
+static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
+                            cudaStream_t s);
+
 template <typename T>
 static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s) {
-    constexpr int C = cols_per_block<T>();
-    const size_t sm = cols_smem<T>(p.ny);
+    const int C = tile_width<T>(p.cols_c);
+    if (C == 8) return cols_tile<T, (sizeof(T) == 4 ? 8 : 4)>(p, in0, in1, out0, out1, buf, stop, s);
+    if (C == 2) return cols_tile<T, (sizeof(T) == 8 ? 2 : 4)>(p, in0, in1, out0, out1, buf, stop, s);
+    return cols_tile<T, 4>(p, in0, in1, out0, out1, buf, stop, s);
+}
+
+template <typename T, int C>
+static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
+                            cudaStream_t s) {
+    const size_t sm = cols_smem<T>(p.ny, C);
     allow_smem(k_cols<T, C>, sm);
     launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32", (double)(in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
            (double)p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), k_cols<T, C>, p.nx / C, C * 32, sm, s, p.NX, p.NY, p.ny,
@@ -169,12 +189,12 @@ static Plan<T> make_plan(iim_geometry g);
 template <>
 Plan<double> make_plan<double>(iim_geometry g) {
     return Plan<double>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x64, g->lam_y64,
-                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny)};
+                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny), g->cols_c};
 }
 template <>
 Plan<float> make_plan<float>(iim_geometry g) {
     return Plan<float>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
-                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny))};
+                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c};
 }
 
 // ------------------------------------------------------------------------- reductions
@@ -588,7 +608,7 @@ __global__ void k_gmres_init(int* __restrict__ di, int maxit, double* __restrict
 // ------------------------------------------------------------------------- solver
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
-    int prec = -1, m = 0;
+    int prec = -1, m = 0, pc = 0;
     cudaStream_t stream = nullptr;
     int nodes = 0;
 };
@@ -608,6 +628,7 @@ struct Solver {
     int iters = 0;
     double last_gmres_rel = 0.0;
     bool use_graph = true;
+    bool precond = false;
     static constexpr int kResBlocks = 1024;
     static constexpr int kNormBlocks = 64;
     static constexpr int kBatch = 6;   // graph replays between host convergence checks
@@ -647,11 +668,16 @@ struct Solver {
     // ---- Schur operator application V_{jd+1} = S_aug V_jd, jd = di[jslot] (device)
     template <typename T>
     iim_status apply_at(int jslot, const int* stop) {
+        return apply_vec<T>(VecArg{g->V, di() + jslot, 0, (long)ns}, di() + jslot, stop);
+    }
+
+    // ---- V_{*out_j + 1} = S_aug vin
+    template <typename T>
+    iim_status apply_vec(VecArg vj, const int* out_j, const int* stop) {
         Plan<T> p = make_plan<T>(g);
         T* tb = (T*)g->tbuf;
         T* pt = (T*)g->psiT;
         const long ld = ns;
-        const VecArg vj{g->V, di() + jslot, 0, ld};
         if (g->na > 0) {
             IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, 0, 0, nullptr, 0.0, g->aff_row_ptr,
                                   g->aff_node, vj, 1.0, tb, stop, s));
@@ -660,8 +686,48 @@ struct Solver {
         }
         const int nga = (g->na + 127) / 128;
         launch("gather", 0.0, 0.0, k_gather<T, 128>, nga + g->ncirc, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx,
-               g->gop_w, pt, g->cp_body, g->body_circ, g->aff_body, vj, 1, g->V, di() + jslot, ld, stop);
+               g->gop_w, pt, g->cp_body, g->body_circ, g->aff_body, vj, 1, g->V, out_j, ld, stop);
         IIM_LAUNCHED();
+        return IIM_OK;
+    }
+
+    // ---- dense Schur-complement preconditioner: columns S e_j from FP32 operator applications,
+    // then [S | I] -> [I | S^-1] by Gauss-Jordan with partial pivoting (FP32)
+    iim_status build_precond() {
+        if (g->pc_ready) return IIM_OK;
+        const int n = ns;
+        const long ld = ns;
+        if (!g->pc_aug) {
+            IIM_TRY(cudaMalloc(&g->pc_aug, sizeof(float) * 2 * (size_t)n * n));
+            IIM_TRY(cudaMalloc(&g->pc_f, sizeof(float) * (size_t)n));
+            IIM_TRY(cudaMalloc(&g->pc_info, sizeof(int)));
+            IIM_TRY(cudaMalloc(&g->pc_z, sizeof(double) * 2 * (size_t)n));
+        }
+        IIM_TRY(cudaEventRecord(g->ev0, s));
+        launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 0);
+        const int eb = (n + 255) / 256;
+        for (int j = 0; j < n; ++j) {
+            launch("pc_unit", 0.0, 0.0, k_unit_vector, eb, 256, 0, s, n, j, g->V);
+            IIM_CHECK(apply_at<float>(DI_TMPJ, nullptr));
+            launch("pc_column", 0.0, 0.0, k_store_column, eb, 256, 0, s, n, j, (const double*)(g->V + ld), g->pc_aug);
+            IIM_LAUNCHED();
+        }
+        IIM_CHECK(gj_invert_aug(g->pc_aug, n, g->pc_f, g->pc_info, s));
+        int info = 0;
+        IIM_TRY(cudaMemcpyAsync(&info, g->pc_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaEventRecord(g->ev1, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        if (info != 0) {
+            snprintf(g_last_error, sizeof(g_last_error), "Schur matrix singular at pivot %d", info);
+            return IIM_ERR_NOT_CONVERGED;
+        }
+        cudaEventElapsedTime(&g->pc_setup_ms, g->ev0, g->ev1);
+        g->pc_ready = 1;
+        // the captured iteration graphs may predate the preconditioner buffers
+        for (void** gp : {&g->graph64, &g->graph32}) {
+            IterGraph* G = (IterGraph*)*gp;
+            if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+        }
         return IIM_OK;
     }
 
@@ -682,13 +748,19 @@ struct Solver {
 
     template <typename T>
     iim_status iteration() {
-        IIM_CHECK(apply_at<T>(DI_J, di() + DI_STOP));
+        if (precond) {
+            // right preconditioning: z = M v_j, v_{j+1} = S z
+            IIM_CHECK(dense_matvec(ns, g->pc_aug + ns, 2L * ns, g->V, di() + DI_J, (long)ns, g->pc_z, 0, di() + DI_STOP, s));
+            IIM_CHECK(apply_vec<T>(VecArg{g->pc_z, nullptr, 0, 0}, di() + DI_J, di() + DI_STOP));
+        } else {
+            IIM_CHECK(apply_at<T>(DI_J, di() + DI_STOP));
+        }
         return ortho_iter();
     }
 
     template <typename T>
     iim_status ensure_graph(IterGraph& G) {
-        if (G.exec && G.prec == (int)sizeof(T) && G.m == m) return IIM_OK;
+        if (G.exec && G.prec == (int)sizeof(T) && G.m == m && G.pc == (int)precond) return IIM_OK;
         if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
         // capture on the geometry's private stream (the caller's may be the legacy stream,
         // which cannot be captured); the graph is then launched on the caller's stream
@@ -717,6 +789,7 @@ struct Solver {
         if (e != cudaSuccess) { G.exec = nullptr; record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); return IIM_ERR_CUDA; }
         G.prec = (int)sizeof(T);
         G.m = m;
+        G.pc = (int)precond;
         G.stream = s;
         G.nodes = (int)nn;
         return IIM_OK;
@@ -805,7 +878,15 @@ struct Solver {
                 IIM_CHECK(read_state(st));
             }
             launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
-            launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, x);
+            if (precond) {
+                // x += M (V y)
+                double* t = g->pc_z + ns_;
+                IIM_TRY(cudaMemsetAsync(t, 0, (size_t)ns_ * sizeof(double), s));
+                launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, t);
+                IIM_CHECK(dense_matvec(ns_, g->pc_aug + ns_, 2L * ns_, t, nullptr, 0, x, 1, nullptr, s));
+            } else {
+                launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, x);
+            }
             IIM_LAUNCHED();
             if (st[DI_CONV] || st[DI_IT] >= max_it) break;
             // restart: V_1 = x, V_2 = S V_1, V_0 = (b - V_2) / ||b - V_2||
@@ -885,7 +966,7 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
                                         const double* gamma, double* psibar, double* psi_out, double* ux_out,
                                         double* uy_out, const double* psi_guess, const iim_opts* opts_in,
                                         iim_stats* stats, iim_stream stream) {
-    iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0};
+    iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
     if (opts_in) opts = *opts_in;
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (!g || !omega || !psi_out || (g->ncp > 0 && !psi_b) || (g->nb > 0 && !psibar)) return IIM_ERR_INVALID_ARG;
@@ -898,13 +979,15 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     IIM_CHECK(ensure_krylov(g, opts.restart));
     if (g->ncirc > 0)
         IIM_TRY(cudaMemcpyAsync(g->d_int + DI_CIRC, g->circ_ids.data(), g->ncirc * sizeof(int), cudaMemcpyHostToDevice, s));
-    IIM_TRY(cudaEventRecord(g->ev0, s));
 
     Solver S;
     S.g = g; S.s = s; S.prec = opts.prec; S.omega = omega; S.psi_b = psi_b; S.ring = psi_box; S.gamma = gamma;
     S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
+    S.precond = opts.precond != 0 && S.ns > 0;
+    if (S.precond && !g->pc_ready) IIM_CHECK(S.build_precond());
+    IIM_TRY(cudaEventRecord(g->ev0, s));
     const long npad = (long)g->nx * g->NY;
-    const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 1e-5);
+    const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 1e-4);
 
     // ||f||: residual at psi = 0 (ghosts from the boundary data only)
     double res2 = 0.0, cerr = 0.0;
@@ -965,6 +1048,33 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
     }
     return st;
+}
+
+extern "C" iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block) {
+    if (!g || (cols_per_block != 2 && cols_per_block != 4 && cols_per_block != 8)) return IIM_ERR_INVALID_ARG;
+    if (g->cols_c != cols_per_block) {
+        g->cols_c = cols_per_block;
+        // captured iteration graphs hold the previous kernels
+        for (void** gp : {&g->graph64, &g->graph32}) {
+            IterGraph* G = (IterGraph*)*gp;
+            if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+        }
+    }
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_build_preconditioner(iim_geometry g, float* setup_ms, iim_stream stream) {
+    if (!g) return IIM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    IIM_CHECK(ensure_twiddles());
+    IIM_CHECK(ensure_krylov(g, std::max(g->krylov_m, 2)));
+    if (g->ncirc > 0)
+        IIM_TRY(cudaMemcpyAsync(g->d_int + DI_CIRC, g->circ_ids.data(), g->ncirc * sizeof(int), cudaMemcpyHostToDevice, s));
+    Solver S;
+    S.g = g; S.s = s; S.prec = IIM_MIXED; S.ns = g->na + g->ncirc; S.m = g->krylov_m; S.L = KLayout{g->krylov_m};
+    if (S.ns > 0) IIM_CHECK(S.build_precond());
+    if (setup_ms) *setup_ms = g->pc_setup_ms;
+    return IIM_OK;
 }
 
 // Rectangular Dirichlet-box solve with caller workspace (Sec. 4.2 solution operator).
@@ -1046,8 +1156,8 @@ static iim_status noalloc_setup(double** out) {
         IIM_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         allow_smem(k_rows_fwd<double, kRowWarps>, rows_smem<double>(kNoAllocMaxN));
         allow_smem(k_rows_fwd<float, kRowWarps>, rows_smem<float>(kNoAllocMaxN));
-        allow_smem(k_cols<double, cols_per_block<double>()>, cols_smem<double>(kNoAllocMaxN));
-        allow_smem(k_cols<float, cols_per_block<float>()>, cols_smem<float>(kNoAllocMaxN));
+        allow_smem(k_cols<double, 4>, cols_smem<double>(kNoAllocMaxN, 4));
+        allow_smem(k_cols<float, 4>, cols_smem<float>(kNoAllocMaxN, 4));
         allow_smem(k_rows_inv<double, kRowWarps, INV_STORE_F64>, rows_smem<double>(kNoAllocMaxN));
         allow_smem(k_rows_inv<float, kRowWarps, INV_STORE_F64>, rows_smem<float>(kNoAllocMaxN));
         g_noalloc_ptr[dev] = (double*)p;

@@ -269,7 +269,7 @@ def ellipses_problem(n: int, seed: int) -> Problem:
     axes = rng.uniform(0.2, 0.6, size=(nb, 2))
     angles = rng.uniform(0.0, math.pi, size=nb)
     gap = max(0.25, 8.0 * g.h)
-    centers = separated_centers(rng, nb, -1.3, 1.3, list(axes.max(axis=1)), gap)
+    centers = separated_centers(rng, nb, -1.2, 1.2, list(axes.max(axis=1)), gap)
     bodies = [phi_ellipse(X, Y, centers[k][0], centers[k][1], axes[k, 0], axes[k, 1], angles[k]) for k in range(nb)]
     phi = union(*bodies)
     w_nodes = vortex_field(g, seed + 7, 50, 0.1)
@@ -294,3 +294,11 @@ def c2_cylinder_flow(nx: int = 1024, ny: int = 512, seed: int = 0) -> Problem:
     return Problem(grid=g, phi=phi, regions=[region_around(g, phi)], modes=[1], omega=omega,
                    psi_box=box_ring(g, 1.0 * Y), psi_b_fn=lambda x, y, body: np.zeros_like(x),
                    psibar=np.zeros(1), gamma=None, exact=None, name=f"c2_cylinder_flow_{nx}x{ny}")
+
+
+def batched_c4(count: int = 96, seed: int = 2, sizes=(128, 256, 512, 1024)):
+    """Batched workload: `count` problems, grid sizes drawn uniformly from `sizes`, each with
+    1-4 seeded ellipses and a Gaussian-vortex right-hand side (ellipses_problem)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=count)
+    return [ellipses_problem(int(n), seed * 1000 + k) for k, n in enumerate(ns)]

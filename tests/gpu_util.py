@@ -55,3 +55,22 @@ def nodes_from_interior(P, interior):
     out = op.ring_to_nodes(g.nx, g.ny, P.psi_box)
     out[1:-1, 1:-1] = interior
     return out
+
+
+def solve_opts(P, geo, gamma=None, psibar=None, opts=None, velocity=False):
+    """Solve with explicit iim_opts (e.g. the preconditioned form)."""
+    g = P.grid
+    NXY = (g.nx - 1) * (g.ny - 1)
+    psi = torch.empty(NXY, dtype=torch.float64, device=dev())
+    ux = torch.empty_like(psi) if velocity else None
+    uy = torch.empty_like(psi) if velocity else None
+    pb = T(np.zeros(len(P.regions)) if psibar is None else psibar)
+    gm = None if gamma is None else T(gamma)
+    st = iim.iim_poisson_solve(geo, T(P.omega), T(psi_b_for(P, geo)), T(P.psi_box), gm, pb, psi, ux, uy, None,
+                               opts=opts)
+    sh = (g.ny - 1, g.nx - 1)
+    out = {"psi": psi.cpu().numpy().reshape(sh), "psibar": pb.cpu().numpy(), "stats": st}
+    if velocity:
+        out["ux"] = ux.cpu().numpy().reshape(sh)
+        out["uy"] = uy.cpu().numpy().reshape(sh)
+    return out

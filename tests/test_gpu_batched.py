@@ -1,0 +1,74 @@
+"""Batched solves: every problem of a mixed-size batch gets exactly the result of its own
+single solve, and matches the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2109_13628_gb300 as iim
+from oracle import poisson as op
+from paper_2109_13628_gb300 import autotune, inputs
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+
+def build_batch(problems):
+    geos, args = [], {k: [] for k in ("omega", "psi_b", "gamma", "psibar", "psi")}
+    kept = []
+    for P in problems:
+        try:
+            geo = gu.setup(P)
+        except iim.IIMError:
+            continue                      # under-resolved draw: skipped like in the benchmark
+        kept.append(P)
+        geos.append(geo)
+        args["omega"].append(gu.T(P.omega.ravel()))
+        args["psi_b"].append(gu.T(gu.psi_b_for(P, geo)))
+        args["gamma"].append(gu.T(op.gamma_from_regions(P)))
+        args["psibar"].append(torch.zeros(len(P.regions), dtype=torch.float64, device=gu.dev()))
+        args["psi"].append(torch.empty(P.omega.size, dtype=torch.float64, device=gu.dev()))
+    return kept, geos, args
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_batched_equals_single_solves_and_oracle(precond):
+    problems = inputs.batched_c4(count=10, seed=5, sizes=(64, 128, 256))
+    kept, geos, a = build_batch(problems)
+    assert len(kept) >= 6
+    opts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-12, precond=precond)
+    st, stats = iim.iim_poisson_solve_batched(geos, a["omega"], a["psi_b"], None, a["gamma"], a["psibar"], a["psi"],
+                                              opts=opts, n_streams=4)
+    assert st == iim.IIM_OK
+    for k, (P, geo) in enumerate(zip(kept, geos)):
+        single = torch.empty_like(a["psi"][k])
+        pb = torch.zeros_like(a["psibar"][k])
+        iim.iim_poisson_solve(geo, a["omega"][k], a["psi_b"][k], None, a["gamma"][k], pb, single, opts=opts)
+        assert torch.equal(single, a["psi"][k])
+        assert stats[k]["rel_res"] < 1e-12
+    # oracle parity on the two smallest problems
+    for k in np.argsort([P.grid.nx for P in kept])[:2]:
+        P = kept[k]
+        ref, pb_ref = op.solve_unreduced(op.Setup(P), gamma=op.gamma_from_regions(P))
+        out = a["psi"][k].cpu().numpy().reshape(P.omega.shape)
+        fl = (P.phi >= 0)[1:-1, 1:-1]
+        assert np.abs(out - ref[1:-1, 1:-1])[fl].max() < 1e-8 * np.abs(ref).max()
+    for g in geos:
+        g.close()
+
+
+def test_autotuner_picks_supported_tiles():
+    problems = inputs.batched_c4(count=4, seed=7, sizes=(128, 256))
+    kept, geos, a = build_batch(problems)
+    opts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10)
+
+    def solve_one(k):
+        pb = torch.zeros_like(a["psibar"][k])
+        iim.iim_poisson_solve(geos[k], a["omega"][k], a["psi_b"][k], None, a["gamma"][k], pb, a["psi"][k], opts=opts)
+
+    best = autotune.tune_tiles(geos, solve_one)
+    assert set(best.values()) <= {2, 4, 8}
+    n_best, times = autotune.tune_streams(lambda c: iim.iim_poisson_solve_batched(
+        geos, a["omega"], a["psi_b"], None, a["gamma"], a["psibar"], a["psi"], opts=opts, n_streams=c), (1, 2, 4))
+    assert n_best in (1, 2, 4) and all(t > 0 for t in times.values())
+    for g in geos:
+        g.close()
