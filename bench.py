@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=8, help="independent problems in flight per step")
     ap.add_argument("--no-c4", action="store_true", help="skip the mixed-size batched workload")
     ap.add_argument("--c4-count", type=int, default=96)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess leg")
+    ap.add_argument("--no-rk3", action="store_true", help="skip the RK3 step leg")
     return ap.parse_args()
 
 
@@ -223,6 +225,125 @@ def c4_batch(iim, inputs, T, dev, count, seed, precond):
             list(ex.map(build, [order[w::nw] for w in range(nw)]))
     torch.cuda.synchronize()
     return kept, geos, om, pb, gm, pbar, out, time.perf_counter() - t0
+
+
+def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, eval_n=1024, eval_count=4):
+    """The learned initial guess: the net trained on the method's own solves (train_n^2, grid
+    symmetries as augmentation, time-bounded), evaluated on unseen eval_n^2 geometries against
+    the plain iteration (zero guess).  Guess time (body-free box solve, net input, forward,
+    composition) counts against the learned solve."""
+    import numpy as np
+    import torch
+    from paper_2109_13628_gb300 import learned
+    t0 = time.perf_counter()
+    data = learned.make_dataset(train_count, train_n, 1000, dev)
+    t_data = time.perf_counter() - t0
+    net = learned.Net(seed=5)
+    t0 = time.perf_counter()
+    losses = learned.train(net, data, epochs=1000, batch=8, lr=2e-3, time_budget_s=train_s)
+    t_train = time.perf_counter() - t0
+    del data
+    rows, seed = [], 90000
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    while len(rows) < eval_count and seed < 90000 + 8 * eval_count:
+        P = learned.training_problem(eval_n, seed)
+        seed += 1
+        g = P.grid
+        try:
+            geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions,
+                                         P.modes)
+        except iim.IIMError:
+            continue
+        om, pb, gm = T(P.omega.ravel()), T(np.zeros(geo.n_control)), T(learned.gamma_of(P))
+        out = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
+        pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
+        res = {}
+        for tag in ("zero", "learned", "zero", "learned"):   # second pass timed (first warms graphs)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            guess = None
+            if tag == "learned":
+                S = learned.Sample(P, dev)
+                guess = S.guess(net, dev)
+            st = iim.iim_poisson_solve(geo, om, pb, None, gm, pbar, out, psi_guess=guess,
+                                       opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10,
+                                                             guess=0 if guess is None else 2))
+            e1.record()
+            torch.cuda.synchronize()
+            res[tag] = (st["iters"], e0.elapsed_time(e1), st["seed_rel_res"], st["rel_res"])
+        rows.append(res)
+        geo.close()
+    net.close()
+    if not rows:
+        return None
+    mean = lambda tag, k: float(np.mean([r[tag][k] for r in rows]))
+    return {"config": f"train {train_count} method solves at {train_n}^2 (random 2-5 circles/ellipses, Gaussian "
+                      f"vortices; 8 grid symmetries), eval {len(rows)} unseen {eval_n}^2 geometries, mixed to 1e-10",
+            "train_s": t_train, "dataset_s": t_data, "loss_first": losses[0],
+            "loss_last": float(np.mean(losses[-10:])), "train_steps": len(losses),
+            "zero_guess": {"krylov_iters": mean("zero", 0), "ms_per_solve": mean("zero", 1),
+                           "solves_per_s": 1e3 / mean("zero", 1)},
+            "learned_guess": {"krylov_iters": mean("learned", 0), "ms_per_solve": mean("learned", 1),
+                              "solves_per_s": 1e3 / mean("learned", 1),
+                              "seed_rel_res_mean": mean("learned", 2),
+                              "max_rel_res": max(r["learned"][3] for r in rows)}}
+
+
+def rk3_c2(iim, inputs, dev, steps=3):
+    """One RK3 step of flow past a cylinder (1024 x 512, Re 200, CFL 0.5): the plain FP64 path
+    and the mixed path, each timed over `steps` steps from the same initial state."""
+    import numpy as np
+    import torch
+    P = inputs.c2_cylinder_flow(1024, 512)
+    g = P.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions, P.modes)
+    h = g.h
+    lx, rx, ly, ry = P.regions[0]
+    gam0 = np.array([h * h * P.omega[ly - 1:ry, lx - 1:rx].sum()])
+    inside = np.zeros(P.omega.shape, dtype=bool)
+    inside[ly - 1:ry, lx - 1:rx] = True
+    ring = T(P.psi_box)
+    w0d, g0d = T(P.omega.ravel()), T(gam0)
+    out = {}
+    # the geometry does not move, so the dense Schur preconditioner is built once for all steps
+    pc_ms = iim.iim_build_preconditioner(geo)
+    for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed", iim.IIM_MIXED, 0),
+                           ("mixed_precond", iim.IIM_MIXED, 1)):
+        w, gam, pbar = T(P.omega.ravel()), T(gam0), torch.zeros(1, dtype=torch.float64, device=dev)
+        opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc)
+
+        def step():
+            w.copy_(w0d)
+            gam.copy_(g0d)
+            pbar.zero_()
+            return iim.iim_rk3_step(geo, w, gam, pbar, None, None, ring, (1.0, 0.0), 0.005, 0.5, opts=opts)
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            dt, stats, _ = step()
+        e1.record()
+        torch.cuda.synchronize()
+        w1 = w.cpu().numpy().reshape(P.omega.shape)
+        kelvin = (gam.cpu().numpy().sum() + h * h * w1[~inside].sum()) - (gam0.sum() + h * h * P.omega[~inside].sum())
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps, "dt": dt,
+                     "krylov_iters_per_stage": [s["iters"] for s in stats],
+                     "circ_err_max": max(s["circ_err_max"] for s in stats),
+                     "kelvin_invariant_drift": float(abs(kelvin)), "omega": w1}
+    w64, w32, wpc = (out[k].pop("omega") for k in ("fp64", "mixed", "mixed_precond"))
+    geo.close()
+    rel = lambda a: float(np.abs(a - w64).max() / np.abs(w64).max())
+    return {"config": "flow past a cylinder R 0.5, [-2,6]x[-2,2], 1024 x 512, U 1, Re 200, CFL 0.5, noise 1e-3 seed 0",
+            **out, "precond_setup_ms": pc_ms, "mixed_vs_fp64_rel_linf": rel(w32),
+            "mixed_precond_vs_fp64_rel_linf": rel(wpc),
+            "speedup_mixed_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
+            "speedup_mixed_precond_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed_precond"]["ms_per_step"],
+            "kelvin_note": "box-wide invariant (Gamma + h^2 sum omega off the bodies' regions) also moves by the "
+                           "vorticity flux through the box edges"}
 
 
 def main():
@@ -421,6 +542,10 @@ def main():
               "krylov_iters_mean": statistics.mean(s["iters"] for o in couts for s in o)}
         for gg in cgeos:
             gg.close()
+    rk3 = None if args.no_rk3 else rk3_c2(iim, inputs, dev)
+    c5 = None
+    if not args.no_learned:
+        c5 = learned_c5(iim, dev, opts_for)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.n)
@@ -452,6 +577,8 @@ def main():
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched_c4": c4,
+        "learned_c5": c5,
+        "rk3_c2": rk3,
         "cpu_baseline": cpu,
     }
     if rank == 0:

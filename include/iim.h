@@ -72,7 +72,13 @@ typedef struct {
     int max_iter;      /* cap on Krylov iterations summed over refinements */
     int restart;       /* GMRES restart length, 1..64 */
     int max_refine;    /* cap on outer refinement steps */
-    int guess;         /* 0: start from psi = 0; 1: start from psi_guess */
+    int guess;         /* 0: start from psi = 0; 1: psi_guess is the first iterate (kept only if it
+                          lowers the un-reduced residual); 2: psi_guess seeds the Krylov unknowns
+                          of the first correction: the body constants psibar0_k it implies
+                          (quadratic extrapolation of psi_guess to the crossings, averaged per
+                          body) and x0 = c [A psi_guess + B sum_k psibar0_k 1_k ; psibar0] with
+                          the c that minimises ||b - S x0||, so ||b - S x0|| <= ||b||; dropped
+                          when c = 0 -- the learned-guess path */
     double inner_rtol; /* Krylov tolerance of each correction solve (<= 0: library default,
                           rtol/20 in FP64 mode, 1e-4 in mixed mode) */
     int precond;       /* 1: right-precondition GMRES with the dense inverse of the Schur matrix
@@ -88,6 +94,8 @@ typedef struct {
     double gmres_rel_res;/* last Krylov relative residual */
     double circ_err_max; /* max_k |Gamma_k - (-h sum_dRk grad_h psi . n)| over circulation bodies */
     float ms;            /* wall time of the call on the stream (CUDA events) */
+    double seed_rel_res; /* guess = 2: ||b - S x0|| / ||b|| of the seed of the first correction
+                            (1 without a seed) */
 } iim_stats;
 
 /* Geometry setup (Sec. 2.2, App. A): finds the control points (grid-line crossings of the
@@ -130,9 +138,12 @@ iim_status iim_geometry_affected_points(iim_geometry g, int* node_i, int* node_j
  *   psibar     n_bodies values: read for fixed bodies, written for circulation bodies
  *   psi_out    interior array: fluid values, 0 in the solid
  *   ux_out, uy_out  interior arrays (0 in the solid), or NULL to skip the velocity
- *   psi_guess  interior array used when opts->guess == 1, else ignored (may be NULL)
+ *   psi_guess  interior array used when opts->guess is 1 or 2, else ignored (may be NULL)
  *   opts       host; NULL = FP64, rtol 1e-10, restart 40, max_iter 2000, max_refine 8
  *   stats      host, may be NULL
+ * Refinement stops when the relative residual is <= rtol and, for circulation bodies, the
+ * circulation error max_k |Gamma_k - (-h sum_dRk grad_h psi . n)| is <= 1e-12 or stopped
+ * halving with the last correction (its rounding floor).
  * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_NONFINITE, IIM_ERR_NOT_CONVERGED (outputs still hold
  * the best iterate), IIM_ERR_CUDA.  Synchronizes `stream` (convergence tests read one scalar
  * per Krylov iteration).  Not re-entrant on one geometry: calls that share an iim_geometry
@@ -244,6 +255,47 @@ iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma, double* ps
                         const double* psi_b, const double* psi_box, const double Uinf[2], double nu,
                         double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
                         iim_stream stream);
+
+/* ---- Learned initial guess (no counterpart in the paper).  A fully convolutional network of
+ * 3x3 dilated convolutions (zero padding, ReLU between layers, BF16 weights, FP32 accumulation)
+ * maps per-pixel inputs to one output channel; trained with a masked mean-squared error and
+ * Adam by the library's own forward/backward kernels.  Tensors are device FP32 arrays of shape
+ * (batch, channels, height, width), row-major.  The solver judges every guess by its residual
+ * (iim_opts.guess = 1 falls back to zero when the guess raises it). */
+typedef struct iim_net_s* iim_net;
+
+/* Layers l = 0..n_layers-1: in_channels -> hidden -> ... -> hidden -> 1, dilation dilations[l]
+ * (host array); He-uniform weights from `seed`, zero biases.  in_channels, hidden <= 32. */
+iim_status iim_net_create(int in_channels, int hidden, int n_layers, const int* dilations,
+                          unsigned long long seed, iim_net* out);
+long long iim_net_num_params(iim_net net);
+/* FP32 parameters (host), per layer the weights (out, in, 3, 3) then the biases.  Setting them
+ * also resets the Adam state.  Errors: IIM_ERR_INVALID_ARG (size), IIM_ERR_CUDA. */
+iim_status iim_net_get_params(iim_net net, float* host, long long n);
+iim_status iim_net_set_params(iim_net net, const float* host, long long n);
+/* y (batch, 1, h, w) = net(x (batch, in_channels, h, w)).  Asynchronous. */
+iim_status iim_net_forward(iim_net net, int batch, int height, int width, const float* x, float* y,
+                           iim_stream stream);
+/* Gradient of sum(dy * net(x)) with respect to every parameter, copied to grad_host (host, may
+ * be NULL).  Synchronizes `stream` when grad_host is given. */
+iim_status iim_net_backward(iim_net net, int batch, int height, int width, const float* x, const float* dy,
+                            float* grad_host, iim_stream stream);
+/* One Adam step (beta 0.9 / 0.999) on loss = sum(mask (net(x) - target)^2) / sum(mask); mask
+ * may be NULL (all ones); the loss before the step goes to *loss (host, may be NULL; then the
+ * call is asynchronous). */
+iim_status iim_net_train_step(iim_net net, int batch, int height, int width, const float* x,
+                              const float* target, const float* mask, float lr, float* loss,
+                              iim_stream stream);
+/* Network input for a solve on an (nx x ny)-cell grid: three planes of the interior grid,
+ * omega * s_omega (0 in the solid), phi * s_phi (level set at the interior nodes of the node
+ * array phi_nodes) and u_box * s_box (the rectangular solve of omega, iim_box_poisson). */
+iim_status iim_net_prepare_input(int nx, int ny, const double* omega, const double* phi_nodes,
+                                 const double* u_box, float s_omega, float s_phi, float s_box, float* x,
+                                 iim_stream stream);
+/* psi_guess = u_box + y / s_out (n values). */
+iim_status iim_net_compose_guess(long long n, const double* u_box, const float* y, float s_out,
+                                 double* psi_guess, iim_stream stream);
+void iim_net_destroy(iim_net net);
 
 /* Number of kernels the library has launched in this process (all threads, all devices);
  * monotonic.  Lets a caller count the launches inside a timed region. */

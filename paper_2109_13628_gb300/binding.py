@@ -41,7 +41,7 @@ class iim_opts(ctypes.Structure):
 
 class iim_stats(ctypes.Structure):
     _fields_ = [("iters", _i), ("refinements", _i), ("fallback", _i), ("status", _i), ("rel_res", _d),
-                ("gmres_rel_res", _d), ("circ_err_max", _d), ("ms", ctypes.c_float)]
+                ("gmres_rel_res", _d), ("circ_err_max", _d), ("ms", ctypes.c_float), ("seed_rel_res", _d)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,6 +65,16 @@ SIGNATURES = [
     ("iim_poisson_solve_batched", _i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
                                        _vp, _i, _vp]),
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
+    ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
+    ("iim_net_num_params", ctypes.c_longlong, [_vp]),
+    ("iim_net_get_params", _i, [_vp, _vp, ctypes.c_longlong]),
+    ("iim_net_set_params", _i, [_vp, _vp, ctypes.c_longlong]),
+    ("iim_net_forward", _i, [_vp, _i, _i, _i, _vp, _vp, _vp]),
+    ("iim_net_backward", _i, [_vp, _i, _i, _i, _vp, _vp, _vp, _vp]),
+    ("iim_net_train_step", _i, [_vp, _i, _i, _i, _vp, _vp, _vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
+    ("iim_net_prepare_input", _i, [_i, _i, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp]),
+    ("iim_net_compose_guess", _i, [ctypes.c_longlong, _vp, _vp, ctypes.c_float, _vp, _vp]),
+    ("iim_net_destroy", None, [_vp]),
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
     ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
                           ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),

@@ -147,6 +147,7 @@ struct iim_geometry_s {
     double* H = nullptr;         // small Hessenberg / Givens storage
     double* xsol = nullptr;      // ns
     double* bvec = nullptr;      // ns
+    double* x0g = nullptr;       // ns: Krylov starting point from a guess
     int* d_int = nullptr;        // device counters / flags
     double* h_pinned = nullptr;  // pinned host scalars
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -339,7 +339,7 @@ __global__ void k_circ_measure(int nx, const double* __restrict__ psi, const iim
 }
 
 // small[] layout
-enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048 };
+enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048, SM_SEED = 2049 };
 constexpr int kRegionParts = 16;
 
 // Combines partial sums into *out_res2 = sum partial + sum rc^2 and, for circulation bodies,
@@ -594,6 +594,75 @@ __global__ void k_axpby(int n, double a, const double* __restrict__ x, double b,
 
 __global__ void k_set_int(int* __restrict__ p, int v) { *p = v; }
 
+__global__ void k_negate(int n, double* __restrict__ v) {
+    const int i = threadIdx.x;
+    if (i < n) v[i] = -v[i];
+}
+
+// Scales a Krylov seed to its best multiple: c = <b, S x0> / <S x0, S x0> minimises
+// ||b - c S x0||, which is then at most ||b||.  x0 and S x0 are scaled in place; out = c.
+// One block.
+template <int BLOCK>
+__global__ void k_seed_scale(int ns, const double* __restrict__ b, double* __restrict__ sx, double* __restrict__ x,
+                             double* __restrict__ out) {
+    __shared__ double c_sh;
+    double d = 0.0, q = 0.0;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) {
+        d += b[e] * sx[e];
+        q += sx[e] * sx[e];
+    }
+    d = block_sum<BLOCK>(d);
+    q = block_sum<BLOCK>(q);
+    if (threadIdx.x == 0) {
+        c_sh = q > 0.0 ? d / q : 0.0;
+        *out = c_sh;
+    }
+    __syncthreads();
+    const double c = c_sh;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) {
+        sx[e] *= c;
+        x[e] *= c;
+    }
+}
+
+// out[c] = sgn * mean over the control points of circulation body c of (psi extrapolated to the
+// crossing - psi_b): the quadratic through the fluid node and the next two fluid nodes on the
+// line, evaluated at the crossing (the fluid value alone when the run is shorter); one block
+// per body.  psi padded.
+template <int BLOCK>
+__global__ void k_psibar_estimate(int ncp, int nx, int ny, const int* __restrict__ axis, const int* __restrict__ ei,
+                                  const int* __restrict__ ej, const double* __restrict__ cp_t,
+                                  const int* __restrict__ cp_body, const int* __restrict__ body_circ,
+                                  const uint8_t* __restrict__ cls, const double* __restrict__ psi,
+                                  const double* __restrict__ psi_b, double* __restrict__ out, double sgn) {
+    const int c = blockIdx.x;
+    double s = 0.0, cnt = 0.0;
+    for (int k = threadIdx.x; k < ncp; k += BLOCK) {
+        if (body_circ[cp_body[k]] != c) continue;
+        const int i0 = ei[k], j0 = ej[k];
+        const bool ax = axis[k] == 0;
+        const int i1 = ax ? i0 + 1 : i0, j1 = ax ? j0 : j0 + 1;
+        const long p0 = (long)(j0 - 1) * nx + i0, p1 = (long)(j1 - 1) * nx + i1;   // padded indices
+        const bool lower_fluid = cls[p0] <= CLS_PLUS;
+        const long pf = lower_fluid ? p0 : p1;
+        const long step = (lower_fluid ? -1 : 1) * (ax ? 1L : (long)nx);   // from the solid node into the fluid
+        const int fi = lower_fluid ? i0 : i1, fj = lower_fluid ? j0 : j1;
+        const int di = ax ? (lower_fluid ? -1 : 1) : 0, dj = ax ? 0 : (lower_fluid ? -1 : 1);
+        const int i2 = fi + 2 * di, j2 = fj + 2 * dj;
+        double val = psi[pf];
+        if (i2 >= 1 && i2 <= nx - 1 && j2 >= 1 && j2 <= ny - 1 && cls[pf + step] <= CLS_PLUS && cls[pf + 2 * step] <= CLS_PLUS) {
+            const double t = -cp_t[k];   // the crossing sits at -t along the line (nodes at 0, 1, 2)
+            val = psi[pf] * (t - 1.0) * (t - 2.0) * 0.5 - psi[pf + step] * t * (t - 2.0) +
+                  psi[pf + 2 * step] * t * (t - 1.0) * 0.5;
+        }
+        s += val - (psi_b ? psi_b[k] : 0.0);
+        cnt += 1.0;
+    }
+    s = block_sum<BLOCK>(s);
+    cnt = block_sum<BLOCK>(cnt);
+    if (threadIdx.x == 0) out[c] = cnt > 0.0 ? sgn * s / cnt : 0.0;
+}
+
 __global__ void k_gmres_init(int* __restrict__ di, int maxit, double* __restrict__ K, KLayout L, const double* __restrict__ b2,
                              double tol) {
     di[DI_J] = 0;
@@ -836,9 +905,9 @@ struct Solver {
         return IIM_OK;
     }
 
-    // ---- restarted GMRES on S_aug x = b, x0 = 0
+    // ---- restarted GMRES on S_aug x = b, from x0 (when given and not worse than zero) or 0
     template <typename T>
-    iim_status gmres(double tol, int max_it) {
+    iim_status gmres(double tol, int max_it, const double* x0 = nullptr) {
         const int ns_ = ns;
         double* V = g->V;
         double* K = g->H;
@@ -850,8 +919,32 @@ struct Solver {
         launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0, nullptr,
                nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
         launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), max_it, K, L, g->small + SM_NORM, tol);
-        // V_0 = b / ||b|| (x0 = 0)
-        launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns_, g->bvec, V, L, K, kNormBlocks, g->partial, di());
+        bool started = false;
+        if (x0) {
+            // r0 = b - S x0 (the restart path); kept only when ||r0|| < ||b||
+            IIM_TRY(cudaMemcpyAsync(x, x0, (size_t)ns_ * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            IIM_TRY(cudaMemcpyAsync(V + ld, x0, (size_t)ns_ * sizeof(double), cudaMemcpyDeviceToDevice, s));
+            IIM_CHECK(restart_residual<T>(true));
+            IIM_TRY(cudaMemcpyAsync(g->h_pinned + 24, K + L.scal() + SC_BETA, sizeof(double), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaMemcpyAsync(g->h_pinned + 25, g->small + SM_NORM, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaStreamSynchronize(s));
+            const double beta = g->h_pinned[24], bnorm = std::sqrt(g->h_pinned[25]);
+            seed_scale = g->h_pinned[26];
+            seed_reduction = bnorm > 0.0 ? beta / bnorm : 1.0;
+            if (std::isfinite(beta) && beta < bnorm) {
+                started = true;
+            } else {
+                x0_fallback = 1;
+                IIM_TRY(cudaMemsetAsync(x, 0, (size_t)ns_ * sizeof(double), s));
+                launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), max_it, K, L, g->small + SM_NORM, tol);
+            }
+        }
+        if (!started) {
+            // V_0 = b / ||b|| (x0 = 0)
+            launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
+            launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns_, g->bvec, V, L, K, kNormBlocks, g->partial,
+                   di());
+        }
         IIM_LAUNCHED();
         IterGraph* G = nullptr;
         if (use_graph && !profiling_active()) {
@@ -902,15 +995,19 @@ struct Solver {
         return IIM_OK;
     }
 
-    // V_2 = S V_1 (V_1 holds x), then V_0 = (b - V_2) / ||b - V_2||
+    // V_2 = S V_1 (V_1 holds x), then V_0 = (b - V_2) / ||b - V_2||.  With `seed`, x and V_2
+    // are first scaled by the c that minimises ||b - c V_2|| (a Krylov seed from a guess).
     template <typename T>
-    iim_status restart_residual() {
+    iim_status restart_residual(bool seed = false) {
         const long ld = ns;
         double* V = g->V;
         double* K = g->H;
         const int eb = (ns + 255) / 256;
         launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 1);
         IIM_CHECK(apply_at<T>(DI_TMPJ, nullptr));
+        if (seed)
+            launch("seed_scale", 0.0, 0.0, k_seed_scale<1024>, 1, 1024, 0, s, ns, (const double*)g->bvec, V + 2 * ld,
+                   g->xsol, g->small + SM_SEED);
         launch("gmres_axpby", 0.0, 0.0, k_axpby, eb, 256, 0, s, ns, 1.0, g->bvec, -1.0, V + 2 * ld, V + 2 * ld);
         launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, V + 2 * ld, ns, g->partial);
         launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns, V + 2 * ld, V, L, K, kNormBlocks, g->partial,
@@ -920,20 +1017,48 @@ struct Solver {
     }
 
     template <typename T>
-    iim_status correction(double tol, int max_it) {
+    iim_status correction(double tol, int max_it, const double* x0 = nullptr) {
         IIM_CHECK(rhs<T>());
-        IIM_CHECK(gmres<T>(tol, max_it));
+        IIM_CHECK(gmres<T>(tol, max_it, x0));
         IIM_CHECK(recover<T>(g->xsol));
         return IIM_OK;
     }
+
+    // Krylov starting point from a streamfunction guess psi0: the body constants it implies,
+    // psibar0_k = mean over body k's control points of (psi0 at the adjacent fluid node - psi_b),
+    // and x0 = [A psi0 + B sum_k psibar0_k 1_k ; psibar0] (homogeneous data, as in the
+    // correction problems).
+    iim_status seed_from_guess(const double* psi_guess) {
+        const long npad = (long)g->nx * g->NY;
+        double* field = (double*)g->tbuf;
+        launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, psi_guess,
+               g->node_class, field);
+        IIM_TRY(cudaMemsetAsync(g->x0g, 0, (size_t)ns * sizeof(double), s));
+        if (g->ncirc > 0)
+            launch("psibar_estimate", 0.0, 0.0, k_psibar_estimate<128>, g->ncirc, 128, 0, s, g->ncp, g->nx, g->ny, g->cp_axis,
+                   g->cp_ei, g->cp_ej, (const double*)g->cp_t, g->cp_body, g->body_circ, g->node_class,
+                   (const double*)field, psi_b, g->x0g + g->na, -1.0);
+        const int nga = (g->na + 127) / 128;
+        if (g->na > 0)
+            launch("gather", 0.0, 0.0, k_gather<double, 128>, nga, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx, g->gop_w,
+                   (const double*)field, g->cp_body, g->body_circ, g->aff_body, VecArg{g->x0g, nullptr, 0, 0}, 1, g->x0g,
+                   nullptr, 0L, nullptr);
+        if (g->ncirc > 0)
+            launch("psibar_negate", 0.0, 0.0, k_negate, 1, 64, 0, s, g->ncirc, g->x0g + g->na);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
+    int x0_fallback = 0;
+    double seed_scale = 0.0, seed_reduction = 1.0;   // the seed's c and ||b - S c x0|| / ||b||
 };
 
 static iim_status ensure_krylov(iim_geometry g, int m) {
     const int ns = g->na + g->ncirc;
     if (g->V && g->krylov_m >= m) return IIM_OK;
-    cudaFree(g->V); cudaFree(g->H); cudaFree(g->xsol); cudaFree(g->bvec);
-    g->V = g->H = g->xsol = g->bvec = nullptr;
+    cudaFree(g->V); cudaFree(g->H); cudaFree(g->xsol); cudaFree(g->bvec); cudaFree(g->x0g);
+    g->V = g->H = g->xsol = g->bvec = g->x0g = nullptr;
     KLayout L{m};
+    IIM_TRY(cudaMalloc(&g->x0g, sizeof(double) * (size_t)std::max(ns, 1)));
     IIM_TRY(cudaMalloc(&g->V, sizeof(double) * (size_t)(m + 1) * std::max(ns, 1)));
     IIM_TRY(cudaMalloc(&g->H, sizeof(double) * (size_t)L.total()));
     IIM_TRY(cudaMalloc(&g->xsol, sizeof(double) * (size_t)std::max(ns, 1)));
@@ -973,7 +1098,8 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     if (opts.prec != IIM_FP64 && opts.prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
     if (opts.restart < 1 || opts.restart > 64 || !(opts.rtol > 0.0) || opts.max_iter < 1 || opts.max_refine < 1)
         return IIM_ERR_INVALID_ARG;
-    if (opts.guess == 1 && !psi_guess) return IIM_ERR_INVALID_ARG;
+    if ((opts.guess == 1 || opts.guess == 2) && !psi_guess) return IIM_ERR_INVALID_ARG;
+    if (opts.guess < 0 || opts.guess > 2) return IIM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
@@ -1020,10 +1146,27 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     double rel = fnorm > 0.0 ? std::sqrt(res2) / fnorm : 0.0;
     int refinements = 0;
     iim_status st = IIM_OK;
-    while (rel > opts.rtol) {
-        if (refinements >= opts.max_refine || S.iters >= opts.max_iter) { st = IIM_ERR_NOT_CONVERGED; break; }
+    const double* x0 = nullptr;
+    if (opts.guess == 2 && S.ns > 0) {
+        IIM_CHECK(S.seed_from_guess(psi_guess));
+        x0 = g->x0g;
+    }
+    // Refinement also goes on while the circulation constraint is off by more than kCircTol and
+    // the previous correction still halved that error (it stops at the rounding floor).
+    constexpr double kCircTol = 1e-12;
+    double cerr_prev = INFINITY;
+    auto circ_open = [&]() { return g->ncirc > 0 && cerr > kCircTol && cerr < 0.5 * cerr_prev; };
+    while (rel > opts.rtol || (refinements > 0 && circ_open())) {
+        if (refinements >= opts.max_refine || S.iters >= opts.max_iter) {
+            if (rel > opts.rtol) st = IIM_ERR_NOT_CONVERGED;
+            break;
+        }
+        cerr_prev = cerr;
         const int budget = opts.max_iter - S.iters;
-        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget) : S.correction<float>(inner, budget);
+        // the guess seeds the Krylov unknowns of the first correction only
+        const double* sx = refinements == 0 ? x0 : nullptr;
+        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget, sx)
+                                              : S.correction<float>(inner, budget, sx);
         if (cs != IIM_OK) { st = cs; break; }
         ++refinements;
         IIM_CHECK(S.residual(&res2, &cerr));
@@ -1040,11 +1183,12 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     if (stats) {
         stats->iters = S.iters;
         stats->refinements = refinements;
-        stats->fallback = fallback;
+        stats->fallback = fallback | S.x0_fallback;
         stats->status = st;
         stats->rel_res = rel;
         stats->gmres_rel_res = S.last_gmres_rel;
         stats->circ_err_max = cerr;
+        stats->seed_rel_res = S.seed_reduction;
         cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
     }
     return st;
