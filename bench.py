@@ -271,7 +271,7 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
                                                              guess=0 if guess is None else 2))
             e1.record()
             torch.cuda.synchronize()
-            res[tag] = (st["iters"], e0.elapsed_time(e1), st["seed_rel_res"], st["rel_res"])
+            res[tag] = (st["iters"], e0.elapsed_time(e1), st["seed_rel_res"], st["rel_res"], st["iters_first"])
         rows.append(res)
         geo.close()
     net.close()
@@ -282,9 +282,11 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
                       f"vortices; 8 grid symmetries), eval {len(rows)} unseen {eval_n}^2 geometries, mixed to 1e-10",
             "train_s": t_train, "dataset_s": t_data, "loss_first": losses[0],
             "loss_last": float(np.mean(losses[-10:])), "train_steps": len(losses),
-            "zero_guess": {"krylov_iters": mean("zero", 0), "ms_per_solve": mean("zero", 1),
+            "zero_guess": {"krylov_iters": mean("zero", 0), "first_correction_iters": mean("zero", 4),
+                           "ms_per_solve": mean("zero", 1),
                            "solves_per_s": 1e3 / mean("zero", 1)},
-            "learned_guess": {"krylov_iters": mean("learned", 0), "ms_per_solve": mean("learned", 1),
+            "learned_guess": {"krylov_iters": mean("learned", 0), "first_correction_iters": mean("learned", 4),
+                              "ms_per_solve": mean("learned", 1),
                               "solves_per_s": 1e3 / mean("learned", 1),
                               "seed_rel_res_mean": mean("learned", 2),
                               "max_rel_res": max(r["learned"][3] for r in rows)}}
@@ -420,6 +422,8 @@ def main():
                                   "refinements": st["refinements"], "rel_res": st["rel_res"]}))
         return
 
+    window = {}   # library launches before / inside the last timed region
+
     def timed(step, k, warm):
         for _ in range(warm):
             step()
@@ -428,6 +432,7 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
         ms, outs = [], []
+        window["before"] = iim.iim_launch_count()
         for _ in range(k):
             flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -437,6 +442,7 @@ def main():
             b.synchronize()
             ms.append(a.elapsed_time(b))
         torch.cuda.synchronize()
+        window["timed"] = iim.iim_launch_count() - window["before"]
         if ws > 1:
             torch.distributed.barrier()
         return ms, outs
@@ -455,10 +461,10 @@ def main():
         n_streams, tuned = autotune.tune_streams(solve_batch, tuple(c for c in (1, 2, 4, 8, 12, 16) if c <= B))
     # ---- chosen form: B problems per step in flight (the timed region), clocks sampled
     with ClockSampler(local) as clk:
-        l0 = iim.iim_launch_count()
         ms, outs = timed(lambda: solve_batch(n_streams)[1] if B > 1 else [solve(iim.IIM_MIXED)], args.steps,
                          args.warmup)
-        launches = iim.iim_launch_count() - l0
+        launches = window["timed"]
+        launch_window = dict(window)
     stats = [s for step_stats in outs for s in step_stats]
     total_ms = max_over_ranks(sum(ms))
     value = ws * B * args.steps / (total_ms * 1e-3)
@@ -574,6 +580,8 @@ def main():
         "kernels": [{"name": r["name"], "launches_per_step": r["launches"] / kprof, "ms_per_step": r["ms"] / kprof,
                      "share": r["ms"] / tot_k if tot_k else None} for r in kern[:12]],
         "gpu_launches": launches,
+        "launch_window": {"library_launches_before_timed": launch_window["before"],
+                          "library_launches_timed": launch_window["timed"]},
         "clocks": clk.summary(),
         "e2e": e2e,
         "batched_c4": c4,

@@ -96,6 +96,7 @@ typedef struct {
     float ms;            /* wall time of the call on the stream (CUDA events) */
     double seed_rel_res; /* guess = 2: ||b - S x0|| / ||b|| of the seed of the first correction
                             (1 without a seed) */
+    int iters_first;     /* Krylov iterations of the first correction (the one a seed starts) */
 } iim_stats;
 
 /* Geometry setup (Sec. 2.2, App. A): finds the control points (grid-line crossings of the

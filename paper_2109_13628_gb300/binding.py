@@ -41,7 +41,8 @@ class iim_opts(ctypes.Structure):
 
 class iim_stats(ctypes.Structure):
     _fields_ = [("iters", _i), ("refinements", _i), ("fallback", _i), ("status", _i), ("rel_res", _d),
-                ("gmres_rel_res", _d), ("circ_err_max", _d), ("ms", ctypes.c_float), ("seed_rel_res", _d)]
+                ("gmres_rel_res", _d), ("circ_err_max", _d), ("ms", ctypes.c_float), ("seed_rel_res", _d),
+                ("iters_first", _i)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

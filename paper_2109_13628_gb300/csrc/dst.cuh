@@ -335,13 +335,14 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
 // Column pass on padded columns p = 1..NX (p = 0 is the pad): forward y transform, division
 // by the eigenvalues (with the 2D normalisation), inverse y transform.  Rows outside [in0, in1]
 // are zero on input; only rows [out0, out1] are written back.  C columns per block, one warp
-// per column.
+// per column; blockIdx.y selects one of several fields fstride elements apart.
 template <typename T, int C>
 __global__ void __launch_bounds__(C * 32)
 k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
        const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
-       const int* __restrict__ stop) {
+       const int* __restrict__ stop, long fstride) {
     if (stop && *stop) return;
+    buf += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
@@ -416,12 +417,15 @@ enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2 };
 //   INV_STORE_T     outT (padded) = transform
 //   INV_STORE_F64   out64[r*old + ooff + i] = transform
 //   INV_ACCUM_FLUID out64 (padded) += transform at fluid nodes (class FLUID / PLUS) only
+// blockIdx.y selects one of several fields fstride elements apart (in and outT).
 template <typename T, int WARPS, int MODE>
 __global__ void __launch_bounds__(WARPS * 32)
 k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __restrict__ in, T* __restrict__ outT,
            double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
-           const cpx<T>* __restrict__ g_tw, const int* __restrict__ stop) {
+           const cpx<T>* __restrict__ g_tw, const int* __restrict__ stop, long fstride) {
     if (stop && *stop) return;
+    in += (long)blockIdx.y * fstride;
+    if (outT) outT += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

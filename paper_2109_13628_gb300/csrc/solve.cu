@@ -15,8 +15,9 @@
 // transforms; in mixed mode FP32 transforms (the refinement keeps the FP64 residual exact).
 //
 // One GMRES iteration is a fixed sequence of kernels that read the iteration index from
-// device memory and become no-ops once a device stop flag is set, so the sequence is captured
-// once as a CUDA graph and replayed; the host reads the convergence state once per batch.
+// device memory and become no-ops once a device stop flag is set.  The sequence is captured
+// once as the body of a WHILE conditional graph node, so a whole restart cycle runs on the
+// device from one graph launch; the host reads the convergence state once per cycle.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -148,38 +149,44 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
 
 template <typename T, int C>
 static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
-                            cudaStream_t s);
+                            cudaStream_t s, int batch, long fstride);
 
+// batch > 1: as many fields, fstride elements apart, in one launch
 template <typename T>
-static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s) {
+static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s,
+                       int batch = 1, long fstride = 0) {
     const int C = tile_width<T>(p.cols_c);
-    if (C == 8) return cols_tile<T, (sizeof(T) == 4 ? 8 : 4)>(p, in0, in1, out0, out1, buf, stop, s);
-    if (C == 2) return cols_tile<T, (sizeof(T) == 8 ? 2 : 4)>(p, in0, in1, out0, out1, buf, stop, s);
-    return cols_tile<T, 4>(p, in0, in1, out0, out1, buf, stop, s);
+    if (C == 8) return cols_tile<T, (sizeof(T) == 4 ? 8 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
+    if (C == 2) return cols_tile<T, (sizeof(T) == 8 ? 2 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
+    return cols_tile<T, 4>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
 }
 
 template <typename T, int C>
 static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
-                            cudaStream_t s) {
+                            cudaStream_t s, int batch, long fstride) {
     const size_t sm = cols_smem<T>(p.ny, C);
     allow_smem(k_cols<T, C>, sm);
-    launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32", (double)(in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
-           (double)p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), k_cols<T, C>, p.nx / C, C * 32, sm, s, p.NX, p.NY, p.ny,
-           p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop);
+    launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32",
+           (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
+           (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), k_cols<T, C>, dim3(p.nx / C, batch), C * 32,
+           sm, s, p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
     IIM_LAUNCHED();
     return IIM_OK;
 }
 
 template <typename T, int MODE>
 static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T* outT, double* out64, int old,
-                           int ooff, const uint8_t* cls, const int* stop, cudaStream_t s) {
+                           int ooff, const uint8_t* cls, const int* stop, cudaStream_t s, int batch = 1,
+                           long fstride = 0) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
     allow_smem(k_rows_inv<T, kRowWarps, MODE>, sm);
     launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
-           (double)nrows * p.NX * (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
-           (double)nrows * dst_flops(p.nx), k_rows_inv<T, kRowWarps, MODE>, (nrows + kRowWarps - 1) / kRowWarps,
-           kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw, stop);
+           (double)batch * nrows * p.NX *
+               (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
+           (double)batch * nrows * dst_flops(p.nx), k_rows_inv<T, kRowWarps, MODE>,
+           dim3((nrows + kRowWarps - 1) / kRowWarps, batch), kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0,
+           nrows, in, outT, out64, old, ooff, cls, p.tw, stop, fstride);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -256,6 +263,61 @@ k_gather(int na, int nga, const int* __restrict__ ptr, const int* __restrict__ i
             if (body_circ[aff_body[a]] == c) acc += v[a];
         acc = block_sum<BLOCK>(acc);
         if (threadIdx.x == 0) out[na + c] = acc;
+    }
+}
+
+// ---- columns of the Schur matrix for the dense preconditioner, many at once
+// Forward row transforms of unit vectors: field f holds 1 at affected point j0 + f, so its row
+// DST-I is sin(pi k s / n) (s = the point's slot in its padded row) on that row and 0 on the
+// other rows of [rmin, rmax].  The sines come from the same twiddle table as the transforms.
+template <typename T>
+__global__ void k_unit_rows(int nx, int logn, int rmin, int rmax, int j0, int na, const int* __restrict__ aff_node,
+                            const cpx<T>* __restrict__ g_tw, T* __restrict__ out, long fstride) {
+    const int f = blockIdx.y, a = j0 + f;
+    T* o = out + (long)f * fstride;
+    int prow = -1, slot = 0;
+    if (a < na) {
+        const int pn = aff_node[a];
+        prow = pn / nx;
+        slot = pn - prow * nx;
+    }
+    const int shift = kTwLog - logn;
+    const long total = (long)(rmax - rmin + 1) * nx;
+    for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int r = rmin + (int)(e / nx), k = (int)(e % nx);
+        T v = T(0);
+        if (r == prow && k > 0) {
+            const int m = (k * slot) & (2 * nx - 1);   // sin(pi m / n) has period 2n
+            const T sn = -g_tw[(m & (nx - 1)) << shift].y;
+            v = m >= nx ? -sn : sn;
+        }
+        o[(long)r * nx + k] = v;
+    }
+}
+
+// Column j0 + f of S (left half of the row-major augmented array A, leading dimension lda):
+// e_j + A (P E_a e_j) on the affected rows, then the circulation rows (sum over body c of e_j).
+// blockIdx.y = f; psi holds P E_a e_j of field f (padded, fields fstride apart).
+template <typename T, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_gather_unit(int na, int nga, int ncirc, const int* __restrict__ ptr, const int* __restrict__ idx,
+              const double* __restrict__ w, const T* __restrict__ psi, long fstride, int j0,
+              const int* __restrict__ aff_body, const int* __restrict__ body_circ, float* __restrict__ A, long lda) {
+    const int f = blockIdx.y, j = j0 + f;
+    if (j >= na) return;
+    if ((int)blockIdx.x < nga) {
+        const int a = blockIdx.x * BLOCK + threadIdx.x;
+        if (a >= na) return;
+        const T* ps = psi + (long)f * fstride;
+        double acc = (a == j) ? 1.0 : 0.0;
+        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+            const int q = idx[e];
+            if (q >= 0) acc += w[e] * (double)ps[q];
+        }
+        A[(long)a * lda + j] = (float)acc;
+    } else {
+        const int c = threadIdx.x;
+        if (c < ncirc) A[(long)(na + c) * lda + j] = (body_circ[aff_body[j]] == c) ? 1.f : 0.f;
     }
 }
 
@@ -423,7 +485,8 @@ __global__ void k_velocity(int NX, int NY, double inv2h, const double* __restric
 // Device state (int): [0] j (column of the current cycle), [1] stop, [2] iterations of this
 // call, [3] max iterations of this call, [4] converged, [5] scratch column index,
 // [32, 96) circulation body ids
-enum { DI_J = 0, DI_STOP = 1, DI_IT = 2, DI_MAXIT = 3, DI_CONV = 4, DI_TMPJ = 5, DI_CIRC = 32 };
+enum { DI_J = 0, DI_STOP = 1, DI_IT = 2, DI_MAXIT = 3, DI_CONV = 4, DI_TMPJ = 5, DI_LOOP = 6, DI_LOOPERR = 7,
+       DI_CIRC = 32 };
 
 // Krylov small-storage layout inside g->H (m <= 64):
 //   H (m+1) x m column-major | cs[m] | sn[m] | gv[m+1] | hc1[m+1] | hc2[m+1] | y[m] | scal[8]
@@ -671,10 +734,27 @@ __global__ void k_gmres_init(int* __restrict__ di, int maxit, double* __restrict
     di[DI_MAXIT] = maxit;
     di[DI_CONV] = 0;
     di[DI_TMPJ] = 0;
+    di[DI_LOOP] = 0;
+    di[DI_LOOPERR] = 0;
     K[L.scal() + SC_TOL] = tol * sqrt(*b2);
 }
 
 // ------------------------------------------------------------------------- solver
+// End of the body of the device-side GMRES loop (a WHILE conditional graph node): counts the
+// body's executions and ends the loop once the iteration kernels have set the stop flag.  The
+// cap (restart length + 2, never reached while the kernels follow their stopping rule) makes
+// the loop finite in any case; hitting it sets the stop flag and an error flag for the host.
+__global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* __restrict__ di, int cap) {
+    const int c = ++di[DI_LOOP];
+    if (!di[DI_STOP] && c >= cap) {
+        di[DI_STOP] = 1;
+        di[DI_LOOPERR] = 1;
+    }
+    if (di[DI_STOP]) cudaGraphSetConditional(h, 0);
+}
+
+// One GMRES cycle as a graph: a WHILE node whose body is one iteration (the captured kernel
+// sequence) plus k_loop_ctl; `nodes` = kernels per body execution.
 struct IterGraph {
     cudaGraphExec_t exec = nullptr;
     int prec = -1, m = 0, pc = 0;
@@ -700,7 +780,6 @@ struct Solver {
     bool precond = false;
     static constexpr int kResBlocks = 1024;
     static constexpr int kNormBlocks = 64;
-    static constexpr int kBatch = 6;   // graph replays between host convergence checks
 
     int* di() const { return g->d_int; }
 
@@ -773,9 +852,47 @@ struct Solver {
             IIM_TRY(cudaMalloc(&g->pc_z, sizeof(double) * 2 * (size_t)n));
         }
         IIM_TRY(cudaEventRecord(g->ev0, s));
+        // gamma columns j < |A|, K at a time: unit row transforms, column pass, inverse rows of
+        // the gathered band, gather straight into the matrix (one launch each per batch)
+        {
+            const long fstride = (long)g->nx * g->NY;
+            const size_t fbytes = sizeof(float) * (size_t)fstride;
+            const int K = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t(256) << 20) / (2 * fbytes)));
+            float* tb = nullptr;
+            IIM_TRY(cudaMalloc(&tb, 2 * fbytes * (size_t)K));
+            float* pt = tb + (size_t)K * fstride;
+            std::vector<int> row_of(g->na);
+            IIM_TRY(cudaMemcpyAsync(row_of.data(), g->aff_node, sizeof(int) * (size_t)g->na, cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaStreamSynchronize(s));
+            Plan<float> p = make_plan<float>(g);
+            const int nga = (g->na + 127) / 128;
+            iim_status bs = IIM_OK;
+            for (int j0 = 0; j0 < g->na && bs == IIM_OK; j0 += K) {
+                const int kb = std::min(K, g->na - j0);
+                const int rmin = row_of[j0] / g->nx, rmax = row_of[j0 + kb - 1] / g->nx;   // row-major order
+                const long cells = (long)(rmax - rmin + 1) * g->nx;
+                launch("pc_unit_rows", 0.0, 0.0, k_unit_rows<float>, dim3((unsigned)std::min<long>((cells + 255) / 256, 64), kb),
+                       256, 0, s, g->nx, ilog2(g->nx), rmin, rmax, j0, g->na, (const int*)g->aff_node, p.tw, tb, fstride);
+                bs = cols<float>(p, rmin, rmax, g->jo0, g->jo1, tb, nullptr, s, kb, fstride);
+                if (bs == IIM_OK)
+                    bs = rows_inv<float, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr,
+                                                      nullptr, s, kb, fstride);
+                if (bs == IIM_OK)
+                    launch("pc_gather", 0.0, 0.0, k_gather_unit<float, 128>, dim3(nga + 1, kb), 128, 0, s, g->na, nga,
+                           g->ncirc, (const int*)g->gop_ptr, (const int*)g->gop_idx, (const double*)g->gop_w,
+                           (const float*)pt, fstride, j0, (const int*)g->aff_body, (const int*)g->body_circ, g->pc_aug,
+                           2L * n);
+                if (bs == IIM_OK && cudaGetLastError() != cudaSuccess) bs = IIM_ERR_CUDA;
+            }
+            cudaError_t se = cudaStreamSynchronize(s);
+            cudaFree(tb);
+            if (bs != IIM_OK) return bs;
+            IIM_TRY(se);
+        }
+        // psibar columns: one operator application each
         launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 0);
         const int eb = (n + 255) / 256;
-        for (int j = 0; j < n; ++j) {
+        for (int j = g->na; j < n; ++j) {
             launch("pc_unit", 0.0, 0.0, k_unit_vector, eb, 256, 0, s, n, j, g->V);
             IIM_CHECK(apply_at<float>(DI_TMPJ, nullptr));
             launch("pc_column", 0.0, 0.0, k_store_column, eb, 256, 0, s, n, j, (const double*)(g->V + ld), g->pc_aug);
@@ -836,23 +953,48 @@ struct Solver {
         cudaGraph_t graph = nullptr;
         const cudaStream_t user = s;
         IIM_TRY(cudaStreamSynchronize(user));
+        IIM_TRY(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle h;
+        cudaGraphNodeParams cp = {};
+        cudaGraphNode_t cn = nullptr;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&cn, graph, nullptr, nullptr, 0, &cp);
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            record_cuda_error(e, "conditional graph node", __FILE__, __LINE__);
+            return IIM_ERR_CUDA;
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
         s = g->cap_stream;
         set_capture(true);
-        cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             set_capture(false);
             s = user;
-            record_cuda_error(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+            cudaGraphDestroy(graph);
+            record_cuda_error(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
             return IIM_ERR_CUDA;
         }
         iim_status st = iteration<T>();
-        e = cudaStreamEndCapture(s, &graph);
+        launch("gmres_loop_ctl", 0.0, 0.0, k_loop_ctl, 1, 1, 0, s, h, di(), m + 2);
+        cudaGraph_t captured = nullptr;
+        e = cudaStreamEndCapture(s, &captured);
         set_capture(false);
         s = user;
-        if (st != IIM_OK) { if (graph) cudaGraphDestroy(graph); return st; }
-        if (e != cudaSuccess) { record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__); return IIM_ERR_CUDA; }
+        if (st != IIM_OK || e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            if (st != IIM_OK) return st;
+            record_cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+            return IIM_ERR_CUDA;
+        }
         size_t nn = 0;
-        cudaGraphGetNodes(graph, nullptr, &nn);
+        cudaGraphGetNodes(body, nullptr, &nn);
         e = cudaGraphInstantiate(&G.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) { G.exec = nullptr; record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); return IIM_ERR_CUDA; }
@@ -961,14 +1103,19 @@ struct Solver {
             // one cycle: iterate until the device stop flag is set
             while (!st[DI_STOP]) {
                 if (G) {
-                    for (int b = 0; b < kBatch; ++b) {
-                        IIM_TRY(cudaGraphLaunch(G->exec, s));
-                        count_launches(G->nodes);
+                    // the whole cycle on the device: the WHILE node iterates until the stop flag
+                    launch("set_loop", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_LOOP, 0);
+                    IIM_TRY(cudaGraphLaunch(G->exec, s));
+                    IIM_CHECK(read_state(st));
+                    count_launches((long long)st[DI_LOOP] * G->nodes);
+                    if (st[DI_LOOPERR]) {
+                        snprintf(g_last_error, sizeof(g_last_error), "GMRES loop ended by its iteration cap");
+                        return IIM_ERR_NOT_CONVERGED;
                     }
                 } else {
                     IIM_CHECK(iteration<T>());
+                    IIM_CHECK(read_state(st));
                 }
-                IIM_CHECK(read_state(st));
             }
             launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
             if (precond) {
@@ -1155,6 +1302,7 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     // the previous correction still halved that error (it stops at the rounding floor).
     constexpr double kCircTol = 1e-12;
     double cerr_prev = INFINITY;
+    int iters_first = 0;
     auto circ_open = [&]() { return g->ncirc > 0 && cerr > kCircTol && cerr < 0.5 * cerr_prev; };
     while (rel > opts.rtol || (refinements > 0 && circ_open())) {
         if (refinements >= opts.max_refine || S.iters >= opts.max_iter) {
@@ -1165,9 +1313,13 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         const int budget = opts.max_iter - S.iters;
         // the guess seeds the Krylov unknowns of the first correction only
         const double* sx = refinements == 0 ? x0 : nullptr;
-        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget, sx)
-                                              : S.correction<float>(inner, budget, sx);
+        // a correction made only for the circulation rows needs three digits, not the full
+        // inner tolerance
+        const double tol_k = rel > opts.rtol ? inner : std::max(inner, 1e-3);
+        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(tol_k, budget, sx)
+                                              : S.correction<float>(tol_k, budget, sx);
         if (cs != IIM_OK) { st = cs; break; }
+        if (refinements == 0) iters_first = S.iters;
         ++refinements;
         IIM_CHECK(S.residual(&res2, &cerr));
         if (!std::isfinite(res2)) { st = IIM_ERR_NONFINITE; break; }
@@ -1189,6 +1341,7 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         stats->gmres_rel_res = S.last_gmres_rel;
         stats->circ_err_max = cerr;
         stats->seed_rel_res = S.seed_reduction;
+        stats->iters_first = iters_first;
         cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
     }
     return st;

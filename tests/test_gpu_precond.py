@@ -42,5 +42,6 @@ def test_preconditioned_c1_1024_to_1e10():
     out = gu.solve_opts(P, geo, opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10, precond=1))
     nodes = gu.nodes_from_interior(P, out["psi"])
     assert op.residual(S, nodes, out["psibar"]) < 1e-10
+    assert out["stats"]["iters"] <= 16, out["stats"]   # plain GMRES needs about 100 here
     assert out["stats"]["iters"] < 20, out["stats"]
     geo.close()
