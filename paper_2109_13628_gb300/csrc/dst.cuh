@@ -98,6 +98,43 @@ __device__ __forceinline__ void dft<float, 8>(cpx<float>* v) { dft8_impl(v); }
 template <>
 __device__ __forceinline__ void dft<double, 8>(cpx<double>* v) { dft8_impl(v); }
 
+// 16-point DFT as 4 x 4: 4-point DFTs over the stride-4 subsets, twiddles W16^(b k), 4-point
+// DFTs across them.  Natural order in and out.
+template <typename T>
+__device__ __forceinline__ void dft16_impl(cpx<T>* v) {
+    const T c = T(0.92387953251128675613), s = T(0.38268343236508977173), r = T(0.70710678118654752440);
+    cpx<T> t[16];
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        cpx<T> u[4] = {v[b], v[4 + b], v[8 + b], v[12 + b]};
+        dft4_impl(u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) t[4 * b + k] = u[k];
+    }
+    // W16^j = exp(-2 pi i j / 16) for the products j = b k that occur: 1, 2, 3, 4, 6, 9
+    const cpx<T> w1 = {c, -s}, w2 = {r, -r}, w3 = {s, -c}, w6 = {-r, -r}, w9 = {-c, s};
+    t[5] = cmul(t[5], w1);
+    t[6] = cmul(t[6], w2);
+    t[7] = cmul(t[7], w3);
+    t[9] = cmul(t[9], w2);
+    t[10] = cmi(t[10]);
+    t[11] = cmul(t[11], w6);
+    t[13] = cmul(t[13], w3);
+    t[14] = cmul(t[14], w6);
+    t[15] = cmul(t[15], w9);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        cpx<T> u[4] = {t[k], t[4 + k], t[8 + k], t[12 + k]};
+        dft4_impl(u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[k + 4 * q] = u[q];
+    }
+}
+template <>
+__device__ __forceinline__ void dft<float, 16>(cpx<float>* v) { dft16_impl(v); }
+template <>
+__device__ __forceinline__ void dft<double, 16>(cpx<double>* v) { dft16_impl(v); }
+
 // Packed FFT input c_m = y_{2m} + i y_{2m+1} from the line x (x_0 = x_n = 0).
 template <typename T>
 __device__ __forceinline__ cpx<T> packed(const T* x, const cpx<T>* tw, int n, int m) {
@@ -112,56 +149,85 @@ __device__ __forceinline__ cpx<T> packed(const T* x, const cpx<T>* tw, int n, in
     return {y0, y1};
 }
 
-// One Stockham radix-R pass of an M-point FFT: in -> out (out-of-place).  With `x` given the
-// input values are the packed line instead of `in`.
+// Shared-memory layout of the complex FFT work arrays: inside every 128-byte block the entry
+// index is XOR-ed with the block number, so that the strided stores of a radix pass and the
+// reads of the next pass fall into distinct banks.  A bijection on [0, M) for M >= 16.
+template <typename T>
+__device__ __forceinline__ int swz(int i) {
+    return sizeof(T) == 4 ? (i ^ ((i >> 4) & 15)) : (i ^ ((i >> 3) & 7));
+}
+
+// Radix of each Stockham pass of an M-point FFT (M = 2^logM): 8 while at least three factors
+// of two remain, then 4 or 2.
+__device__ __forceinline__ int pass_radix(int rem) { return rem >= 3 ? 8 : (rem == 2 ? 4 : 2); }
+
+// Per-pass twiddle tables.  The pass with stride Ns > 1 and radix R multiplies value r of
+// butterfly k by exp(-2 pi i k r / (Ns R)); its table holds these for r = 1..R-1, k < Ns at
+// [(r - 1) Ns + k] (consecutive k for one r: conflict-free reads), the passes' tables one after
+// another (fewer than M entries in all).
+template <typename T>
+__device__ __forceinline__ cpx<T> pass_twiddle_entry(const cpx<T>* __restrict__ g_tw, int n, int logn, int e,
+                                                     bool& valid) {
+    const int M = n >> 1;
+    int rem = logn - 1, Ns = 1, off = 0;
+    valid = false;
+    while (rem > 0) {
+        const int R = pass_radix(rem);
+        if (Ns > 1) {
+            const int size = (R - 1) * Ns;
+            if (e < off + size) {
+                const int q = e - off, r = q / Ns + 1, k = q - (r - 1) * Ns;
+                const int t = ((4 * M) / (Ns * R)) * k * r;   // exp(-i pi t / n), t < 2n
+                const int shift = kTwLog - logn;
+                const cpx<T> w = g_tw[(t & (n - 1)) << shift];
+                valid = true;
+                return t >= n ? cpx<T>{-w.x, -w.y} : w;
+            }
+            off += size;
+        }
+        Ns *= R;
+        rem -= (R == 8 ? 3 : R == 4 ? 2 : 1);
+    }
+    return cpx<T>{T(0), T(0)};
+}
+
+// One Stockham radix-R pass of an M-point FFT: in -> out (out-of-place, swizzled layout).
+// With `x` given the input values are the packed line (natural layout) instead of `in`.
 template <typename T, int R>
-__device__ __forceinline__ void stockham_pass(const cpx<T>* in, const T* x, cpx<T>* out, const cpx<T>* tw, int n,
-                                              int M, int Ns, int lane) {
+__device__ __forceinline__ void stockham_pass(const cpx<T>* in, const T* x, cpx<T>* out, const cpx<T>* tw,
+                                              const cpx<T>* ptw, int n, int M, int Ns, int lane) {
     const int J = M / R;
-    const int tstep = (4 * M) / (Ns * R);
     for (int j = lane; j < J; j += 32) {
         cpx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = x ? packed(x, tw, n, j + r * J) : in[j + r * J];
+        for (int r = 0; r < R; ++r) v[r] = x ? packed(x, tw, n, j + r * J) : in[swz<T>(j + r * J)];
         const int k = j & (Ns - 1);
         if (Ns > 1) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw_full(tw, tstep * k * r, n));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], ptw[(r - 1) * Ns + k]);
         }
         dft<T, R>(v);
         const int idx = (j - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) out[idx + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) out[swz<T>(idx + r * Ns)] = v[r];
     }
     __syncwarp();
 }
 
-// DST-I of the line held in buf0[1..n-1] (buf0[0] ignored), with buf1 (n values) as scratch.
-// tw[k] = exp(-i pi k / n), k < n.  Returns the buffer holding the result in [1..n-1].
+// Lines whose half-length FFT has M = 32 P points with P = 8 or 16 use a register-resident
+// FFT: M = P x 32 with the P-point DFTs in registers (lane l holds the samples l + 32 p), the
+// twiddles W_M^(l k), one transpose through shared memory, P-point DFTs again and a
+// (32 / P)-point DFT across the lanes of each group.  Other sizes use the Stockham passes.
+__host__ __device__ constexpr bool reg_fft(int n) { return n == 512 || n == 1024; }
+__host__ __device__ constexpr int fft_path(int n) { return n == 1024 ? 16 : n == 512 ? 8 : 0; }
+
+// Split step of the real FFT and the prefix sum of the odd outputs (see the file header): C
+// (swizzled, M values) -> dst (natural layout, X_k at index k).
 template <typename T>
-__device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int lane) {
-    const int M = n >> 1;
-    const int logM = logn - 1;
-    // FFT passes: radix 8 while possible, then 4 or 2
-    T* src = buf0;
-    T* dst = buf1;
-    int Ns = 1, rem = logM;
-    bool first = true;
-    while (rem > 0) {
-        const cpx<T>* in = reinterpret_cast<const cpx<T>*>(src);
-        cpx<T>* out = reinterpret_cast<cpx<T>*>(dst);
-        const T* px = first ? src : nullptr;
-        if (rem >= 3) { stockham_pass<T, 8>(in, px, out, tw, n, M, Ns, lane); Ns *= 8; rem -= 3; }
-        else if (rem == 2) { stockham_pass<T, 4>(in, px, out, tw, n, M, Ns, lane); Ns *= 4; rem -= 2; }
-        else { stockham_pass<T, 2>(in, px, out, tw, n, M, Ns, lane); Ns *= 2; rem -= 1; }
-        first = false;
-        T* t = src; src = dst; dst = t;
-    }
-    // src holds C_k (natural order); split step into dst
-    const cpx<T>* C = reinterpret_cast<const cpx<T>*>(src);
+__device__ __forceinline__ void dst_finish(const cpx<T>* C, T* dst, const cpx<T>* tw, int M, int lane) {
     for (int k = lane; k < M; k += 32) {
-        const cpx<T> ck = C[k];
-        const cpx<T> cm = C[k == 0 ? 0 : M - k];
+        const cpx<T> ck = C[swz<T>(k)];
+        const cpx<T> cm = C[swz<T>(k == 0 ? 0 : M - k)];
         const T ex = T(0.5) * (ck.x + cm.x), ey = T(0.5) * (ck.y - cm.y);
         const T dx = T(0.5) * (ck.x - cm.x), dy = T(0.5) * (ck.y + cm.y);
         const cpx<T> w = tw[2 * k];
@@ -170,7 +236,6 @@ __device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int 
         reinterpret_cast<cpx<T>*>(dst)[k] = cpx<T>{k == 0 ? T(0) : -yy, k == 0 ? T(0.5) * yx : yx};
     }
     __syncwarp();
-    // odd outputs: inclusive prefix sum of dst[2m+1], m = 0..M-1, 32 values per step
     T carry = T(0);
     for (int base = 0; base < M; base += 32) {
         const int m = base + lane;
@@ -185,11 +250,104 @@ __device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int 
         carry = __shfl_sync(0xffffffffu, v, 31);
     }
     __syncwarp();
+}
+
+template <typename T>
+__device__ __forceinline__ cpx<T> shfl_cpx(cpx<T> v, int src) {
+    return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
+}
+
+// Register-path DST-I (P = 8 or 16, n = 64 P).  rtw = tw + n: [k * 32 + l] = W_M^(l k) for
+// k < P, then W_32^j, j < 32.  buf1 is the transpose buffer, C goes to buf0; returns buf1.
+template <typename T, int P>
+__device__ __forceinline__ T* dst1_warp_reg(T* buf0, T* buf1, const cpx<T>* tw, int n, int lane) {
+    constexpr int M = 32 * P;
+    constexpr int G = 32 / P;   // lanes per 32-point DFT in the second stage
+    const cpx<T>* rtw = tw + n;
+    const cpx<T>* w32 = rtw + M;
+    cpx<T> v[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) v[p] = packed(buf0, tw, n, 32 * p + lane);
+    dft<T, P>(v);
+#pragma unroll
+    for (int k = 1; k < P; ++k) v[k] = cmul(v[k], rtw[k * 32 + lane]);
+    cpx<T>* sc = reinterpret_cast<cpx<T>*>(buf1);
+#pragma unroll
+    for (int k = 0; k < P; ++k) sc[swz<T>(k * 32 + lane)] = v[k];
+    __syncwarp();
+    const int k1 = lane / G, h = lane - k1 * G;
+#pragma unroll
+    for (int l1 = 0; l1 < P; ++l1) v[l1] = sc[swz<T>(k1 * 32 + G * l1 + h)];
+    dft<T, P>(v);
+    if (h) {
+#pragma unroll
+        for (int q = 1; q < P; ++q) v[q] = cmul(v[q], w32[(h * q) & 31]);
+    }
+    // G-point DFT across the group's lanes; lane h keeps output h
+    const int gb = lane - h;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        if (G == 2) {
+            const cpx<T> o = shfl_cpx(v[q], lane ^ 1);
+            v[q] = h ? csub(o, v[q]) : cadd(v[q], o);
+        } else {
+            cpx<T> u[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[j] = shfl_cpx(v[q], gb + j);
+            dft4_impl(u);
+            v[q] = h == 0 ? u[0] : h == 1 ? u[1] : h == 2 ? u[2] : u[3];
+        }
+    }
+    cpx<T>* C = reinterpret_cast<cpx<T>*>(buf0);
+#pragma unroll
+    for (int q = 0; q < P; ++q) C[swz<T>(k1 + P * q + P * P * h)] = v[q];
+    __syncwarp();
+    dst_finish(C, buf1, tw, M, lane);
+    return buf1;
+}
+
+// DST-I of the line held in buf0[1..n-1] (buf0[0] ignored), with buf1 (n values) as scratch.
+// tw[k] = exp(-i pi k / n), k < n; tw + n holds the register-path or per-pass tables.  Returns
+// the buffer holding the result in [1..n-1] (natural layout).
+// FP = 16 or 8 selects the register path (n = 1024 or 512), FP = 0 the Stockham passes; the
+// kernels are instantiated per path so that each holds the code of one path only.
+template <typename T, int FP>
+__device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int lane) {
+    if constexpr (FP != 0) return dst1_warp_reg<T, FP>(buf0, buf1, tw, n, lane);
+    const int M = n >> 1;
+    const int logM = logn - 1;
+    const cpx<T>* ptw = tw + n;
+    // FFT passes: radix 8 while possible, then 4 or 2
+    T* src = buf0;
+    T* dst = buf1;
+    int Ns = 1, rem = logM;
+    bool first = true;
+    while (rem > 0) {
+        const cpx<T>* in = reinterpret_cast<const cpx<T>*>(src);
+        cpx<T>* out = reinterpret_cast<cpx<T>*>(dst);
+        const T* px = first ? src : nullptr;
+        const int R = pass_radix(rem);
+        if (R == 8) stockham_pass<T, 8>(in, px, out, tw, ptw, n, M, Ns, lane);
+        else if (R == 4) stockham_pass<T, 4>(in, px, out, tw, ptw, n, M, Ns, lane);
+        else stockham_pass<T, 2>(in, px, out, tw, ptw, n, M, Ns, lane);
+        if (Ns > 1) ptw += (R - 1) * Ns;
+        Ns *= R;
+        rem -= (R == 8 ? 3 : R == 4 ? 2 : 1);
+        first = false;
+        T* t = src; src = dst; dst = t;
+    }
+    // src holds C_k (swizzled); split step into dst (natural layout)
+    dst_finish(reinterpret_cast<const cpx<T>*>(src), dst, tw, M, lane);
     return dst;
 }
 
-// Copies exp(-i pi k / n), k < n, from the 4096-entry table into shared memory; the loads of
-// one thread are issued back to back (batches of 8) before their shared-memory stores.
+// Complex entries of the shared-memory twiddle region for lines of n points: the full table
+// exp(-i pi k / n), k < n, then the register-path tables (n / 2 + 32 entries) or the per-pass
+// tables (fewer than n / 2 entries).
+__host__ __device__ constexpr int tw_region(int n) { return n + n / 2 + 32; }
+
+// Fills the twiddle region from the 4096-entry table; the loads of one thread are issued back
+// to back (batches of 8) before their shared-memory stores.
 template <typename T>
 __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, int n, int logn) {
     const int stride_shift = kTwLog - logn;
@@ -205,6 +363,21 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, 
         for (int b = 0; b < 8; ++b) {
             const int k = k0 + b * nt;
             if (k < n) s_tw[k] = v[b];
+        }
+    }
+    if (reg_fft(n)) {
+        // W_M^(l k) at [k * 32 + l] (M = n / 2), then W_32^j
+        const int M = n >> 1;
+        for (int e = threadIdx.x; e < M + 32; e += nt) {
+            const int t = e < M ? (4 * (e & 31) * (e >> 5)) % (2 * n) : (e - M) * (n / 16);
+            const cpx<T> w = g_tw[(t & (n - 1)) << stride_shift];
+            s_tw[n + e] = t >= n ? cpx<T>{-w.x, -w.y} : w;
+        }
+    } else {
+        for (int e = threadIdx.x; e < n / 2; e += nt) {
+            bool valid;
+            const cpx<T> w = pass_twiddle_entry(g_tw, n, logn, e, valid);
+            if (valid) s_tw[n + e] = w;
         }
     }
 }
@@ -280,7 +453,7 @@ struct VecArg {
 //   + gsign * gamma at the affected points of the row (optional)
 // and the transformed row is written to out (padded layout).  `stop` (optional): a set flag
 // makes the launch a no-op.
-template <typename T, int WARPS>
+template <typename T, int WARPS, int FP>
 __global__ void __launch_bounds__(WARPS * 32)
 k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
            const double* __restrict__ ring, double ih2, const int* __restrict__ aff_row_ptr,
@@ -290,7 +463,7 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* b0 = reinterpret_cast<T*>(s_tw + n) + (size_t)warp * (2 * n);
+    T* b0 = reinterpret_cast<T*>(s_tw + tw_region(n)) + (size_t)warp * (2 * n);
     T* b1 = b0 + n;
     load_twiddles(s_tw, g_tw, n, logn);
     __syncthreads();
@@ -326,7 +499,7 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
         for (int a = a0 + lane; a < a1; a += 32) b0[aff_node[a] - r * n] += (T)(gsign * gv[a]);
         __syncwarp();
     }
-    T* res = dst1_warp(b0, b1, s_tw, n, logn, lane);
+    T* res = dst1_warp<T, FP>(b0, b1, s_tw, n, logn, lane);
     if (lane == 0) res[0] = T(0);
     __syncwarp();
     store_row_vec(out + (size_t)r * n, res, n, lane);
@@ -336,7 +509,7 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
 // by the eigenvalues (with the 2D normalisation), inverse y transform.  Rows outside [in0, in1]
 // are zero on input; only rows [out0, out1] are written back.  C columns per block, one warp
 // per column; blockIdx.y selects one of several fields fstride elements apart.
-template <typename T, int C>
+template <typename T, int C, int FP>
 __global__ void __launch_bounds__(C * 32)
 k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
        const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
@@ -347,11 +520,13 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
     const int stride = 2 * n + PAD;
-    T* lines = reinterpret_cast<T*>(s_tw + n);
+    T* s_lam = reinterpret_cast<T*>(s_tw + tw_region(n));   // lam_y, NY values
+    T* lines = s_lam + n;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ld = NX + 1;
     const int col0 = blockIdx.x * C;   // padded column index
     load_twiddles(s_tw, g_tw, n, logn);
+    for (int l = threadIdx.x; l < NY; l += C * 32) s_lam[l] = lam_y[l];
     // tile load: C consecutive padded columns of rows [in0, in1]; rows outside are zero
     constexpr int V = 16 / sizeof(T);
     constexpr int VPR = C / V;                   // vectors per row
@@ -385,12 +560,21 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
     if (p >= 1 && p <= NX) {
         T* b0 = lines + warp * stride;
         T* b1 = b0 + n;
-        T* f = dst1_warp(b0, b1, s_tw, n, logn, lane);
+        // forward transform, division, inverse transform: one copy of the transform code
+        T* in = b0;
+        T* other = b1;
         const T lx = lam_x[p - 1];
-        for (int l = lane; l < NY; l += 32) f[l + 1] = f[l + 1] * (norm / (lx + lam_y[l]));
-        __syncwarp();
-        T* other = (f == b0) ? b1 : b0;
-        resline = dst1_warp(f, other, s_tw, n, logn, lane);
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            T* f = dst1_warp<T, FP>(in, other, s_tw, n, logn, lane);
+            if (pass == 0) {
+                for (int l = lane; l < NY; l += 32) f[l + 1] = f[l + 1] * (norm / (lx + s_lam[l]));
+                __syncwarp();
+            }
+            other = (f == in) ? other : in;
+            in = f;
+        }
+        resline = in;
         // bring the result back to b0 so that the tile store below has a fixed layout
         if (resline != b0) {
             for (int l = lane; l < NY; l += 32) b0[l + 1] = resline[l + 1];
@@ -418,7 +602,7 @@ enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2 };
 //   INV_STORE_F64   out64[r*old + ooff + i] = transform
 //   INV_ACCUM_FLUID out64 (padded) += transform at fluid nodes (class FLUID / PLUS) only
 // blockIdx.y selects one of several fields fstride elements apart (in and outT).
-template <typename T, int WARPS, int MODE>
+template <typename T, int WARPS, int MODE, int FP>
 __global__ void __launch_bounds__(WARPS * 32)
 k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __restrict__ in, T* __restrict__ outT,
            double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
@@ -429,7 +613,7 @@ k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* b0 = reinterpret_cast<T*>(s_tw + n) + (size_t)warp * (2 * n);
+    T* b0 = reinterpret_cast<T*>(s_tw + tw_region(n)) + (size_t)warp * (2 * n);
     T* b1 = b0 + n;
     load_twiddles(s_tw, g_tw, n, logn);
     __syncthreads();
@@ -437,7 +621,7 @@ k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __rest
     if (r >= row0 + nrows || r >= NY) return;
     load_row_vec(b0, in + (size_t)r * n, n, lane);
     __syncwarp();
-    T* res = dst1_warp(b0, b1, s_tw, n, logn, lane);
+    T* res = dst1_warp<T, FP>(b0, b1, s_tw, n, logn, lane);
     if (MODE == INV_STORE_T) {
         if (lane == 0) res[0] = T(0);
         __syncwarp();

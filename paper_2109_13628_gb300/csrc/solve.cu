@@ -100,11 +100,13 @@ constexpr int cols_per_block() { return 4; }
 constexpr int kRowWarps = 4;
 
 template <typename T>
-static size_t rows_smem(int n) { return (size_t)n * sizeof(cpx<T>) + (size_t)kRowWarps * 2 * n * sizeof(T); }
+static size_t rows_smem(int n) {
+    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)kRowWarps * 2 * n * sizeof(T);
+}
 template <typename T>
 static size_t cols_smem(int n, int C = cols_per_block<T>()) {
     const int pad = sizeof(T) == 4 ? 4 : 2;
-    return (size_t)n * sizeof(cpx<T>) + (size_t)C * (2 * n + pad) * sizeof(T);
+    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)n * sizeof(T) + (size_t)C * (2 * n + pad) * sizeof(T);
 }
 
 // Tile widths the column pass supports: FP32 4 or 8 columns, FP64 2 or 4 (16-byte row segments).
@@ -138,11 +140,17 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
                            double gsign, T* out, const int* stop, cudaStream_t s) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
-    allow_smem(k_rows_fwd<T, kRowWarps>, sm);
-    launch(sizeof(T) == 8 ? "dst_rows_fwd_f64" : "dst_rows_fwd_f32",
-           (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx),
-           k_rows_fwd<T, kRowWarps>, (nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s, p.NX, p.NY, p.nx,
-           p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
+    auto go = [&](auto kern) {
+        allow_smem(kern, sm);
+        launch(sizeof(T) == 8 ? "dst_rows_fwd_f64" : "dst_rows_fwd_f32",
+               (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx), kern,
+               (nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows,
+               dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
+    };
+    const int fp = fft_path(p.nx);
+    if (fp == 16) go(k_rows_fwd<T, kRowWarps, 16>);
+    else if (fp == 8) go(k_rows_fwd<T, kRowWarps, 8>);
+    else go(k_rows_fwd<T, kRowWarps, 0>);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -165,11 +173,17 @@ template <typename T, int C>
 static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
                             cudaStream_t s, int batch, long fstride) {
     const size_t sm = cols_smem<T>(p.ny, C);
-    allow_smem(k_cols<T, C>, sm);
-    launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32",
-           (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
-           (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), k_cols<T, C>, dim3(p.nx / C, batch), C * 32,
-           sm, s, p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
+    auto go = [&](auto kern) {
+        allow_smem(kern, sm);
+        launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32",
+               (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
+               (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), kern, dim3(p.nx / C, batch), C * 32, sm, s,
+               p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
+    };
+    const int fp = fft_path(p.ny);
+    if (fp == 16) go(k_cols<T, C, 16>);
+    else if (fp == 8) go(k_cols<T, C, 8>);
+    else go(k_cols<T, C, 0>);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -180,13 +194,19 @@ static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T
                            long fstride = 0) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
-    allow_smem(k_rows_inv<T, kRowWarps, MODE>, sm);
-    launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
-           (double)batch * nrows * p.NX *
-               (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
-           (double)batch * nrows * dst_flops(p.nx), k_rows_inv<T, kRowWarps, MODE>,
-           dim3((nrows + kRowWarps - 1) / kRowWarps, batch), kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0,
-           nrows, in, outT, out64, old, ooff, cls, p.tw, stop, fstride);
+    auto go = [&](auto kern) {
+        allow_smem(kern, sm);
+        launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
+               (double)batch * nrows * p.NX *
+                   (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
+               (double)batch * nrows * dst_flops(p.nx), kern, dim3((nrows + kRowWarps - 1) / kRowWarps, batch),
+               kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw,
+               stop, fstride);
+    };
+    const int fp = fft_path(p.nx);
+    if (fp == 16) go(k_rows_inv<T, kRowWarps, MODE, 16>);
+    else if (fp == 8) go(k_rows_inv<T, kRowWarps, MODE, 8>);
+    else go(k_rows_inv<T, kRowWarps, MODE, 0>);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -1439,6 +1459,22 @@ __global__ void k_box_eigs(int NX, int NY, int nx, int ny, double h, int as_floa
     else lam[k] = v;
 }
 
+// Shared-memory limits of every transform kernel the allocation-free solve may launch (all
+// FFT paths), sized for the largest supported line.
+template <typename T>
+static void allow_noalloc_smem() {
+    const size_t rs = rows_smem<T>(kNoAllocMaxN), cs = cols_smem<T>(kNoAllocMaxN, 4);
+    allow_smem(k_rows_fwd<T, kRowWarps, 0>, rs);
+    allow_smem(k_rows_fwd<T, kRowWarps, 8>, rs);
+    allow_smem(k_rows_fwd<T, kRowWarps, 16>, rs);
+    allow_smem(k_cols<T, 4, 0>, cs);
+    allow_smem(k_cols<T, 4, 8>, cs);
+    allow_smem(k_cols<T, 4, 16>, cs);
+    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 0>, rs);
+    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 8>, rs);
+    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 16>, rs);
+}
+
 // Once per device, with that device current: twiddle tables, the device address of the
 // static scratch, and the shared-memory limits of the transform kernels for the largest
 // supported line, so that later calls touch nothing but their stream.
@@ -1451,12 +1487,8 @@ static iim_status noalloc_setup(double** out) {
         IIM_CHECK(ensure_twiddles());
         void* p = nullptr;
         IIM_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        allow_smem(k_rows_fwd<double, kRowWarps>, rows_smem<double>(kNoAllocMaxN));
-        allow_smem(k_rows_fwd<float, kRowWarps>, rows_smem<float>(kNoAllocMaxN));
-        allow_smem(k_cols<double, 4>, cols_smem<double>(kNoAllocMaxN, 4));
-        allow_smem(k_cols<float, 4>, cols_smem<float>(kNoAllocMaxN, 4));
-        allow_smem(k_rows_inv<double, kRowWarps, INV_STORE_F64>, rows_smem<double>(kNoAllocMaxN));
-        allow_smem(k_rows_inv<float, kRowWarps, INV_STORE_F64>, rows_smem<float>(kNoAllocMaxN));
+        allow_noalloc_smem<double>();
+        allow_noalloc_smem<float>();
         g_noalloc_ptr[dev] = (double*)p;
     }
     *out = g_noalloc_ptr[dev];
