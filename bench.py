@@ -409,7 +409,7 @@ def main():
         for prec, pc in ((iim.IIM_MIXED, 1), (iim.IIM_FP64, 1), (iim.IIM_MIXED, 0), (iim.IIM_FP64, 0)):
             if pc and not precond:
                 continue
-            for inner in ((1e-3, 1e-4, 1e-5) if prec == iim.IIM_MIXED else (5e-12, 5e-11)):
+            for inner in ((1e-3, 1e-4, 1e-5, 1e-6, 3e-7) if prec == iim.IIM_MIXED else (5e-12, 5e-11)):
                 for _ in range(2):
                     solve(prec, inner, pc)
                 torch.cuda.synchronize()
