@@ -8,6 +8,8 @@
 // residual of the exact operator.
 #include <cmath>
 
+#include <cstdint>
+
 #include "common.cuh"
 
 namespace iim {
@@ -82,20 +84,46 @@ __global__ void k_set_identity_aug(float* __restrict__ A, int n) {
     A[i * ld + n + j] = (i == j) ? 1.f : 0.f;
 }
 
-// out = M v (+ out when accumulate), M row-major n x n FP32 with leading dimension ldm; one warp
-// per row.  v = vbase + (jidx ? *jidx : 0) * vstride.
-__global__ void k_dense_matvec(int n, const float* __restrict__ M, long ldm, const double* __restrict__ vbase,
-                               const int* __restrict__ jidx, long vstride, double* __restrict__ out, int accumulate,
-                               const int* __restrict__ stop) {
+// out = M v (+ out when accumulate), M row-major n x n FP32 with leading dimension ldm (even);
+// one warp per row.  v = vbase + (jidx ? *jidx : 0) * vstride is staged in shared memory as
+// FP32; each lane reads the row in 8-byte pairs (after one odd leading element when the row
+// starts 4 bytes off an 8-byte boundary) into four independent accumulators.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_dense_matvec(int n, const float* __restrict__ M, long ldm, const double* __restrict__ vbase,
+               const int* __restrict__ jidx, long vstride, double* __restrict__ out, int accumulate,
+               const int* __restrict__ stop) {
     if (stop && *stop) return;
+    extern __shared__ float s_v[];
     const double* v = jidx ? vbase + (long)(*jidx) * vstride : vbase;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (warp >= n) return;
-    const float* row = M + (long)warp * ldm;
-    float acc = 0.f;
-    for (int j = lane; j < n; j += 32) acc = fmaf(row[j], (float)v[j], acc);
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) out[warp] = accumulate ? out[warp] + (double)acc : (double)acc;
+    for (int j = threadIdx.x; j < n; j += WARPS * 32) s_v[j] = (float)v[j];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * WARPS + (threadIdx.x >> 5); row < n; row += gridDim.x * WARPS) {
+        const float* r = M + (long)row * ldm;
+        const int head = (reinterpret_cast<uintptr_t>(r) & 7) ? 1 : 0;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (head && lane == 0) a0 = r[0] * s_v[0];
+        const float2* r2 = reinterpret_cast<const float2*>(r + head);
+        const float* sv = s_v + head;
+        const int np = (n - head) >> 1;
+        int q = lane;
+        for (; q + 96 < np; q += 128) {
+            const float2 x0 = r2[q], x1 = r2[q + 32], x2 = r2[q + 64], x3 = r2[q + 96];
+            a0 = fmaf(x0.x, sv[2 * q], fmaf(x0.y, sv[2 * q + 1], a0));
+            a1 = fmaf(x1.x, sv[2 * q + 64], fmaf(x1.y, sv[2 * q + 65], a1));
+            a2 = fmaf(x2.x, sv[2 * q + 128], fmaf(x2.y, sv[2 * q + 129], a2));
+            a3 = fmaf(x3.x, sv[2 * q + 192], fmaf(x3.y, sv[2 * q + 193], a3));
+        }
+        for (; q < np; q += 32) {
+            const float2 x0 = r2[q];
+            a0 = fmaf(x0.x, sv[2 * q], fmaf(x0.y, sv[2 * q + 1], a0));
+        }
+        if (((n - head) & 1) && lane == 31) a1 = fmaf(r[n - 1], s_v[n - 1], a1);
+        float acc = (a0 + a1) + (a2 + a3);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) out[row] = accumulate ? out[row] + (double)acc : (double)acc;
+    }
 }
 
 iim_status gj_invert_aug(float* A, int n, float* f, int* info, cudaStream_t s) {
@@ -113,9 +141,11 @@ iim_status gj_invert_aug(float* A, int n, float* f, int* info, cudaStream_t s) {
 
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
                         int accumulate, const int* stop, cudaStream_t s) {
-    const int warps_per_block = 8;
-    launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec, (n + warps_per_block - 1) / warps_per_block,
-           warps_per_block * 32, 0, s, n, M, ldm, v, jidx, vstride, out, accumulate, stop);
+    constexpr int W = 8;
+    const size_t sm = sizeof(float) * (size_t)n;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_dense_matvec<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec<W>, (n + W - 1) / W, W * 32, sm, s, n, M,
+           ldm, v, jidx, vstride, out, accumulate, stop);
     IIM_LAUNCHED();
     return IIM_OK;
 }

@@ -247,7 +247,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------------- IIM operators
-// Blocks [0, nga): out[a] = (v ? v[a] : 0) + sum_e w_e * (idx >= 0 ? psi[idx] : bc(cp)),
+// Blocks [0, nga), one warp per affected point (BLOCK / 32 points per block):
+// out[a] = (v ? v[a] : 0) + sum_e w_e * (idx >= 0 ? psi[idx] : bc(cp)),
 // bc = -xc[body_circ[body]] for circulation bodies (the -B sum psibar 1_k column) when xc is
 // given, else 0.  Blocks [nga, nga + ncirc): out[na + c] = sum of v over body c's affected
 // points (the circulation rows), when v is given.
@@ -261,11 +262,12 @@ k_gather(int na, int nga, const int* __restrict__ ptr, const int* __restrict__ i
     const double* v = vin.base ? vin.get() : nullptr;
     double* out = jidx ? outb + (long)(*jidx + 1) * stride : outb;
     if ((int)blockIdx.x < nga) {
-        const int a = blockIdx.x * BLOCK + threadIdx.x;
+        // one warp per affected point, the lanes over its CSR entries
+        const int a = blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
         if (a >= na) return;
         const double* xc = (use_xc && v) ? v + na : nullptr;
         double acc = 0.0;
-        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+        for (int e = ptr[a] + lane; e < ptr[a + 1]; e += 32) {
             const int q = idx[e];
             if (q >= 0) {
                 acc += w[e] * (double)psi[q];
@@ -274,7 +276,8 @@ k_gather(int na, int nga, const int* __restrict__ ptr, const int* __restrict__ i
                 if (bc >= 0) acc -= w[e] * xc[bc];
             }
         }
-        out[a] = (v ? v[a] : 0.0) + acc;
+        acc = warp_sum(acc);
+        if (lane == 0) out[a] = (v ? v[a] : 0.0) + acc;
     } else {
         if (!v) return;
         const int c = blockIdx.x - nga;
@@ -365,11 +368,12 @@ template <int BLOCK>
 __global__ void k_residual(int NX, int NY, double ih2, const double* __restrict__ psi, const double* __restrict__ omega,
                            const uint8_t* __restrict__ cls, const double* __restrict__ ring, double* __restrict__ res,
                            double* __restrict__ partial) {
-    const int nx = NX + 1;
-    const long n = (long)nx * NY;
+    const int nx = NX + 1;               // a power of two: row index by shift, column by mask
+    const int sh = __ffs(nx) - 1;
+    const int n = nx * NY;               // < 2^31 for the supported sizes
     double acc = 0.0;
-    for (long k = (long)blockIdx.x * BLOCK + threadIdx.x; k < n; k += (long)gridDim.x * BLOCK) {
-        const int j = (int)(k / nx), i = (int)(k - (long)j * nx) - 1;
+    for (int k = blockIdx.x * BLOCK + threadIdx.x; k < n; k += gridDim.x * BLOCK) {
+        const int j = k >> sh, i = (k & (nx - 1)) - 1;
         double r = 0.0;
         if (i >= 0 && cls[k] <= CLS_PLUS) {
             const double c = psi[k];
@@ -454,10 +458,10 @@ __global__ void k_finish_residual(int nparts, const double* __restrict__ partial
 
 __global__ void k_init_psi(int NX, int NY, const double* __restrict__ guess, const uint8_t* __restrict__ cls,
                            double* __restrict__ psi) {
-    const int nx = NX + 1;
-    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long)nx * NY) return;
-    const int j = (int)(k / nx), i = (int)(k - (long)j * nx) - 1;
+    const int nx = NX + 1;               // a power of two
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx * NY) return;
+    const int j = k >> (__ffs(nx) - 1), i = (k & (nx - 1)) - 1;
     psi[k] = (guess && i >= 0 && cls[k] <= CLS_PLUS) ? guess[(long)j * NX + i] : 0.0;
 }
 
@@ -479,12 +483,12 @@ __global__ void k_add_psibar(int ncirc, const int* __restrict__ circ_ids, const 
 __global__ void k_velocity(int NX, int NY, double inv2h, const double* __restrict__ psi, const uint8_t* __restrict__ cls,
                            const double* __restrict__ ring, double* __restrict__ psi_out, double* __restrict__ ux,
                            double* __restrict__ uy) {
-    const long n = (long)NX * NY;
-    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = NX * NY;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int nx = NX + 1;
-    const int i = (int)(k % NX), j = (int)(k / NX);
-    const long p = (long)j * nx + 1 + i;
+    const int j = k / NX, i = k - j * NX;
+    const int p = j * nx + 1 + i;
     const bool fl = cls[p] <= CLS_PLUS;
     if (psi_out) psi_out[k] = fl ? psi[p] : 0.0;
     if (!ux && !uy) return;
@@ -852,7 +856,7 @@ struct Solver {
             IIM_CHECK(cols<T>(p, g->ja0, g->ja1, g->jo0, g->jo1, tb, stop, s));
             IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, stop, s)));
         }
-        const int nga = (g->na + 127) / 128;
+        const int nga = (g->na + 3) / 4;   // gather blocks: 4 warps, one affected point each
         launch("gather", 0.0, 0.0, k_gather<T, 128>, nga + g->ncirc, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx,
                g->gop_w, pt, g->cp_body, g->body_circ, g->aff_body, vj, 1, g->V, out_j, ld, stop);
         IIM_LAUNCHED();
@@ -885,7 +889,7 @@ struct Solver {
             IIM_TRY(cudaMemcpyAsync(row_of.data(), g->aff_node, sizeof(int) * (size_t)g->na, cudaMemcpyDeviceToHost, s));
             IIM_TRY(cudaStreamSynchronize(s));
             Plan<float> p = make_plan<float>(g);
-            const int nga = (g->na + 127) / 128;
+            const int nga = (g->na + 127) / 128;   // k_gather_unit: one thread per affected point
             iim_status bs = IIM_OK;
             for (int j0 = 0; j0 < g->na && bs == IIM_OK; j0 += K) {
                 const int kb = std::min(K, g->na - j0);
@@ -1036,7 +1040,7 @@ struct Solver {
         IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, g->nx, 1, nullptr, 0.0, nullptr, nullptr, kNoVec, 0.0, tb, nullptr, s));
         IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->jo0, g->jo1, tb, nullptr, s));
         IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
-        const int nga = (g->na + 127) / 128;
+        const int nga = (g->na + 3) / 4;   // gather blocks: 4 warps, one affected point each
         launch("gather", 0.0, 0.0, k_gather<T, 128>, nga, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx, g->gop_w, pt,
                g->cp_body, g->body_circ, g->aff_body, kNoVec, 0, g->bvec, nullptr, 0L, nullptr);
         IIM_LAUNCHED();
@@ -1205,7 +1209,7 @@ struct Solver {
             launch("psibar_estimate", 0.0, 0.0, k_psibar_estimate<128>, g->ncirc, 128, 0, s, g->ncp, g->nx, g->ny, g->cp_axis,
                    g->cp_ei, g->cp_ej, (const double*)g->cp_t, g->cp_body, g->body_circ, g->node_class,
                    (const double*)field, psi_b, g->x0g + g->na, -1.0);
-        const int nga = (g->na + 127) / 128;
+        const int nga = (g->na + 3) / 4;   // gather blocks: 4 warps, one affected point each
         if (g->na > 0)
             launch("gather", 0.0, 0.0, k_gather<double, 128>, nga, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx, g->gop_w,
                    (const double*)field, g->cp_body, g->body_circ, g->aff_body, VecArg{g->x0g, nullptr, 0, 0}, 1, g->x0g,

@@ -110,10 +110,10 @@ __device__ double t_face_flux(const TrView& v, double nu, int axis, int ai, int 
 
 // user layout (NX stride) -> padded, fluid values only
 __global__ void k_pack(int NX, int NY, const double* __restrict__ src, const uint8_t* __restrict__ cls, double* __restrict__ dst) {
-    const int nx = NX + 1;
-    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= (long)nx * NY) return;
-    const int j = (int)(k / nx), i = (int)(k - (long)j * nx) - 1;
+    const int nx = NX + 1;   // a power of two
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx * NY) return;
+    const int j = k >> (__ffs(nx) - 1), i = (k & (nx - 1)) - 1;
     dst[k] = (i >= 0 && cls[k] <= CLS_PLUS) ? src[(long)j * NX + i] : 0.0;
 }
 
@@ -295,11 +295,11 @@ __global__ void k_kelvin(TrView v, double nu, const iim_region* __restrict__ R, 
 
 __global__ void k_rk_omega(int NX, int NY, double b, const double* __restrict__ dw, const uint8_t* __restrict__ cls,
                            double* __restrict__ omega) {
-    const long n = (long)NX * NY;
-    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = NX * NY;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int i = (int)(k % NX), j = (int)(k / NX);
-    const long p = (long)j * (NX + 1) + 1 + i;
+    const int j = k / NX, i = k - j * NX;
+    const int p = j * (NX + 1) + 1 + i;
     omega[k] = cls[p] <= CLS_PLUS ? omega[k] + b * dw[p] : 0.0;
 }
 
