@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--c4-count", type=int, default=96)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess leg")
     ap.add_argument("--no-rk3", action="store_true", help="skip the RK3 step leg")
+    ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 multi-body leg")
     return ap.parse_args()
 
 
@@ -348,6 +349,67 @@ def rk3_c2(iim, inputs, dev, steps=3):
                            "vorticity flux through the box edges"}
 
 
+def c3_multibody(iim, inputs, dev, steps=3):
+    """The 2048^2 multi-body workload (three circles, an annulus, a five-petal star; 50 Gaussian
+    vortices; circulation mode): plain FP64 solve and mixed solve to 1e-10, their difference,
+    and the per-kernel profile of one mixed solve (a 2048^2 FP64 field is 32 MB, the solve's
+    working set about 0.2 GB, beyond the 129 MB L2)."""
+    import numpy as np
+    import torch
+    P = inputs.multibody(2048)
+    g = P.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions, P.modes)
+    h = g.h
+    gam = T([h * h * P.omega[r[2] - 1:r[3], r[0] - 1:r[1]].sum() for r in P.regions])
+    om, pb = T(P.omega.ravel()), T(np.zeros(geo.n_control))
+    out, res = {}, {}
+    for name, prec in (("fp64", iim.IIM_FP64), ("mixed", iim.IIM_MIXED)):
+        psi = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
+        pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
+        opts = iim.default_opts(prec=prec, rtol=1e-10, max_iter=4000)
+        iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, opts=opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            st = iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = psi
+        out[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "krylov_iters": st["iters"],
+                     "refinements": st["refinements"], "rel_res": st["rel_res"], "circ_err_max": st["circ_err_max"]}
+    out["mixed_vs_fp64_rel_linf"] = float((res["mixed"] - res["fp64"]).abs().max() / res["fp64"].abs().max())
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    iim.iim_profile_begin()
+    psi = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
+    pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
+    torch.cuda.nvtx.range_push("profile_c3")
+    iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10,
+                                                                                    max_iter=4000))
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    kern = sorted(iim.iim_profile_end(), key=lambda r: -r["ms"])
+    tot = sum(r["ms"] for r in kern)
+    peaks, src = measured_peaks()
+    mem = [r for r in kern if r["bytes"] > 0]
+    if mem:
+        d = mem[0]
+        us = d["ms"] * 1e3 / d["launches"]
+        ach = d["bytes"] / d["launches"] / (us * 1e-6) / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": d["name"], "achieved": ach, "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "peak_source": src,
+                           "alg_bytes_per_launch": d["bytes"] / d["launches"], "avg_launch_us": us,
+                           "share_of_kernel_time": d["ms"] / tot if tot else None}
+    out["kernels"] = [{"name": r["name"], "launches": r["launches"], "ms": r["ms"], "share": r["ms"] / tot if tot else None}
+                      for r in kern[:6]]
+    out["config"] = ("multibody_2048: [-4,4]^2, 2048^2 cells, 3 circles R~U(0.3,0.6), annulus 0.4/0.8, star "
+                     "r = 0.5 + 0.15 cos 5 theta; 50 Gaussian vortices sigma 0.1; circulation mode; "
+                     f"|A| = {geo.n_affected}, |C| = {geo.n_control}")
+    geo.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -554,6 +616,7 @@ def main():
         for gg in cgeos:
             gg.close()
     rk3 = None if args.no_rk3 else rk3_c2(iim, inputs, dev)
+    c3 = None if args.no_c3 else c3_multibody(iim, inputs, dev)
     c5 = None
     if not args.no_learned:
         c5 = learned_c5(iim, dev, opts_for)
@@ -592,6 +655,7 @@ def main():
         "batched_c4": c4,
         "learned_c5": c5,
         "rk3_c2": rk3,
+        "multibody_c3": c3,
         "cpu_baseline": cpu,
     }
     if rank == 0:

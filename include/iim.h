@@ -142,9 +142,11 @@ iim_status iim_geometry_affected_points(iim_geometry g, int* node_i, int* node_j
  *   psi_guess  interior array used when opts->guess is 1 or 2, else ignored (may be NULL)
  *   opts       host; NULL = FP64, rtol 1e-10, restart 40, max_iter 2000, max_refine 8
  *   stats      host, may be NULL
- * Refinement stops when the relative residual is <= rtol and, for circulation bodies, the
- * circulation error max_k |Gamma_k - (-h sum_dRk grad_h psi . n)| is <= 1e-12 or stopped
- * halving with the last correction (its rounding floor).
+ * Refinement stops when the relative residual is <= rtol.  With circulation bodies the solve
+ * then makes the circulation constraint exact to rounding by capacitance: the first solve on
+ * a geometry also computes, once, the response to unit circulation of each circulation body
+ * (one solve each, kept with the geometry), and every solve adds the combination of them that
+ * cancels Gamma_k - (-h sum_dRk grad_h psi . n).
  * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_NONFINITE, IIM_ERR_NOT_CONVERGED (outputs still hold
  * the best iterate), IIM_ERR_CUDA.  Synchronizes `stream` (convergence tests read one scalar
  * per Krylov iteration).  Not re-entrant on one geometry: calls that share an iim_geometry

@@ -159,6 +159,12 @@ struct iim_geometry_s {
     int pc_ready = 0;
     float pc_setup_ms = 0.f;
     int cols_c = 4;              // column-pass tile width (autotuned per size bucket)
+    // capacitance correction of the circulation: responses to unit circulation of each
+    // circulation body (padded psi_ext fields, ncirc of them), their psibar values
+    // ([response][circulation body]) and the inverse of their measured circulations
+    int cap_ready = 0;
+    double* cap_psi = nullptr;
+    std::vector<double> cap_pb, cap_cinv;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     void* graph64 = nullptr;     // captured GMRES iteration (FP64 transforms)
     void* graph32 = nullptr;     // captured GMRES iteration (FP32 transforms)

@@ -425,7 +425,8 @@ __global__ void k_circ_measure(int nx, const double* __restrict__ psi, const iim
 }
 
 // small[] layout
-enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048, SM_SEED = 2049 };
+enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048, SM_SEED = 2049,
+       SM_CAPC = 2112, SM_CAPP = 2176 };
 constexpr int kRegionParts = 16;
 
 // Combines partial sums into *out_res2 = sum partial + sum rc^2 and, for circulation bodies,
@@ -476,6 +477,16 @@ __global__ void k_init_psibar(int nb, const int* __restrict__ body_circ, const d
 __global__ void k_add_psibar(int ncirc, const int* __restrict__ circ_ids, const double* __restrict__ x, double* __restrict__ psibar) {
     const int c = threadIdx.x;
     if (c < ncirc) psibar[circ_ids[c]] += x[c];
+}
+
+// psi_ext += sum_l coef[l] resp_l (padded fields, npad values each): the capacitance correction.
+__global__ void k_cap_update(long npad, int ncirc, const double* __restrict__ resp, const double* __restrict__ coef,
+                             double* __restrict__ psi) {
+    const long p = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npad) return;
+    double acc = 0.0;
+    for (int l = 0; l < ncirc; ++l) acc += coef[l] * resp[(long)l * npad + p];
+    psi[p] += acc;
 }
 
 // Velocity u = (d_y psi, -d_x psi) by centered differences of psi_ext at fluid nodes (Sec. 4.2,
@@ -1258,10 +1269,102 @@ void destroy_graphs(iim_geometry g) {
 
 using namespace iim;
 
+static iim_status poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
+                                const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
+                                const double* psi_guess, const iim_opts* opts_in, iim_stats* stats, cudaStream_t s,
+                                bool capacitance);
+
+// Responses to unit circulation (Sec. 4.2's circulation constraint, solved by capacitance): for
+// each circulation body l, the solve with omega = 0, zero body and box data and Gamma = e_l; its
+// padded psi_ext, its psibar values and the circulations it measures on every R_k.  C (measured
+// circulations, k x l) is inverted on the host; a solve then adds sum_l (C^-1 e)_l resp_l with
+// e = Gamma - measured circulation, which makes the measured circulation equal Gamma to rounding.
+static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaStream_t s) {
+    const int nc = g->ncirc, nb = g->nb;
+    const long npad = (long)g->nx * g->NY, nxy = (long)g->NX * g->NY;
+    if (!g->cap_psi) IIM_TRY(cudaMalloc(&g->cap_psi, sizeof(double) * (size_t)nc * npad));
+    double *w0 = nullptr, *out = nullptr, *pb0 = nullptr, *gam = nullptr, *pbar = nullptr;
+    iim_status st = IIM_OK;
+    auto alloc = [&](double** p, size_t n) {
+        if (st == IIM_OK && cudaMalloc(p, sizeof(double) * std::max<size_t>(n, 1)) != cudaSuccess) st = IIM_ERR_CUDA;
+        if (st == IIM_OK && cudaMemsetAsync(*p, 0, sizeof(double) * std::max<size_t>(n, 1), s) != cudaSuccess)
+            st = IIM_ERR_CUDA;
+    };
+    alloc(&w0, nxy); alloc(&out, nxy); alloc(&pb0, g->ncp); alloc(&gam, nb); alloc(&pbar, nb);
+    std::vector<double> C((size_t)nc * nc), pbv((size_t)nc * nc), hg(nb), hp(nb), circ(nc);
+    iim_opts o = opts;
+    o.rtol = std::min(opts.rtol, 1e-11);
+    o.guess = 0;
+    for (int l = 0; l < nc && st == IIM_OK; ++l) {
+        std::fill(hg.begin(), hg.end(), 0.0);
+        hg[g->circ_ids[l]] = 1.0;
+        if (cudaMemcpyAsync(gam, hg.data(), sizeof(double) * nb, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            st = IIM_ERR_CUDA;
+            break;
+        }
+        st = poisson_solve(g, w0, pb0, nullptr, gam, pbar, out, nullptr, nullptr, nullptr, &o, nullptr, s, false);
+        if (st != IIM_OK) break;
+        if (cudaMemcpyAsync(g->cap_psi + (size_t)l * npad, g->psi_ext, sizeof(double) * npad, cudaMemcpyDeviceToDevice,
+                            s) != cudaSuccess ||
+            cudaMemcpyAsync(hp.data(), pbar, sizeof(double) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(circ.data(), g->small + SM_CIRC, sizeof(double) * nc, cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = IIM_ERR_CUDA;
+            break;
+        }
+        for (int k = 0; k < nc; ++k) {
+            C[(size_t)k * nc + l] = circ[k];
+            pbv[(size_t)l * nc + k] = hp[g->circ_ids[k]];
+        }
+    }
+    cudaFree(w0); cudaFree(out); cudaFree(pb0); cudaFree(gam); cudaFree(pbar);
+    if (st != IIM_OK) return st;
+    // invert C (close to the identity) by Gauss-Jordan with partial pivoting
+    std::vector<double> inv((size_t)nc * nc, 0.0);
+    for (int k = 0; k < nc; ++k) inv[(size_t)k * nc + k] = 1.0;
+    for (int k = 0; k < nc; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < nc; ++r)
+            if (std::fabs(C[(size_t)r * nc + k]) > std::fabs(C[(size_t)piv * nc + k])) piv = r;
+        if (!(std::fabs(C[(size_t)piv * nc + k]) > 0.0)) {
+            snprintf(g_last_error, sizeof(g_last_error), "circulation capacitance matrix singular");
+            return IIM_ERR_NOT_CONVERGED;
+        }
+        for (int c = 0; c < nc; ++c) {
+            std::swap(C[(size_t)k * nc + c], C[(size_t)piv * nc + c]);
+            std::swap(inv[(size_t)k * nc + c], inv[(size_t)piv * nc + c]);
+        }
+        const double d = 1.0 / C[(size_t)k * nc + k];
+        for (int c = 0; c < nc; ++c) { C[(size_t)k * nc + c] *= d; inv[(size_t)k * nc + c] *= d; }
+        for (int r = 0; r < nc; ++r) {
+            if (r == k) continue;
+            const double f = C[(size_t)r * nc + k];
+            if (f == 0.0) continue;
+            for (int c = 0; c < nc; ++c) {
+                C[(size_t)r * nc + c] -= f * C[(size_t)k * nc + c];
+                inv[(size_t)r * nc + c] -= f * inv[(size_t)k * nc + c];
+            }
+        }
+    }
+    g->cap_cinv = inv;
+    g->cap_pb = pbv;
+    g->cap_ready = 1;
+    return IIM_OK;
+}
+
 extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
                                         const double* gamma, double* psibar, double* psi_out, double* ux_out,
                                         double* uy_out, const double* psi_guess, const iim_opts* opts_in,
                                         iim_stats* stats, iim_stream stream) {
+    return poisson_solve(g, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out, uy_out, psi_guess, opts_in, stats,
+                         (cudaStream_t)stream, true);
+}
+
+static iim_status poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
+                                const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
+                                const double* psi_guess, const iim_opts* opts_in, iim_stats* stats, cudaStream_t s,
+                                bool capacitance) {
     iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
     if (opts_in) opts = *opts_in;
     if (stats) std::memset(stats, 0, sizeof(*stats));
@@ -1271,7 +1374,6 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         return IIM_ERR_INVALID_ARG;
     if ((opts.guess == 1 || opts.guess == 2) && !psi_guess) return IIM_ERR_INVALID_ARG;
     if (opts.guess < 0 || opts.guess > 2) return IIM_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
     if (g->ncirc > 0)
@@ -1282,6 +1384,13 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
     S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
     S.precond = opts.precond != 0 && S.ns > 0;
     if (S.precond && !g->pc_ready) IIM_CHECK(S.build_precond());
+    const bool use_cap = capacitance && g->ncirc > 0;
+    if (use_cap && !g->cap_ready) {
+        IIM_CHECK(build_capacitance(g, opts, s));
+        if (g->ncirc > 0)
+            IIM_TRY(cudaMemcpyAsync(g->d_int + DI_CIRC, g->circ_ids.data(), g->ncirc * sizeof(int),
+                                    cudaMemcpyHostToDevice, s));
+    }
     IIM_TRY(cudaEventRecord(g->ev0, s));
     const long npad = (long)g->nx * g->NY;
     const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 1e-4);
@@ -1322,32 +1431,45 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
         IIM_CHECK(S.seed_from_guess(psi_guess));
         x0 = g->x0g;
     }
-    // Refinement also goes on while the circulation constraint is off by more than kCircTol and
-    // the previous correction still halved that error (it stops at the rounding floor).
-    constexpr double kCircTol = 1e-12;
-    double cerr_prev = INFINITY;
     int iters_first = 0;
-    auto circ_open = [&]() { return g->ncirc > 0 && cerr > kCircTol && cerr < 0.5 * cerr_prev; };
-    while (rel > opts.rtol || (refinements > 0 && circ_open())) {
-        if (refinements >= opts.max_refine || S.iters >= opts.max_iter) {
-            if (rel > opts.rtol) st = IIM_ERR_NOT_CONVERGED;
-            break;
-        }
-        cerr_prev = cerr;
+    while (rel > opts.rtol) {
+        if (refinements >= opts.max_refine || S.iters >= opts.max_iter) { st = IIM_ERR_NOT_CONVERGED; break; }
         const int budget = opts.max_iter - S.iters;
         // the guess seeds the Krylov unknowns of the first correction only
         const double* sx = refinements == 0 ? x0 : nullptr;
-        // a correction made only for the circulation rows needs three digits, not the full
-        // inner tolerance
-        const double tol_k = rel > opts.rtol ? inner : std::max(inner, 1e-3);
-        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(tol_k, budget, sx)
-                                              : S.correction<float>(tol_k, budget, sx);
+        iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget, sx)
+                                              : S.correction<float>(inner, budget, sx);
         if (cs != IIM_OK) { st = cs; break; }
         if (refinements == 0) iters_first = S.iters;
         ++refinements;
         IIM_CHECK(S.residual(&res2, &cerr));
         if (!std::isfinite(res2)) { st = IIM_ERR_NONFINITE; break; }
         rel = std::sqrt(res2) / fnorm;
+    }
+    if (use_cap && g->cap_ready && (st == IIM_OK || st == IIM_ERR_NOT_CONVERGED)) {
+        // e_c = Gamma - measured circulation (from the last residual), coefficients C^-1 e, then
+        // psi_ext and psibar move along the unit-circulation responses; the residual is redone
+        const int nc = g->ncirc;
+        std::vector<double> rc(nc), coef(nc), dpb(nc, 0.0);
+        IIM_TRY(cudaMemcpyAsync(rc.data(), g->small + SM_RC, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        const double h2 = g->h * g->h;
+        for (int l = 0; l < nc; ++l) {
+            double a = 0.0;
+            for (int k = 0; k < nc; ++k) a += g->cap_cinv[(size_t)l * nc + k] * (rc[k] * h2);
+            coef[l] = a;
+        }
+        for (int l = 0; l < nc; ++l)
+            for (int c = 0; c < nc; ++c) dpb[c] += coef[l] * g->cap_pb[(size_t)l * nc + c];
+        IIM_TRY(cudaMemcpyAsync(g->small + SM_CAPC, coef.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
+        IIM_TRY(cudaMemcpyAsync(g->small + SM_CAPP, dpb.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
+        launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((npad + 255) / 256), 256, 0, s, npad, nc,
+               (const double*)g->cap_psi, (const double*)(g->small + SM_CAPC), g->psi_ext);
+        launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, nc, (const int*)(g->d_int + DI_CIRC),
+               (const double*)(g->small + SM_CAPP), psibar);
+        IIM_LAUNCHED();
+        IIM_CHECK(S.residual(&res2, &cerr));
+        rel = fnorm > 0.0 ? std::sqrt(res2) / fnorm : 0.0;
     }
     const long n = (long)g->NX * g->NY;
     launch("velocity_f64", (double)n * (9.0 + 8.0 + (ux_out ? 8.0 : 0.0) + (uy_out ? 8.0 : 0.0)), 0.0, k_velocity,

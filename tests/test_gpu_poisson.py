@@ -192,3 +192,22 @@ def test_guess_fallback_and_benefit():
     fl = (P.phi >= 0)[1:-1, 1:-1]
     assert rel_linf(bad["psi"], ref[1:-1, 1:-1], fl) < 1e-10
     geo.close()
+
+
+@pytest.mark.parametrize("prec,precond", [(iim.IIM_FP64, 0), (iim.IIM_MIXED, 0), (iim.IIM_MIXED, 1)])
+def test_circulation_exact_in_every_mode(prec, precond):
+    """Sec. 4.2's circulation constraint on the returned psi, measured on the host from the
+    returned node values (the oracle's flux sum over the faces of R_k), to 1e-12 absolute:
+    cylinder in a 1024 x 512 channel with noise vorticity and a nonzero Gamma."""
+    P = inputs.c2_cylinder_flow(1024, 512)
+    geo = gu.setup(P)
+    gam = op.gamma_from_regions(P) + np.array([0.3])
+    if precond:
+        iim.iim_build_preconditioner(geo)
+    out = gu.solve_opts(P, geo, gamma=gam, opts=iim.default_opts(prec=prec, rtol=1e-10, precond=precond))
+    nodes = gu.nodes_from_interior(P, out["psi"])
+    circ = op.discrete_circulation(nodes, P.regions[0])
+    assert abs(circ - gam[0]) < 1e-12, (circ, gam[0], out["stats"])
+    assert out["stats"]["circ_err_max"] < 1e-12
+    assert out["stats"]["rel_res"] <= 1e-10
+    geo.close()
