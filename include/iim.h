@@ -179,6 +179,12 @@ iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const dou
  * IIM_ERR_INVALID_ARG. */
 iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
 
+/* Threads per transformed line for 1024-point lines: 32 (default: one warp, fewest
+ * instructions, best when many solves share the GPU) or 64 (two warps per line: lower latency
+ * of one solve, about 6 % more instructions).  Other line lengths use one warp.  Errors:
+ * IIM_ERR_INVALID_ARG. */
+iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_line);
+
 /* Builds the dense Schur-complement preconditioner of a geometry: the matrix S of the augmented
  * system of Sec. 4.2 (gamma plus circulation unknowns), one column per FP32 operator
  * application, and its inverse by Gauss-Jordan elimination with partial pivoting in FP32,

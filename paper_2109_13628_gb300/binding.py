@@ -66,6 +66,7 @@ SIGNATURES = [
     ("iim_poisson_solve_batched", _i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
                                        _vp, _i, _vp]),
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
+    ("iim_geometry_set_lines", _i, [_vp, _i]),
     ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
     ("iim_net_num_params", ctypes.c_longlong, [_vp]),
     ("iim_net_get_params", _i, [_vp, _vp, ctypes.c_longlong]),
@@ -220,6 +221,11 @@ def default_opts(prec=IIM_FP64, rtol=1e-10, max_iter=2000, restart=64, max_refin
 
 def iim_geometry_set_tiles(g: "Geometry", cols_per_block: int):
     _check(load().iim_geometry_set_tiles(g.handle, int(cols_per_block)), "iim_geometry_set_tiles")
+
+
+def iim_geometry_set_lines(g: "Geometry", threads_per_line: int):
+    """32 (one warp per 1024-point line, the default) or 64 (lower single-solve latency)."""
+    _check(load().iim_geometry_set_lines(g.handle, int(threads_per_line)), "iim_geometry_set_lines")
 
 
 def _ptr_array(tensors, dtype, sizes, name):

@@ -159,6 +159,7 @@ struct iim_geometry_s {
     int pc_ready = 0;
     float pc_setup_ms = 0.f;
     int cols_c = 4;              // column-pass tile width (autotuned per size bucket)
+    int wide_lines = 0;          // 64 threads per 1024-point line (lower latency, more instructions)
     // capacitance correction of the circulation: responses to unit circulation of each
     // circulation body (padded psi_ext fields, ncirc of them), their psibar values
     // ([response][circulation body]) and the inverse of their measured circulations

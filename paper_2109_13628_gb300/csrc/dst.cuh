@@ -219,7 +219,13 @@ __device__ __forceinline__ void stockham_pass(const cpx<T>* in, const T* x, cpx<
 // twiddles W_M^(l k), one transpose through shared memory, P-point DFTs again and a
 // (32 / P)-point DFT across the lanes of each group.  Other sizes use the Stockham passes.
 __host__ __device__ constexpr bool reg_fft(int n) { return n == 512 || n == 1024; }
-__host__ __device__ constexpr int fft_path(int n) { return n == 1024 ? 16 : n == 512 ? 8 : 0; }
+// FFT path per line length: 16 / 8 = register path on one warp (n = 1024 / 512), 64 = three
+// register radix-8 stages on 64 threads (n = 1024, when wide lines are asked for: lower
+// latency per line, more instructions), 0 = Stockham passes on one warp (other sizes).
+__host__ __device__ constexpr int fft_path(int n, bool wide = false) {
+    return n == 1024 ? (wide ? 64 : 16) : n == 512 ? 8 : 0;
+}
+__host__ __device__ constexpr int line_threads(int fp) { return fp == 64 ? 64 : 32; }
 
 // Split step of the real FFT and the prefix sum of the odd outputs (see the file header): C
 // (swizzled, M values) -> dst (natural layout, X_k at index k).
@@ -306,6 +312,95 @@ __device__ __forceinline__ T* dst1_warp_reg(T* buf0, T* buf1, const cpx<T>* tw, 
     return buf1;
 }
 
+// Synchronises the TN threads of line group grp (TN = 32: the warp; TN = 64: named barrier
+// 1 + grp, one per group of a block).
+template <int TN>
+__device__ __forceinline__ void line_sync(int grp) {
+    if constexpr (TN == 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + grp), "r"(TN) : "memory");
+    }
+}
+
+// DST-I of a 1023-point line (n = 1024) on 64 threads: the n/2 = 512-point FFT as 8 x 8 x 8 with
+// m = 64 m3 + 8 m2 + m1 and k = k1 + 8 k2 + 64 k3 -- radix-8 DFTs in registers over m3, then
+// (after the twiddles W_512^((8 m2 + m1) k1) and a transpose) over m2, then (after W_64^(m1 k2)
+// and a second transpose) over m1.  Then the split step in striped order (k = tid + 64 i) and
+// the prefix sum of the odd outputs: warp scans of the 8 chunks, one exchange of the 16 warp
+// totals through `tot`.  Returns buf0 (natural layout); ends with the group synchronised.
+template <typename T>
+__device__ __forceinline__ T* dst1_line64(T* buf0, T* buf1, const cpx<T>* tw, int tid, int grp, T* tot) {
+    constexpr int n = 1024, M = 512;
+    const cpx<T>* t1 = tw + n;        // [k1 * 64 + t] = W_512^(t k1)
+    const cpx<T>* t2 = t1 + 512;      // [k2 * 8 + m1] = W_64^(m1 k2)
+    cpx<T> v[8];
+#pragma unroll
+    for (int m3 = 0; m3 < 8; ++m3) v[m3] = packed(buf0, tw, n, 64 * m3 + tid);
+    dft8_impl(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 8; ++k1) v[k1] = cmul(v[k1], t1[k1 * 64 + tid]);
+    cpx<T>* sc = reinterpret_cast<cpx<T>*>(buf1);
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) sc[swz<T>(k1 * 64 + tid)] = v[k1];
+    line_sync<64>(grp);
+    const int hi = tid >> 3, lo = tid & 7;    // stage 2: (k1, m1); stage 3: (k1, k2)
+#pragma unroll
+    for (int m2 = 0; m2 < 8; ++m2) v[m2] = sc[swz<T>(hi * 64 + 8 * m2 + lo)];
+    dft8_impl(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 8; ++k2) v[k2] = cmul(v[k2], t2[k2 * 8 + lo]);
+    cpx<T>* sc2 = reinterpret_cast<cpx<T>*>(buf0);   // the line was consumed before the first sync
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) sc2[swz<T>((hi * 8 + k2) * 8 + lo)] = v[k2];
+    line_sync<64>(grp);
+#pragma unroll
+    for (int m1 = 0; m1 < 8; ++m1) v[m1] = sc2[swz<T>(tid * 8 + m1)];
+    dft8_impl(v);
+    cpx<T>* C = reinterpret_cast<cpx<T>*>(buf1);
+#pragma unroll
+    for (int k3 = 0; k3 < 8; ++k3) C[swz<T>(hi + 8 * lo + 64 * k3)] = v[k3];
+    line_sync<64>(grp);
+    // split step (see dst_finish) in striped order; odd outputs kept for the prefix sum
+    T* dst = buf0;
+    const int lane = tid & 31, w = tid >> 5;
+    T odd[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = tid + 64 * i;
+        const cpx<T> ck = C[swz<T>(k)];
+        const cpx<T> cm = C[swz<T>(k == 0 ? 0 : M - k)];
+        const T ex = T(0.5) * (ck.x + cm.x), ey = T(0.5) * (ck.y - cm.y);
+        const T dx = T(0.5) * (ck.x - cm.x), dy = T(0.5) * (ck.y + cm.y);
+        const cpx<T> wt = tw[2 * k];
+        const T yx = ex + (wt.x * dy + wt.y * dx);
+        const T yy = ey + (wt.y * dy - wt.x * dx);
+        dst[2 * k] = k == 0 ? T(0) : -yy;
+        T val = k == 0 ? T(0.5) * yx : yx;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T u = __shfl_up_sync(0xffffffffu, val, off);
+            if (lane >= off) val += u;
+        }
+        odd[i] = val;
+        if (lane == 31) tot[2 * i + w] = val;
+    }
+    line_sync<64>(grp);
+    T carry = T(0);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int k = tid + 64 * i;
+        dst[2 * k + 1] = odd[i] + carry + (w ? tot[2 * i] : T(0));
+        carry += tot[2 * i] + tot[2 * i + 1];
+    }
+    line_sync<64>(grp);
+    return dst;
+}
+
+// One DST-I of a line on the FP path's threads (tid < line_threads(FP), group grp of the block).
+template <typename T, int FP>
+__device__ __forceinline__ T* dst_line(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int tid, int grp, T* tot);
+
 // DST-I of the line held in buf0[1..n-1] (buf0[0] ignored), with buf1 (n values) as scratch.
 // tw[k] = exp(-i pi k / n), k < n; tw + n holds the register-path or per-pass tables.  Returns
 // the buffer holding the result in [1..n-1] (natural layout).
@@ -341,14 +436,20 @@ __device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int 
     return dst;
 }
 
+template <typename T, int FP>
+__device__ __forceinline__ T* dst_line(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int tid, int grp, T* tot) {
+    if constexpr (FP == 64) return dst1_line64<T>(buf0, buf1, tw, tid, grp, tot);
+    else return dst1_warp<T, FP>(buf0, buf1, tw, n, logn, tid);
+}
+
 // Complex entries of the shared-memory twiddle region for lines of n points: the full table
 // exp(-i pi k / n), k < n, then the register-path tables (n / 2 + 32 entries) or the per-pass
 // tables (fewer than n / 2 entries).
-__host__ __device__ constexpr int tw_region(int n) { return n + n / 2 + 32; }
+__host__ __device__ constexpr int tw_region(int n) { return n + n / 2 + 64; }
 
 // Fills the twiddle region from the 4096-entry table; the loads of one thread are issued back
 // to back (batches of 8) before their shared-memory stores.
-template <typename T>
+template <int FP, typename T>
 __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, int n, int logn) {
     const int stride_shift = kTwLog - logn;
     const int nt = blockDim.x;
@@ -365,7 +466,15 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, 
             if (k < n) s_tw[k] = v[b];
         }
     }
-    if (reg_fft(n)) {
+    if (FP == 64) {
+        // 64-thread path: W_512^(t k1) at [k1 * 64 + t], then W_64^(m1 k2) at [512 + k2 * 8 + m1]
+        for (int e = threadIdx.x; e < 576; e += nt) {
+            const int j = e < 512 ? (e & 63) * (e >> 6) : 8 * ((e - 512) & 7) * ((e - 512) >> 3);
+            const int t = (4 * j) % (2 * n);
+            const cpx<T> w = g_tw[(t & (n - 1)) << stride_shift];
+            s_tw[n + e] = t >= n ? cpx<T>{-w.x, -w.y} : w;
+        }
+    } else if (FP == 8 || FP == 16) {
         // W_M^(l k) at [k * 32 + l] (M = n / 2), then W_32^j
         const int M = n >> 1;
         for (int e = threadIdx.x; e < M + 32; e += nt) {
@@ -387,25 +496,25 @@ using vec16_t = typename std::conditional<sizeof(T) == 4, float4, double2>::type
 
 // Loads nx values of a padded row (16-byte aligned) into a line buffer with vector loads,
 // batches of 8 loads in flight per lane.
-template <typename T>
+template <typename T, int TN = 32>
 __device__ __forceinline__ void load_row_vec(T* line, const T* __restrict__ g, int nx, int lane) {
     constexpr int V = 16 / sizeof(T);
     using VT = vec16_t<T>;
     const VT* src = reinterpret_cast<const VT*>(g);
     VT* dst = reinterpret_cast<VT*>(line);
     const int nv = nx / V;
-    for (int q0 = lane; q0 < nv; q0 += 8 * 32) {
+    for (int q0 = lane; q0 < nv; q0 += 8 * TN) {
         VT v[8];
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            if (q0 + 32 * b < nv) v[b] = src[q0 + 32 * b];
+            if (q0 + TN * b < nv) v[b] = src[q0 + TN * b];
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            if (q0 + 32 * b < nv) dst[q0 + 32 * b] = v[b];
+            if (q0 + TN * b < nv) dst[q0 + TN * b] = v[b];
     }
 }
 
-template <typename T>
+template <typename T, int TN = 32>
 __device__ __forceinline__ void store_row_vec(T* __restrict__ g, const T* line, int nx, int lane) {
     constexpr int V = 16 / sizeof(T);
     using VT = vec16_t<T>;
@@ -413,22 +522,22 @@ __device__ __forceinline__ void store_row_vec(T* __restrict__ g, const T* line, 
     VT* dst = reinterpret_cast<VT*>(g);
     const int nv = nx / V;
 #pragma unroll 4
-    for (int q = lane; q < nv; q += 32) dst[q] = src[q];
+    for (int q = lane; q < nv; q += TN) dst[q] = src[q];
 }
 
 // Loads a padded FP64 row (16-byte aligned, nx values) into a line buffer of T.
-template <typename T>
+template <typename T, int TN = 32>
 __device__ __forceinline__ void load_row_f64(T* line, const double* __restrict__ g, int nx, int lane) {
     const double2* src = reinterpret_cast<const double2*>(g);
     const int nv = nx / 2;
-    for (int q0 = lane; q0 < nv; q0 += 8 * 32) {
+    for (int q0 = lane; q0 < nv; q0 += 8 * TN) {
         double2 v[8];
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            if (q0 + 32 * b < nv) v[b] = src[q0 + 32 * b];
+            if (q0 + TN * b < nv) v[b] = src[q0 + TN * b];
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            const int q = q0 + 32 * b;
+            const int q = q0 + TN * b;
             if (q < nv) {
                 line[2 * q] = (T)v[b].x;
                 line[2 * q + 1] = (T)v[b].y;
@@ -448,11 +557,14 @@ struct VecArg {
     }
 };
 
+// Per-line scratch for the 64-thread path's prefix sum (16 values per line).
+constexpr int kLineScratch = 16;
+
 // Forward row transforms.  Row r (interior row index) of the input is
 //   dense[r*dld + doff + i] (FP64, optional) + box terms / h^2 (optional ring)
 //   + gsign * gamma at the affected points of the row (optional)
 // and the transformed row is written to out (padded layout).  `stop` (optional): a set flag
-// makes the launch a no-op.
+// makes the launch a no-op.  Each line is handled by line_threads(FP) threads.
 template <typename T, int WARPS, int FP>
 __global__ void __launch_bounds__(WARPS * 32)
 k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
@@ -460,61 +572,66 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
            const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
            T* __restrict__ out, const int* __restrict__ stop) {
     if (stop && *stop) return;
+    constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* b0 = reinterpret_cast<T*>(s_tw + tw_region(n)) + (size_t)warp * (2 * n);
+    const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
+    T* lines = reinterpret_cast<T*>(s_tw + tw_region(n));
+    T* b0 = lines + (size_t)grp * (2 * n);
     T* b1 = b0 + n;
-    load_twiddles(s_tw, g_tw, n, logn);
+    T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
+    load_twiddles<FP>(s_tw, g_tw, n, logn);
     __syncthreads();
-    const int r = row0 + blockIdx.x * WARPS + warp;
-    if (r >= row0 + nrows || r >= NY) return;
+    const int r = row0 + blockIdx.x * LPB + grp;
+    if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
     if (dense && dld == n && doff == 1) {
-        load_row_f64(b0, dense + (size_t)r * n, n, lane);   // padded row: slot 0 is a pad
+        load_row_f64<T, TN>(b0, dense + (size_t)r * n, n, tid);   // padded row: slot 0 is a pad
     } else if (dense) {
         const double* src = dense + (size_t)r * dld + doff;
 #pragma unroll 8
-        for (int i = lane; i < NX; i += 32) b0[i + 1] = (T)src[i];
+        for (int i = tid; i < NX; i += TN) b0[i + 1] = (T)src[i];
     } else {
-        for (int i = lane; i < NX; i += 32) b0[i + 1] = T(0);
+        for (int i = tid; i < NX; i += TN) b0[i + 1] = T(0);
     }
-    __syncwarp();
+    line_sync<TN>(grp);
     if (ring) {
         // ring: bottom row (nx+1), top row (nx+1), left column (ny-1), right column (ny-1)
         const int nxp1 = NX + 2;
-        if (lane == 0) {
+        if (tid == 0) {
             b0[1] += (T)(ring[2 * nxp1 + r] * ih2);
             b0[NX] += (T)(ring[2 * nxp1 + NY + r] * ih2);
         }
-        __syncwarp();
+        line_sync<TN>(grp);
         if (r == 0)
-            for (int i = lane; i < NX; i += 32) b0[i + 1] += (T)(ring[i + 1] * ih2);
+            for (int i = tid; i < NX; i += TN) b0[i + 1] += (T)(ring[i + 1] * ih2);
         if (r == NY - 1)
-            for (int i = lane; i < NX; i += 32) b0[i + 1] += (T)(ring[nxp1 + i + 1] * ih2);
-        __syncwarp();
+            for (int i = tid; i < NX; i += TN) b0[i + 1] += (T)(ring[nxp1 + i + 1] * ih2);
+        line_sync<TN>(grp);
     }
     if (gam.base) {
         const double* gv = gam.get();
         const int a0 = aff_row_ptr[r], a1 = aff_row_ptr[r + 1];
-        for (int a = a0 + lane; a < a1; a += 32) b0[aff_node[a] - r * n] += (T)(gsign * gv[a]);
-        __syncwarp();
+        for (int a = a0 + tid; a < a1; a += TN) b0[aff_node[a] - r * n] += (T)(gsign * gv[a]);
+        line_sync<TN>(grp);
     }
-    T* res = dst1_warp<T, FP>(b0, b1, s_tw, n, logn, lane);
-    if (lane == 0) res[0] = T(0);
-    __syncwarp();
-    store_row_vec(out + (size_t)r * n, res, n, lane);
+    T* res = dst_line<T, FP>(b0, b1, s_tw, n, logn, tid, grp, tot);
+    if (tid == 0) res[0] = T(0);
+    line_sync<TN>(grp);
+    store_row_vec<T, TN>(out + (size_t)r * n, res, n, tid);
 }
 
 // Column pass on padded columns p = 1..NX (p = 0 is the pad): forward y transform, division
 // by the eigenvalues (with the 2D normalisation), inverse y transform.  Rows outside [in0, in1]
-// are zero on input; only rows [out0, out1] are written back.  C columns per block, one warp
-// per column; blockIdx.y selects one of several fields fstride elements apart.
+// are zero on input; only rows [out0, out1] are written back.  C columns per block,
+// line_threads(FP) threads per column; blockIdx.y selects one of several fields fstride
+// elements apart.
 template <typename T, int C, int FP>
-__global__ void __launch_bounds__(C * 32)
+__global__ void __launch_bounds__(C * line_threads(FP))
 k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
        const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
        const int* __restrict__ stop, long fstride) {
     if (stop && *stop) return;
+    constexpr int TN = line_threads(FP);
     buf += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -522,16 +639,17 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
     const int stride = 2 * n + PAD;
     T* s_lam = reinterpret_cast<T*>(s_tw + tw_region(n));   // lam_y, NY values
     T* lines = s_lam + n;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
+    T* tot = lines + (size_t)C * stride + grp * kLineScratch;
     const int ld = NX + 1;
     const int col0 = blockIdx.x * C;   // padded column index
-    load_twiddles(s_tw, g_tw, n, logn);
-    for (int l = threadIdx.x; l < NY; l += C * 32) s_lam[l] = lam_y[l];
+    constexpr int nthr = C * TN;
+    load_twiddles<FP>(s_tw, g_tw, n, logn);
+    for (int l = threadIdx.x; l < NY; l += nthr) s_lam[l] = lam_y[l];
     // tile load: C consecutive padded columns of rows [in0, in1]; rows outside are zero
     constexpr int V = 16 / sizeof(T);
     constexpr int VPR = C / V;                   // vectors per row
     using VT = vec16_t<T>;
-    const int nthr = C * 32;
     const int total = NY * VPR;
     for (int t0 = threadIdx.x; t0 < total; t0 += 8 * nthr) {
         VT v[8];
@@ -555,10 +673,9 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
         }
     }
     __syncthreads();
-    const int p = col0 + warp;
-    T* resline = nullptr;
-    if (p >= 1 && p <= NX) {
-        T* b0 = lines + warp * stride;
+    const int p = col0 + grp;
+    if (p >= 1 && p <= NX) {   // uniform over the column's threads
+        T* b0 = lines + grp * stride;
         T* b1 = b0 + n;
         // forward transform, division, inverse transform: one copy of the transform code
         T* in = b0;
@@ -566,23 +683,22 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
         const T lx = lam_x[p - 1];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            T* f = dst1_warp<T, FP>(in, other, s_tw, n, logn, lane);
+            T* f = dst_line<T, FP>(in, other, s_tw, n, logn, tid, grp, tot);
             if (pass == 0) {
-                for (int l = lane; l < NY; l += 32) f[l + 1] = f[l + 1] * (norm / (lx + s_lam[l]));
-                __syncwarp();
+                for (int l = tid; l < NY; l += TN) f[l + 1] = f[l + 1] * (norm / (lx + s_lam[l]));
+                line_sync<TN>(grp);
             }
             other = (f == in) ? other : in;
             in = f;
         }
-        resline = in;
         // bring the result back to b0 so that the tile store below has a fixed layout
-        if (resline != b0) {
-            for (int l = lane; l < NY; l += 32) b0[l + 1] = resline[l + 1];
+        if (in != b0) {
+            for (int l = tid; l < NY; l += TN) b0[l + 1] = in[l + 1];
         }
     }
     __syncthreads();
     const int nout = out1 - out0 + 1;
-    for (int t = threadIdx.x; t < nout * VPR; t += C * 32) {
+    for (int t = threadIdx.x; t < nout * VPR; t += nthr) {
         const int rr = out0 + t / VPR, q = t % VPR;
         VT v;
         T* vs = reinterpret_cast<T*>(&v);
@@ -608,32 +724,35 @@ k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __rest
            double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
            const cpx<T>* __restrict__ g_tw, const int* __restrict__ stop, long fstride) {
     if (stop && *stop) return;
+    constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
     in += (long)blockIdx.y * fstride;
     if (outT) outT += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T* b0 = reinterpret_cast<T*>(s_tw + tw_region(n)) + (size_t)warp * (2 * n);
+    const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
+    T* lines = reinterpret_cast<T*>(s_tw + tw_region(n));
+    T* b0 = lines + (size_t)grp * (2 * n);
     T* b1 = b0 + n;
-    load_twiddles(s_tw, g_tw, n, logn);
+    T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
+    load_twiddles<FP>(s_tw, g_tw, n, logn);
     __syncthreads();
-    const int r = row0 + blockIdx.x * WARPS + warp;
-    if (r >= row0 + nrows || r >= NY) return;
-    load_row_vec(b0, in + (size_t)r * n, n, lane);
-    __syncwarp();
-    T* res = dst1_warp<T, FP>(b0, b1, s_tw, n, logn, lane);
+    const int r = row0 + blockIdx.x * LPB + grp;
+    if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
+    load_row_vec<T, TN>(b0, in + (size_t)r * n, n, tid);
+    line_sync<TN>(grp);
+    T* res = dst_line<T, FP>(b0, b1, s_tw, n, logn, tid, grp, tot);
     if (MODE == INV_STORE_T) {
-        if (lane == 0) res[0] = T(0);
-        __syncwarp();
-        store_row_vec(outT + (size_t)r * n, res, n, lane);
+        if (tid == 0) res[0] = T(0);
+        line_sync<TN>(grp);
+        store_row_vec<T, TN>(outT + (size_t)r * n, res, n, tid);
     } else if (MODE == INV_STORE_F64) {
         double* dst = out64 + (size_t)r * old + ooff;
 #pragma unroll 4
-        for (int i = lane; i < NX; i += 32) dst[i] = (double)res[i + 1];
+        for (int i = tid; i < NX; i += TN) dst[i] = (double)res[i + 1];
     } else {
         const size_t base = (size_t)r * n;
 #pragma unroll 4
-        for (int i = lane; i < NX; i += 32)
+        for (int i = tid; i < NX; i += TN)
             if (cls[base + 1 + i] <= CLS_PLUS) out64[base + 1 + i] += (double)res[i + 1];
     }
 }

@@ -89,6 +89,7 @@ struct Plan {
     const cpx<T>* tw;
     T norm;
     int cols_c = 4;   // columns per block of the column pass (tile width)
+    int wide = 0;     // 64 threads per 1024-point line instead of one warp
 };
 
 // Algorithmic flops of one DST-I of n - 1 points through an n/2-point complex FFT
@@ -101,13 +102,16 @@ constexpr int kRowWarps = 4;
 
 template <typename T>
 static size_t rows_smem(int n) {
-    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)kRowWarps * 2 * n * sizeof(T);
+    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)kRowWarps * (2 * n + kLineScratch) * sizeof(T);
 }
 template <typename T>
 static size_t cols_smem(int n, int C = cols_per_block<T>()) {
     const int pad = sizeof(T) == 4 ? 4 : 2;
-    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)n * sizeof(T) + (size_t)C * (2 * n + pad) * sizeof(T);
+    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)n * sizeof(T) +
+           (size_t)C * (2 * n + pad + kLineScratch) * sizeof(T);
 }
+// Rows per block of the row passes for lines of n points.
+static inline int rows_per_block(int n, bool wide) { return kRowWarps * 32 / line_threads(fft_path(n, wide)); }
 
 // Tile widths the column pass supports: FP32 4 or 8 columns, FP64 2 or 4 (16-byte row segments).
 template <typename T>
@@ -144,11 +148,13 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
         allow_smem(kern, sm);
         launch(sizeof(T) == 8 ? "dst_rows_fwd_f64" : "dst_rows_fwd_f32",
                (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx), kern,
-               (nrows + kRowWarps - 1) / kRowWarps, kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows,
-               dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
+               (nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), kRowWarps * 32, sm, s, p.NX,
+               p.NY, p.nx,
+               p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
     };
-    const int fp = fft_path(p.nx);
-    if (fp == 16) go(k_rows_fwd<T, kRowWarps, 16>);
+    const int fp = fft_path(p.nx, p.wide);
+    if (fp == 64) go(k_rows_fwd<T, kRowWarps, 64>);
+    else if (fp == 16) go(k_rows_fwd<T, kRowWarps, 16>);
     else if (fp == 8) go(k_rows_fwd<T, kRowWarps, 8>);
     else go(k_rows_fwd<T, kRowWarps, 0>);
     IIM_LAUNCHED();
@@ -177,11 +183,13 @@ static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int ou
         allow_smem(kern, sm);
         launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32",
                (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
-               (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), kern, dim3(p.nx / C, batch), C * 32, sm, s,
+               (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), kern, dim3(p.nx / C, batch),
+               C * line_threads(fft_path(p.ny, p.wide)), sm, s,
                p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
     };
-    const int fp = fft_path(p.ny);
-    if (fp == 16) go(k_cols<T, C, 16>);
+    const int fp = fft_path(p.ny, p.wide);
+    if (fp == 64) go(k_cols<T, C, 64>);
+    else if (fp == 16) go(k_cols<T, C, 16>);
     else if (fp == 8) go(k_cols<T, C, 8>);
     else go(k_cols<T, C, 0>);
     IIM_LAUNCHED();
@@ -199,12 +207,14 @@ static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T
         launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
                (double)batch * nrows * p.NX *
                    (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
-               (double)batch * nrows * dst_flops(p.nx), kern, dim3((nrows + kRowWarps - 1) / kRowWarps, batch),
+               (double)batch * nrows * dst_flops(p.nx), kern,
+               dim3((nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), batch),
                kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw,
                stop, fstride);
     };
-    const int fp = fft_path(p.nx);
-    if (fp == 16) go(k_rows_inv<T, kRowWarps, MODE, 16>);
+    const int fp = fft_path(p.nx, p.wide);
+    if (fp == 64) go(k_rows_inv<T, kRowWarps, MODE, 64>);
+    else if (fp == 16) go(k_rows_inv<T, kRowWarps, MODE, 16>);
     else if (fp == 8) go(k_rows_inv<T, kRowWarps, MODE, 8>);
     else go(k_rows_inv<T, kRowWarps, MODE, 0>);
     IIM_LAUNCHED();
@@ -216,12 +226,12 @@ static Plan<T> make_plan(iim_geometry g);
 template <>
 Plan<double> make_plan<double>(iim_geometry g) {
     return Plan<double>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x64, g->lam_y64,
-                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny), g->cols_c};
+                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny), g->cols_c, g->wide_lines};
 }
 template <>
 Plan<float> make_plan<float>(iim_geometry g) {
     return Plan<float>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
-                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c};
+                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c, g->wide_lines};
 }
 
 // ------------------------------------------------------------------------- reductions
@@ -1491,6 +1501,20 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
     }
     return st;
+}
+
+extern "C" iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_line) {
+    if (!g || (threads_per_line != 32 && threads_per_line != 64)) return IIM_ERR_INVALID_ARG;
+    const int wide = threads_per_line == 64 ? 1 : 0;
+    if (g->wide_lines != wide) {
+        g->wide_lines = wide;
+        // captured iteration graphs hold the previous kernels
+        for (void** gp : {&g->graph64, &g->graph32}) {
+            IterGraph* G = (IterGraph*)*gp;
+            if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+        }
+    }
+    return IIM_OK;
 }
 
 extern "C" iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block) {

@@ -127,12 +127,14 @@ def test_solve_matches_oracle_vortex_field(n, prec, circulation):
 
 
 @pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
-@pytest.mark.parametrize("n", [1024, 2048])
-def test_polynomial_exactness_full_size(prec, n):
-    """Any size: a bicubic psi* is reproduced exactly by the discrete IIM problem."""
+@pytest.mark.parametrize("n,lines", [(1024, 32), (1024, 64), (2048, 32)])
+def test_polynomial_exactness_full_size(prec, n, lines):
+    """Any size: a bicubic psi* is reproduced exactly by the discrete IIM problem (1024-point
+    lines also on the 64-thread transform path)."""
     P = inputs.bicubic_bodies(n, seed=7, circulation=True)
     gam = np.array([op.discrete_circulation(P.exact, r) for r in P.regions])
     geo = gu.setup(P)
+    iim.iim_geometry_set_lines(geo, lines)
     out = gu.solve(P, geo, gamma=gam, prec=prec, rtol=1e-12)
     fl = (P.phi >= 0)[1:-1, 1:-1]
     assert rel_linf(out["psi"], P.exact[1:-1, 1:-1], fl) < TOL[prec], out["stats"]
