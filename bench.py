@@ -3,10 +3,11 @@
 cells to a relative un-reduced residual of 1e-10 (chosen form: FP32 transforms inside FP64
 iterative refinement), with the plain FP64 iteration timed beside it.
 
-One step = one iim_poisson_solve (omega -> psi, u) through the C ABI with inputs resident in
-HBM.  L2 is flushed (256 MiB write) before every timed step; the flush is outside the step's
-CUDA events.  Under torchrun each rank runs independent solves on its own GPU (replicas, weak
-scaling); rank 0 prints one JSON line.
+One step = B independent iim_poisson_solve calls (omega -> psi, u) in flight together through the
+C ABI (iim_poisson_solve_batched) with inputs resident in HBM.  L2 is flushed (256 MiB write)
+before every timed step; the flush is outside the step's CUDA events.  Under torchrun each rank
+runs independent solves on its own GPU (replicas, weak scaling): time = max over ranks, solves
+= sum over ranks; rank 0 prints one JSON line.
 
 --impl reference times the CPU oracle (Schur-form GMRES with scipy's DST-I, FP64) on the
 host cores on the same workload, metric and unit.
@@ -63,6 +64,21 @@ def parse():
     ap.add_argument("--no-rk3", action="store_true", help="skip the RK3 step leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 multi-body leg")
     return ap.parse_args()
+
+
+def replica_totals(local_ms, local_units, device="cpu"):
+    """Whole-job figures of independent replicas: (max over ranks of the timed milliseconds,
+    sum over ranks of the units processed).  Without an initialised process group: the local
+    figures."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(local_ms), float(local_units)
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
 
 
 def dist_env():
@@ -513,12 +529,6 @@ def main():
             torch.distributed.barrier()
         return ms, outs
 
-    def max_over_ranks(x):
-        if ws > 1:
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return x
 
     # ---- concurrency autotuning of the batched form (untimed)
     n_streams = B
@@ -532,8 +542,8 @@ def main():
         launches = window["timed"]
         launch_window = dict(window)
     stats = [s for step_stats in outs for s in step_stats]
-    total_ms = max_over_ranks(sum(ms))
-    value = ws * B * args.steps / (total_ms * 1e-3)
+    total_ms, total_solves = replica_totals(sum(ms), B * args.steps, dev)
+    value = total_solves / (total_ms * 1e-3)
     # ---- the same form one problem at a time (latency view)
     ms1, outs1 = timed(lambda: solve(iim.IIM_MIXED), args.steps, 2)
     single = args.steps / (sum(ms1) * 1e-3)
@@ -593,8 +603,8 @@ def main():
                     h.copy_(d, non_blocking=True)
 
         ems, _ = timed(e2e_step, args.steps, args.warmup)
-        e_total = max_over_ranks(sum(ems))
-        e2e = {"value": ws * B * args.steps / (e_total * 1e-3), "unit": UNIT,
+        e_total, e_solves = replica_totals(sum(ems), B * args.steps, dev)
+        e2e = {"value": e_solves / (e_total * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": B * 8 * (NXY + psi_b.numel() + ring.numel()), "d2h_bytes_per_step": B * 8 * 3 * NXY}
     # ---- mixed-size batched workload (96 problems, 128^2 .. 1024^2)
     c4 = None

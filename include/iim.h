@@ -81,14 +81,18 @@ typedef struct {
                           when c = 0 -- the learned-guess path */
     double inner_rtol; /* Krylov tolerance of each correction solve (<= 0: library default,
                           rtol/20 in FP64 mode, 1e-4 in mixed mode) */
-    int precond;       /* 1: right-precondition GMRES with the dense inverse of the Schur matrix
-                          (built on first use, see iim_build_preconditioner); 0: plain GMRES */
+    int precond;       /* 0: plain GMRES; 1: right-precondition GMRES with the dense inverse of
+                          the Schur matrix (built on first use, see iim_build_preconditioner);
+                          2: each correction applies that inverse once, x = M b, with no Krylov
+                          iterations; when a correction fails to halve the FP64 residual the
+                          remaining corrections use mode 1 (stats fallback bit 1) */
 } iim_opts;
 
 typedef struct {
     int iters;           /* Krylov iterations, all refinements */
     int refinements;     /* correction solves performed */
-    int fallback;        /* 1 when a caller guess raised the residual and was dropped */
+    int fallback;        /* bit 0: a caller guess raised the residual and was dropped; bit 1:
+                            direct corrections (precond 2) handed over to GMRES */
     int status;          /* same value as returned */
     double rel_res;      /* final un-reduced FP64 relative residual */
     double gmres_rel_res;/* last Krylov relative residual */

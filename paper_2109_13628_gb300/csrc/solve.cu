@@ -1211,10 +1211,16 @@ struct Solver {
     template <typename T>
     iim_status correction(double tol, int max_it, const double* x0 = nullptr) {
         IIM_CHECK(rhs<T>());
-        IIM_CHECK(gmres<T>(tol, max_it, x0));
+        if (direct) {
+            // x = M b with the dense inverse of the Schur matrix: no Krylov iterations
+            IIM_CHECK(dense_matvec(ns, g->pc_aug + ns, 2L * ns, g->bvec, nullptr, 0, g->xsol, 0, nullptr, s));
+        } else {
+            IIM_CHECK(gmres<T>(tol, max_it, x0));
+        }
         IIM_CHECK(recover<T>(g->xsol));
         return IIM_OK;
     }
+    int direct = 0;   // corrections by one application of the dense inverse (opts.precond == 2)
 
     // Krylov starting point from a streamfunction guess psi0: the body constants it implies,
     // psibar0_k = mean over body k's control points of (psi0 at the adjacent fluid node - psi_b),
@@ -1383,7 +1389,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     if (opts.restart < 1 || opts.restart > 64 || !(opts.rtol > 0.0) || opts.max_iter < 1 || opts.max_refine < 1)
         return IIM_ERR_INVALID_ARG;
     if ((opts.guess == 1 || opts.guess == 2) && !psi_guess) return IIM_ERR_INVALID_ARG;
-    if (opts.guess < 0 || opts.guess > 2) return IIM_ERR_INVALID_ARG;
+    if (opts.guess < 0 || opts.guess > 2 || opts.precond < 0 || opts.precond > 2) return IIM_ERR_INVALID_ARG;
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
     if (g->ncirc > 0)
@@ -1393,6 +1399,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     S.g = g; S.s = s; S.prec = opts.prec; S.omega = omega; S.psi_b = psi_b; S.ring = psi_box; S.gamma = gamma;
     S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
     S.precond = opts.precond != 0 && S.ns > 0;
+    S.direct = opts.precond == 2 && S.ns > 0;
     if (S.precond && !g->pc_ready) IIM_CHECK(S.build_precond());
     const bool use_cap = capacitance && g->ncirc > 0;
     if (use_cap && !g->cap_ready) {
@@ -1441,12 +1448,13 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         IIM_CHECK(S.seed_from_guess(psi_guess));
         x0 = g->x0g;
     }
-    int iters_first = 0;
+    int iters_first = 0, direct_fallback = 0;
     while (rel > opts.rtol) {
         if (refinements >= opts.max_refine || S.iters >= opts.max_iter) { st = IIM_ERR_NOT_CONVERGED; break; }
         const int budget = opts.max_iter - S.iters;
         // the guess seeds the Krylov unknowns of the first correction only
         const double* sx = refinements == 0 ? x0 : nullptr;
+        const double rel_before = rel;
         iim_status cs = opts.prec == IIM_FP64 ? S.correction<double>(inner, budget, sx)
                                               : S.correction<float>(inner, budget, sx);
         if (cs != IIM_OK) { st = cs; break; }
@@ -1455,6 +1463,11 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         IIM_CHECK(S.residual(&res2, &cerr));
         if (!std::isfinite(res2)) { st = IIM_ERR_NONFINITE; break; }
         rel = std::sqrt(res2) / fnorm;
+        // a direct correction that did not halve the residual hands over to preconditioned GMRES
+        if (S.direct && !(rel < 0.5 * rel_before)) {
+            S.direct = 0;
+            direct_fallback = 1;
+        }
     }
     if (use_cap && g->cap_ready && (st == IIM_OK || st == IIM_ERR_NOT_CONVERGED)) {
         // e_c = Gamma - measured circulation (from the last residual), coefficients C^-1 e, then
@@ -1491,7 +1504,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     if (stats) {
         stats->iters = S.iters;
         stats->refinements = refinements;
-        stats->fallback = fallback | S.x0_fallback;
+        stats->fallback = fallback | S.x0_fallback | (direct_fallback << 1);
         stats->status = st;
         stats->rel_res = rel;
         stats->gmres_rel_res = S.last_gmres_rel;

@@ -45,3 +45,25 @@ def test_preconditioned_c1_1024_to_1e10():
     assert out["stats"]["iters"] <= 16, out["stats"]   # plain GMRES needs about 100 here
     assert out["stats"]["iters"] < 20, out["stats"]
     geo.close()
+
+
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_direct_corrections_match_oracle(prec):
+    """precond = 2: every correction is one application of the dense inverse (no Krylov
+    iterations unless the fallback to GMRES fires); the result is the same discrete solution."""
+    n = 128
+    P = inputs.bicubic_bodies(n, seed=n + 9, circulation=True)
+    w = inputs.vortex_field(P.grid, 31, count=20, sigma=0.2)
+    P.omega = np.where(P.phi >= 0, w, 0.0)[1:-1, 1:-1]
+    S = op.Setup(P)
+    gam = op.gamma_from_regions(P) + np.array([0.05, -0.1, 0.02])
+    ref, pb_ref = op.solve_unreduced(S, gamma=gam)
+    geo = gu.setup(P)
+    out = gu.solve_opts(P, geo, gamma=gam, opts=iim.default_opts(prec=prec, rtol=1e-13, max_iter=3000, precond=2))
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    err = np.abs(out["psi"] - ref[1:-1, 1:-1])[fl].max() / np.abs(ref).max()
+    assert err < TOL[prec], (err, out["stats"])
+    assert out["stats"]["rel_res"] <= 1e-13
+    if not out["stats"]["fallback"] & 2:
+        assert out["stats"]["iters"] == 0
+    geo.close()
