@@ -1210,6 +1210,7 @@ struct Solver {
 
     template <typename T>
     iim_status correction(double tol, int max_it, const double* x0 = nullptr) {
+        if (ns == 0) return recover<T>(g->xsol);   // no body: the correction is one box solve
         IIM_CHECK(rhs<T>());
         if (direct) {
             // x = M b with the dense inverse of the Schur matrix: no Krylov iterations
