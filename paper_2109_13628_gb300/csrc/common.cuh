@@ -166,6 +166,12 @@ struct iim_geometry_s {
     int cap_ready = 0;
     double* cap_psi = nullptr;
     std::vector<double> cap_pb, cap_cinv;
+    double* cap_dev = nullptr;   // device copies: C^-1 (nc x nc), then the psibar table (nc x nc)
+    // the whole solve as one graph (device-driven refinement; see solve.cu), its key, and the
+    // number of host-driven solves done on this geometry (the first solve always runs on the host)
+    void* solve_graph = nullptr;
+    int host_solves = 0;
+    int solve_graph_failed = 0;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
     void* graph64 = nullptr;     // captured GMRES iteration (FP64 transforms)
     void* graph32 = nullptr;     // captured GMRES iteration (FP32 transforms)

@@ -436,7 +436,7 @@ __global__ void k_circ_measure(int nx, const double* __restrict__ psi, const iim
 
 // small[] layout
 enum { SM_RES2 = 0, SM_CIRC_ERR = 1, SM_CIRC = 8, SM_RC = 8 + 64, SM_REG = 8 + 128, SM_NORM = 2048, SM_SEED = 2049,
-       SM_CAPC = 2112, SM_CAPP = 2176 };
+       SM_CAPC = 2112, SM_CAPP = 2176, SM_FNORM = 2240, SM_REL = 2241 };
 constexpr int kRegionParts = 16;
 
 // Combines partial sums into *out_res2 = sum partial + sum rc^2 and, for circulation bodies,
@@ -531,7 +531,10 @@ __global__ void k_velocity(int NX, int NY, double inv2h, const double* __restric
 // call, [3] max iterations of this call, [4] converged, [5] scratch column index,
 // [32, 96) circulation body ids
 enum { DI_J = 0, DI_STOP = 1, DI_IT = 2, DI_MAXIT = 3, DI_CONV = 4, DI_TMPJ = 5, DI_LOOP = 6, DI_LOOPERR = 7,
-       DI_CIRC = 32 };
+       // device-driven whole solve: refinements, Krylov iterations (all / first correction),
+       // cycles of the current correction, cap hits, non-finite residual, cycles and restarts
+       DI_REF = 8, DI_ITS = 9, DI_FIRST = 10, DI_CYC = 11, DI_CYCERR = 12, DI_NONFIN = 13, DI_CYCS = 14,
+       DI_RSS = 15, DI_CIRC = 32 };
 
 // Krylov small-storage layout inside g->H (m <= 64):
 //   H (m+1) x m column-major | cs[m] | sn[m] | gv[m+1] | hc1[m+1] | hc2[m+1] | y[m] | scal[8]
@@ -798,6 +801,94 @@ __global__ void k_loop_ctl(cudaGraphConditionalHandle h, int* __restrict__ di, i
     if (di[DI_STOP]) cudaGraphSetConditional(h, 0);
 }
 
+// ---- control kernels of the whole solve run as one graph (nested WHILE / IF nodes)
+// Before the refinement loop: ||f|| from the residual at psi = 0, counters reset, loop entered
+// unless there is nothing to solve.
+__global__ void k_ref_init(cudaGraphConditionalHandle h, int* __restrict__ di, double* __restrict__ small, double rtol) {
+    const double r2 = small[SM_RES2];
+    const double fn = sqrt(r2);
+    small[SM_FNORM] = fn;
+    small[SM_REL] = fn > 0.0 ? 1.0 : 0.0;
+    di[DI_REF] = 0; di[DI_ITS] = 0; di[DI_FIRST] = 0; di[DI_CYCERR] = 0; di[DI_CYCS] = 0; di[DI_RSS] = 0;
+    di[DI_LOOPERR] = 0;
+    const bool fin = isfinite(r2);
+    di[DI_NONFIN] = fin ? 0 : 1;
+    cudaGraphSetConditional(h, (fin && fn > 0.0 && 1.0 > rtol) ? 1 : 0);
+}
+
+// After gmres_init: the Krylov budget left for this correction; cycle counter reset; the cycle
+// loop entered unless the start already stopped (converged or no budget).
+__global__ void k_cyc_begin(cudaGraphConditionalHandle h, int* __restrict__ di, int max_iter) {
+    const int left = max_iter - di[DI_ITS];
+    di[DI_MAXIT] = left > 1 ? left : 1;
+    di[DI_CYC] = 0;
+    if (di[DI_IT] >= di[DI_MAXIT]) di[DI_STOP] = 1;
+    cudaGraphSetConditional(h, di[DI_STOP] ? 0 : 1);
+}
+
+// Start of a cycle: the iteration loop is entered unless the stop flag is set.
+__global__ void k_it_begin(cudaGraphConditionalHandle h, int* __restrict__ di) {
+    di[DI_LOOP] = 0;
+    cudaGraphSetConditional(h, di[DI_STOP] ? 0 : 1);
+}
+
+// End of a cycle (after the solution update): another cycle, with the restart residual, unless
+// converged, out of budget, or capped (cap: max_iter / restart + 2 cycles; reaching it without
+// one of the others sets an error flag).
+__global__ void k_cyc_ctl(cudaGraphConditionalHandle hc, cudaGraphConditionalHandle hr, int* __restrict__ di, int cap) {
+    const int c = ++di[DI_CYC];
+    ++di[DI_CYCS];
+    bool done = di[DI_CONV] || di[DI_IT] >= di[DI_MAXIT] || di[DI_LOOPERR];
+    if (!done && c >= cap) {
+        done = true;
+        di[DI_CYCERR] = 1;
+    }
+    if (!done) ++di[DI_RSS];
+    cudaGraphSetConditional(hc, done ? 0 : 1);
+    cudaGraphSetConditional(hr, done ? 0 : 1);
+}
+
+// End of a refinement: counters, the relative FP64 residual, and whether to go on (at most
+// max_refine corrections and max_iter Krylov iterations).
+__global__ void k_ref_ctl(cudaGraphConditionalHandle h, int* __restrict__ di, double* __restrict__ small, double rtol,
+                          int max_refine, int max_iter) {
+    if (di[DI_REF] == 0) di[DI_FIRST] = di[DI_IT];
+    di[DI_ITS] += di[DI_IT];
+    const int r = ++di[DI_REF];
+    const double r2 = small[SM_RES2], fn = small[SM_FNORM];
+    const bool fin = isfinite(r2);
+    if (!fin) di[DI_NONFIN] = 1;
+    const double rel = fn > 0.0 ? sqrt(r2) / fn : 0.0;
+    small[SM_REL] = rel;
+    const bool go = fin && rel > rtol && r < max_refine && di[DI_ITS] < max_iter && !di[DI_LOOPERR] && !di[DI_CYCERR];
+    cudaGraphSetConditional(h, go ? 1 : 0);
+}
+
+// Capacitance coefficients on the device: coef = C^-1 (h^2 rc), dpb = coef . Pb (one block).
+__global__ void k_cap_coef(int nc, const double* __restrict__ rc, const double* __restrict__ cinv,
+                           const double* __restrict__ pb, double h2, double* __restrict__ coef, double* __restrict__ dpb) {
+    __shared__ double c_sh[64];
+    const int t = threadIdx.x;
+    if (t < nc) {
+        double a = 0.0;
+        for (int k = 0; k < nc; ++k) a += cinv[t * nc + k] * (rc[k] * h2);
+        c_sh[t] = a;
+        coef[t] = a;
+    }
+    __syncthreads();
+    if (t < nc) {
+        double d = 0.0;
+        for (int l = 0; l < nc; ++l) d += c_sh[l] * pb[l * nc + t];
+        dpb[t] = d;
+    }
+}
+
+__global__ void k_final_rel(int* __restrict__ di, double* __restrict__ small) {
+    const double r2 = small[SM_RES2], fn = small[SM_FNORM];
+    if (!isfinite(r2)) di[DI_NONFIN] = 1;
+    small[SM_REL] = fn > 0.0 ? sqrt(r2) / fn : 0.0;
+}
+
 // One GMRES cycle as a graph: a WHILE node whose body is one iteration (the captured kernel
 // sequence) plus k_loop_ctl; `nodes` = kernels per body execution.
 struct IterGraph {
@@ -806,6 +897,76 @@ struct IterGraph {
     cudaStream_t stream = nullptr;
     int nodes = 0;
 };
+
+// The whole solve as one executable graph: the initial residual, a WHILE node over the
+// refinements whose body holds the right-hand side, the GMRES start, a WHILE node over restart
+// cycles (its body: a WHILE node over iterations, the solution update, an IF node with the
+// restart residual), the recovery and the residual; then the capacitance correction and the
+// velocity.  Control kernels decide every loop on the device (caps on every loop); the host
+// launches the graph once and reads the counters.  Valid for the exact arguments it was built
+// with (the key) and the geometry's tile settings.
+struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    // key
+    int prec = -1, m = 0, pc = 0, max_refine = 0, max_iter = 0, cap = 0;
+    double inner = 0.0, rtol = 0.0;
+    const void* ptrs[9] = {};   // caller arrays and the Krylov basis
+    // kernel nodes per execution of each level (launch accounting)
+    long long k_top = 0, k_ref = 0, k_cyc = 0, k_it = 0, k_rs = 0;
+};
+
+// Stream capture into an existing graph in pieces, so that conditional nodes can be placed
+// between the pieces: `deps` is the frontier the next node depends on.
+struct CapSeg {
+    cudaStream_t s;
+    cudaGraph_t graph;
+    std::vector<cudaGraphNode_t> deps;
+    cudaError_t begin() {
+        return cudaStreamBeginCaptureToGraph(s, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                             cudaStreamCaptureModeThreadLocal);
+    }
+    cudaError_t end() {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* d = nullptr;
+        size_t nd = 0;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &d, nullptr, &nd);
+        std::vector<cudaGraphNode_t> tail;
+        if (e == cudaSuccess && d) tail.assign(d, d + nd);
+        cudaGraph_t out = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(s, &out);
+        if (e == cudaSuccess && e2 == cudaSuccess) deps = tail;
+        return e != cudaSuccess ? e : e2;
+    }
+    // a conditional node after the frontier; *body receives its body graph
+    cudaError_t cond(cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = type;
+        p.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        cudaError_t e = cudaGraphAddNode(&node, graph, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &p);
+        if (e == cudaSuccess) {
+            deps.assign(1, node);
+            *body = p.conditional.phGraph_out[0];
+        }
+        return e;
+    }
+};
+
+// Kernel nodes directly in a graph (not inside its conditional bodies).
+static long long kernel_nodes(cudaGraph_t graph) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &n) != cudaSuccess || n == 0) return 0;
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess) return 0;
+    long long k = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+    }
+    return k;
+}
 
 struct Solver {
     iim_geometry g;
@@ -830,6 +991,17 @@ struct Solver {
 
     // ---- residual of the un-reduced system; fills g->res, small[], bvec circulation rows
     iim_status residual(double* res2_out, double* circ_err_out) {
+        IIM_CHECK(residual_launch());
+        IIM_TRY(cudaMemcpyAsync(g->h_pinned, g->small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        IIM_TRY(cudaStreamSynchronize(s));
+        *res2_out = g->h_pinned[SM_RES2];
+        *circ_err_out = g->h_pinned[SM_CIRC_ERR];
+        return IIM_OK;
+    }
+
+    // the kernels of residual(): ghosts, residual and partial norms, circulation measure,
+    // region sums, small[SM_RES2], small[SM_CIRC_ERR], small[SM_RC..], circulation rows of bvec
+    iim_status residual_launch() {
         const double ih2 = 1.0 / (g->h * g->h);
         if (g->nminus > 0) {
             launch("ghost_f64", 0.0, 0.0, k_ghost, (g->nminus + 255) / 256, 256, 0, s, g->nminus, g->minus_node, g->gh_ptr,
@@ -851,10 +1023,6 @@ struct Solver {
         launch("finish_residual", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kResBlocks, g->partial, g->ncirc,
                circ_ids_d, gamma, ih2, small, small + SM_REG, g->bvec ? g->bvec + g->na : nullptr, small + SM_RES2);
         IIM_LAUNCHED();
-        IIM_TRY(cudaMemcpyAsync(g->h_pinned, small, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        IIM_TRY(cudaStreamSynchronize(s));
-        *res2_out = g->h_pinned[SM_RES2];
-        *circ_err_out = g->h_pinned[SM_CIRC_ERR];
         return IIM_OK;
     }
 
@@ -1223,6 +1391,160 @@ struct Solver {
     }
     int direct = 0;   // corrections by one application of the dense inverse (opts.precond == 2)
 
+    // ---- the whole solve as one graph (SolveGraph); built on the private capture stream
+    template <typename T>
+    iim_status build_solve_graph(SolveGraph& G, const iim_opts& o, double inner, bool use_cap, double* psi_out,
+                                 double* ux_out, double* uy_out) {
+        const cudaStream_t user = s;
+        IIM_TRY(cudaStreamSynchronize(user));
+        cudaGraph_t top = nullptr;
+        IIM_TRY(cudaGraphCreate(&top, 0));
+        s = g->cap_stream;
+        set_capture(true);
+        iim_status st = IIM_OK;
+        cudaError_t ce = cudaSuccess;
+        // one captured piece: begin, launches, end (the capture is always ended)
+        auto piece = [&](CapSeg& seg, auto&& body) {
+            if (st != IIM_OK || ce != cudaSuccess) return;
+            ce = seg.begin();
+            if (ce != cudaSuccess) return;
+            st = body();
+            const cudaError_t e2 = seg.end();
+            if (ce == cudaSuccess) ce = e2;
+        };
+        auto handle = [&](cudaGraph_t graph, cudaGraphConditionalHandle* h) {
+            if (st == IIM_OK && ce == cudaSuccess) ce = cudaGraphConditionalHandleCreate(h, graph, 0, 0);
+        };
+        auto cond = [&](CapSeg& seg, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType t, cudaGraph_t* body) {
+            if (st == IIM_OK && ce == cudaSuccess) ce = seg.cond(h, t, body);
+        };
+        const long npad = (long)g->nx * g->NY;
+        const int ns_ = ns, eb = (ns_ + 255) / 256;
+        const long ld = ns_;
+        double* K = g->H;
+        double* x = g->xsol;
+        CapSeg top_seg{s, top, {}};
+        cudaGraphConditionalHandle h_ref = 0, h_cyc = 0, h_it = 0, h_rs = 0;
+        cudaGraph_t ref_body = nullptr, cyc_body = nullptr, it_body = nullptr, rs_body = nullptr;
+        handle(top, &h_ref);
+        piece(top_seg, [&]() -> iim_status {
+            launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, nullptr,
+                   g->node_class, g->psi_ext);
+            if (g->nb > 0)
+                launch("init_psibar", 0.0, 0.0, k_init_psibar, 1, 64, 0, s, g->nb, g->body_circ, psibar, 0, psibar);
+            IIM_CHECK(residual_launch());
+            launch("ref_init", 0.0, 0.0, k_ref_init, 1, 1, 0, s, h_ref, di(), g->small, o.rtol);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        });
+        cond(top_seg, h_ref, cudaGraphCondTypeWhile, &ref_body);
+        CapSeg ref_seg{s, ref_body, {}};
+        if (ns_ > 0) {
+            handle(ref_body, &h_cyc);
+            piece(ref_seg, [&]() -> iim_status {
+                IIM_CHECK(rhs<T>());
+                IIM_TRY(cudaMemsetAsync(x, 0, (size_t)ns_ * sizeof(double), s));
+                launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
+                launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0,
+                       nullptr, nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
+                launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), o.max_iter, K, L, g->small + SM_NORM,
+                       inner);
+                launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
+                launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns_, g->bvec, g->V, L, K, kNormBlocks,
+                       g->partial, di());
+                launch("cyc_begin", 0.0, 0.0, k_cyc_begin, 1, 1, 0, s, h_cyc, di(), o.max_iter);
+                IIM_LAUNCHED();
+                return IIM_OK;
+            });
+            cond(ref_seg, h_cyc, cudaGraphCondTypeWhile, &cyc_body);
+            CapSeg cyc_seg{s, cyc_body, {}};
+            handle(cyc_body, &h_it);
+            handle(cyc_body, &h_rs);
+            piece(cyc_seg, [&]() -> iim_status {
+                launch("it_begin", 0.0, 0.0, k_it_begin, 1, 1, 0, s, h_it, di());
+                IIM_LAUNCHED();
+                return IIM_OK;
+            });
+            cond(cyc_seg, h_it, cudaGraphCondTypeWhile, &it_body);
+            CapSeg it_seg{s, it_body, {}};
+            piece(it_seg, [&]() -> iim_status {
+                IIM_CHECK(iteration<T>());
+                launch("gmres_loop_ctl", 0.0, 0.0, k_loop_ctl, 1, 1, 0, s, h_it, di(), m + 2);
+                IIM_LAUNCHED();
+                return IIM_OK;
+            });
+            piece(cyc_seg, [&]() -> iim_status {
+                launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
+                if (precond) {
+                    double* t = g->pc_z + ns_;
+                    IIM_TRY(cudaMemsetAsync(t, 0, (size_t)ns_ * sizeof(double), s));
+                    launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), g->V, ld, K + L.y(), ns_, t);
+                    IIM_CHECK(dense_matvec(ns_, g->pc_aug + ns_, 2L * ns_, t, nullptr, 0, x, 1, nullptr, s));
+                } else {
+                    launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), g->V, ld, K + L.y(), ns_, x);
+                }
+                launch("cyc_ctl", 0.0, 0.0, k_cyc_ctl, 1, 1, 0, s, h_cyc, h_rs, di(), o.max_iter / m + 2);
+                IIM_LAUNCHED();
+                return IIM_OK;
+            });
+            cond(cyc_seg, h_rs, cudaGraphCondTypeIf, &rs_body);
+            CapSeg rs_seg{s, rs_body, {}};
+            piece(rs_seg, [&]() -> iim_status {
+                IIM_TRY(cudaMemcpyAsync(g->V + ld, x, (size_t)ns_ * sizeof(double), cudaMemcpyDeviceToDevice, s));
+                return restart_residual<T>();
+            });
+            G.k_cyc = kernel_nodes(cyc_body);
+            G.k_it = kernel_nodes(it_body);
+            G.k_rs = kernel_nodes(rs_body);
+        }
+        piece(ref_seg, [&]() -> iim_status {
+            IIM_CHECK(recover<T>(x));
+            IIM_CHECK(residual_launch());
+            launch("ref_ctl", 0.0, 0.0, k_ref_ctl, 1, 1, 0, s, h_ref, di(), g->small, o.rtol,
+                   std::min(o.max_refine, 1000), o.max_iter);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        });
+        piece(top_seg, [&]() -> iim_status {
+            if (use_cap) {
+                const int nc = g->ncirc;
+                launch("cap_coef", 0.0, 0.0, k_cap_coef, 1, 64, 0, s, nc, (const double*)(g->small + SM_RC),
+                       (const double*)g->cap_dev, (const double*)(g->cap_dev + (size_t)nc * nc), g->h * g->h,
+                       g->small + SM_CAPC, g->small + SM_CAPP);
+                launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((npad + 255) / 256), 256, 0, s, npad, nc,
+                       (const double*)g->cap_psi, (const double*)(g->small + SM_CAPC), g->psi_ext);
+                launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, nc, (const int*)(g->d_int + DI_CIRC),
+                       (const double*)(g->small + SM_CAPP), psibar);
+                IIM_CHECK(residual_launch());
+                launch("final_rel", 0.0, 0.0, k_final_rel, 1, 1, 0, s, di(), g->small);
+            }
+            const long n = (long)g->NX * g->NY;
+            launch("velocity_f64", 0.0, 0.0, k_velocity, (unsigned)((n + 255) / 256), 256, 0, s, g->NX, g->NY,
+                   0.5 / g->h, g->psi_ext, g->node_class, ring, psi_out, ux_out, uy_out);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        });
+        set_capture(false);
+        s = user;
+        if (st == IIM_OK && ce == cudaSuccess) {
+            G.k_top = kernel_nodes(top);
+            G.k_ref = ref_body ? kernel_nodes(ref_body) : 0;
+            ce = cudaGraphInstantiate(&G.exec, top, 0);
+        }
+        cudaGraphDestroy(top);
+        if (ce != cudaSuccess) {
+            G.exec = nullptr;
+            record_cuda_error(ce, "whole-solve graph", __FILE__, __LINE__);
+            cudaGetLastError();
+            return IIM_ERR_CUDA;
+        }
+        if (st != IIM_OK) {
+            if (G.exec) cudaGraphExecDestroy(G.exec);
+            G.exec = nullptr;
+        }
+        return st;
+    }
+
     // Krylov starting point from a streamfunction guess psi0: the body constants it implies,
     // psibar0_k = mean over body k's control points of (psi0 at the adjacent fluid node - psi_b),
     // and x0 = [A psi0 + B sum_k psibar0_k 1_k ; psibar0] (homogeneous data, as in the
@@ -1271,7 +1593,17 @@ static iim_status ensure_krylov(iim_geometry g, int m) {
     return IIM_OK;
 }
 
+static void drop_solve_graph(iim_geometry g) {
+    SolveGraph* G = (SolveGraph*)g->solve_graph;
+    if (G) {
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        delete G;
+        g->solve_graph = nullptr;
+    }
+}
+
 void destroy_graphs(iim_geometry g) {
+    drop_solve_graph(g);
     for (void** gp : {&g->graph64, &g->graph32}) {
         IterGraph* G = (IterGraph*)*gp;
         if (G) {
@@ -1366,6 +1698,11 @@ static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaSt
     }
     g->cap_cinv = inv;
     g->cap_pb = pbv;
+    if (!g->cap_dev) IIM_TRY(cudaMalloc(&g->cap_dev, sizeof(double) * 2 * (size_t)nc * nc));
+    IIM_TRY(cudaMemcpyAsync(g->cap_dev, inv.data(), sizeof(double) * (size_t)nc * nc, cudaMemcpyHostToDevice, s));
+    IIM_TRY(cudaMemcpyAsync(g->cap_dev + (size_t)nc * nc, pbv.data(), sizeof(double) * (size_t)nc * nc,
+                            cudaMemcpyHostToDevice, s));
+    IIM_TRY(cudaStreamSynchronize(s));
     g->cap_ready = 1;
     return IIM_OK;
 }
@@ -1409,9 +1746,77 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
             IIM_TRY(cudaMemcpyAsync(g->d_int + DI_CIRC, g->circ_ids.data(), g->ncirc * sizeof(int),
                                     cudaMemcpyHostToDevice, s));
     }
-    IIM_TRY(cudaEventRecord(g->ev0, s));
     const long npad = (long)g->nx * g->NY;
     const double inner = opts.inner_rtol > 0.0 ? opts.inner_rtol : (opts.prec == IIM_FP64 ? opts.rtol / 20.0 : 1e-4);
+
+    // After one host-driven solve on the geometry, solves without a guess (and not profiled,
+    // not in direct-correction mode) run as one device-driven graph: no host round trip per
+    // refinement or GMRES cycle.  The graph is rebuilt when the arguments change.
+    if (capacitance && S.use_graph && !profiling_active() && opts.guess == 0 && opts.precond != 2 &&
+        g->host_solves > 0 && !g->solve_graph_failed) {
+        const void* key[9] = {omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out, uy_out, g->V};
+        SolveGraph* G = (SolveGraph*)g->solve_graph;
+        const bool match = G && G->exec && G->prec == opts.prec && G->m == opts.restart && G->pc == (int)S.precond &&
+                           G->max_refine == opts.max_refine && G->max_iter == opts.max_iter &&
+                           G->cap == (int)use_cap && G->inner == inner && G->rtol == opts.rtol &&
+                           std::memcmp(G->ptrs, key, sizeof(key)) == 0;
+        if (!match) {
+            drop_solve_graph(g);
+            G = new SolveGraph();
+            G->prec = opts.prec; G->m = opts.restart; G->pc = (int)S.precond; G->max_refine = opts.max_refine;
+            G->max_iter = opts.max_iter; G->cap = (int)use_cap; G->inner = inner; G->rtol = opts.rtol;
+            std::memcpy(G->ptrs, key, sizeof(key));
+            const iim_status bs =
+                opts.prec == IIM_FP64
+                    ? S.build_solve_graph<double>(*G, opts, inner, use_cap, psi_out, ux_out, uy_out)
+                    : S.build_solve_graph<float>(*G, opts, inner, use_cap, psi_out, ux_out, uy_out);
+            if (bs != IIM_OK || !G->exec) {
+                delete G;
+                G = nullptr;
+                g->solve_graph_failed = 1;   // the host-driven path below, from now on
+            } else {
+                g->solve_graph = G;
+            }
+        }
+        if (G) {
+            IIM_TRY(cudaEventRecord(g->ev0, s));
+            IIM_TRY(cudaGraphLaunch(G->exec, s));
+            IIM_TRY(cudaEventRecord(g->ev1, s));
+            int* hi = reinterpret_cast<int*>(g->h_pinned + 32);
+            IIM_TRY(cudaMemcpyAsync(hi, g->d_int, 16 * sizeof(int), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaMemcpyAsync(g->h_pinned + 40, g->small + SM_REL, sizeof(double), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaMemcpyAsync(g->h_pinned + 41, g->small + SM_CIRC_ERR, sizeof(double), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaMemcpyAsync(g->h_pinned + 44, g->H + S.L.scal(), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            IIM_TRY(cudaStreamSynchronize(s));
+            const double rel = g->h_pinned[40];
+            iim_status st = IIM_OK;
+            if (hi[DI_NONFIN]) {
+                st = IIM_ERR_NONFINITE;
+            } else if (hi[DI_LOOPERR] || hi[DI_CYCERR]) {
+                snprintf(g_last_error, sizeof(g_last_error), "GMRES loop ended by its iteration cap");
+                st = IIM_ERR_NOT_CONVERGED;
+            } else if (rel > opts.rtol) {
+                st = IIM_ERR_NOT_CONVERGED;
+            }
+            count_launches(G->k_top + (long long)hi[DI_REF] * G->k_ref + (long long)hi[DI_CYCS] * G->k_cyc +
+                           (long long)hi[DI_ITS] * G->k_it + (long long)hi[DI_RSS] * G->k_rs);
+            if (stats) {
+                stats->iters = hi[DI_ITS];
+                stats->refinements = hi[DI_REF];
+                stats->fallback = 0;
+                stats->status = st;
+                stats->rel_res = rel;
+                const double bn = g->h_pinned[44 + SC_TOL] / std::max(inner, 1e-300);
+                stats->gmres_rel_res = S.ns > 0 && bn > 0.0 ? g->h_pinned[44 + SC_RESID] / bn : 0.0;
+                stats->circ_err_max = g->h_pinned[41];
+                stats->seed_rel_res = 1.0;
+                stats->iters_first = hi[DI_FIRST];
+                cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
+            }
+            return st;
+        }
+    }
+    IIM_TRY(cudaEventRecord(g->ev0, s));
 
     // ||f||: residual at psi = 0 (ghosts from the boundary data only)
     double res2 = 0.0, cerr = 0.0;
@@ -1514,6 +1919,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         stats->iters_first = iters_first;
         cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
     }
+    if (capacitance && st == IIM_OK) ++g->host_solves;
     return st;
 }
 
@@ -1522,6 +1928,7 @@ extern "C" iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_lin
     const int wide = threads_per_line == 64 ? 1 : 0;
     if (g->wide_lines != wide) {
         g->wide_lines = wide;
+        drop_solve_graph(g);
         // captured iteration graphs hold the previous kernels
         for (void** gp : {&g->graph64, &g->graph32}) {
             IterGraph* G = (IterGraph*)*gp;
@@ -1535,6 +1942,7 @@ extern "C" iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block)
     if (!g || (cols_per_block != 2 && cols_per_block != 4 && cols_per_block != 8)) return IIM_ERR_INVALID_ARG;
     if (g->cols_c != cols_per_block) {
         g->cols_c = cols_per_block;
+        drop_solve_graph(g);
         // captured iteration graphs hold the previous kernels
         for (void** gp : {&g->graph64, &g->graph32}) {
             IterGraph* G = (IterGraph*)*gp;
