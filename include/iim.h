@@ -146,6 +146,9 @@ iim_status iim_geometry_affected_points(iim_geometry g, int* node_i, int* node_j
  *   psi_guess  interior array used when opts->guess is 1 or 2, else ignored (may be NULL)
  *   opts       host; NULL = FP64, rtol 1e-10, restart 40, max_iter 2000, max_refine 8
  *   stats      host, may be NULL
+ * From the second solve on a geometry (no guess, precond 0 or 1, no profiling), the whole solve
+ * -- refinements, GMRES cycles and iterations -- runs as one CUDA graph whose loops are decided
+ * on the device; it is captured again when the arguments or the geometry's tile settings change.
  * Refinement stops when the relative residual is <= rtol.  With circulation bodies the solve
  * then makes the circulation constraint exact to rounding by capacitance: the first solve on
  * a geometry also computes, once, the response to unit circulation of each circulation body
@@ -165,9 +168,12 @@ iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* 
  * and geometries).  Problem k uses geoms[k] (all distinct: each geometry owns the workspace
  * of its solve) and the k-th pointer of every array argument, with the meaning of
  * iim_poisson_solve; psi_box, gamma, ux_out, uy_out may be NULL arrays (then NULL for every
- * problem).  n_streams worker threads, each on its own stream, take the problems largest
- * first; every solve replays its GMRES iterations as a CUDA graph.  The work is ordered after
- * prior work on `stream` and `stream` waits for all of it.  stats: host, n entries or NULL.
+ * problem).  The problems go to n_streams streams, largest first.  A problem whose geometry
+ * has already been solved once runs as one whole-solve graph launch (see iim_poisson_solve),
+ * all of them launched from the calling thread without waiting; first solves (host-driven, with
+ * their set-up) are shared by n_streams worker threads.  The work is ordered after prior work
+ * on `stream` and `stream` waits for all of it; the call returns when every problem is done.
+ * stats: host, n entries or NULL.
  * Returns the first non-OK status of any problem (all problems are attempted).  The paper
  * solves one problem at a time; batching is this library's throughput mode. */
 iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const double* const* omega,

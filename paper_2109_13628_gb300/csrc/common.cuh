@@ -179,6 +179,12 @@ struct iim_geometry_s {
 
 namespace iim {
 void destroy_graphs(iim_geometry g);
+// whole-solve graph without waiting: *enqueued = 1 launched on s (then solve_finish after the
+// stream is synchronised), 0 solved to completion, -1 not applicable yet (nothing done)
+iim_status solve_enqueue(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
+                         const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
+                         const iim_opts* opts, iim_stats* stats, cudaStream_t s, int* enqueued);
+iim_status solve_finish(iim_geometry g, const iim_opts* opts, iim_stats* stats);
 // dense Schur-complement preconditioner (precond.cu)
 iim_status gj_invert_aug(float* A, int n, float* f, int* info, cudaStream_t s);
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,

@@ -1621,7 +1621,8 @@ using namespace iim;
 static iim_status poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
                                 const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
                                 const double* psi_guess, const iim_opts* opts_in, iim_stats* stats, cudaStream_t s,
-                                bool capacitance);
+                                bool capacitance, int* enqueued = nullptr);
+static iim_status graph_finish(iim_geometry g, const iim_opts& opts, iim_stats* stats);
 
 // Responses to unit circulation (Sec. 4.2's circulation constraint, solved by capacitance): for
 // each circulation body l, the solve with omega = 0, zero body and box data and Gamma = e_l; its
@@ -1707,6 +1708,22 @@ static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaSt
     return IIM_OK;
 }
 
+namespace iim {
+// For the batched solver: launch the whole-solve graph without waiting (see poisson_solve's
+// `enqueued`), and read its results once the stream has been synchronised.
+iim_status solve_enqueue(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
+                         const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
+                         const iim_opts* opts, iim_stats* stats, cudaStream_t s, int* enqueued) {
+    return poisson_solve(g, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out, uy_out, nullptr, opts, stats, s,
+                         true, enqueued);
+}
+iim_status solve_finish(iim_geometry g, const iim_opts* opts_in, iim_stats* stats) {
+    iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
+    if (opts_in) opts = *opts_in;
+    return graph_finish(g, opts, stats);
+}
+}  // namespace iim
+
 extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
                                         const double* gamma, double* psibar, double* psi_out, double* ux_out,
                                         double* uy_out, const double* psi_guess, const iim_opts* opts_in,
@@ -1715,12 +1732,57 @@ extern "C" iim_status iim_poisson_solve(iim_geometry g, const double* omega, con
                          (cudaStream_t)stream, true);
 }
 
+// Reads the counters a whole-solve graph run left in the pinned block and fills the status and
+// the stats (the stream that ran it has been synchronised).
+static iim_status graph_finish(iim_geometry g, const iim_opts& opts, iim_stats* stats) {
+    const SolveGraph* G = (const SolveGraph*)g->solve_graph;
+    const int* hi = reinterpret_cast<const int*>(g->h_pinned + 32);
+    const double rel = g->h_pinned[40];
+    iim_status st = IIM_OK;
+    if (hi[DI_NONFIN]) {
+        st = IIM_ERR_NONFINITE;
+    } else if (hi[DI_LOOPERR] || hi[DI_CYCERR]) {
+        snprintf(g_last_error, sizeof(g_last_error), "GMRES loop ended by its iteration cap");
+        st = IIM_ERR_NOT_CONVERGED;
+    } else if (rel > opts.rtol) {
+        st = IIM_ERR_NOT_CONVERGED;
+    }
+    count_launches(G->k_top + (long long)hi[DI_REF] * G->k_ref + (long long)hi[DI_CYCS] * G->k_cyc +
+                   (long long)hi[DI_ITS] * G->k_it + (long long)hi[DI_RSS] * G->k_rs);
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->iters = hi[DI_ITS];
+        stats->refinements = hi[DI_REF];
+        stats->status = st;
+        stats->rel_res = rel;
+        const double bn = g->h_pinned[44 + SC_TOL] / std::max(G->inner, 1e-300);
+        stats->gmres_rel_res = (g->na + g->ncirc) > 0 && bn > 0.0 ? g->h_pinned[44 + SC_RESID] / bn : 0.0;
+        stats->circ_err_max = g->h_pinned[41];
+        stats->seed_rel_res = 1.0;
+        stats->iters_first = hi[DI_FIRST];
+        cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
+    }
+    return st;
+}
+
+// `enqueued` (batched solves): NULL = ordinary blocking call.  Otherwise *enqueued = 1 when the
+// whole-solve graph was launched on s and nothing was waited for (graph_finish after the stream
+// is synchronised), 0 when the solve ran to completion here, -1 when the graph path does not
+// apply yet and nothing was done.
 static iim_status poisson_solve(iim_geometry g, const double* omega, const double* psi_b, const double* psi_box,
                                 const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
                                 const double* psi_guess, const iim_opts* opts_in, iim_stats* stats, cudaStream_t s,
-                                bool capacitance) {
+                                bool capacitance, int* enqueued) {
     iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
     if (opts_in) opts = *opts_in;
+    if (enqueued) {
+        *enqueued = 0;
+        if (!(g && g->host_solves > 0 && !g->solve_graph_failed && opts.guess == 0 && opts.precond != 2 &&
+              !profiling_active())) {
+            *enqueued = -1;
+            return IIM_OK;
+        }
+    }
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (!g || !omega || !psi_out || (g->ncp > 0 && !psi_b) || (g->nb > 0 && !psibar)) return IIM_ERR_INVALID_ARG;
     if (opts.prec != IIM_FP64 && opts.prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
@@ -1787,33 +1849,12 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
             IIM_TRY(cudaMemcpyAsync(g->h_pinned + 40, g->small + SM_REL, sizeof(double), cudaMemcpyDeviceToHost, s));
             IIM_TRY(cudaMemcpyAsync(g->h_pinned + 41, g->small + SM_CIRC_ERR, sizeof(double), cudaMemcpyDeviceToHost, s));
             IIM_TRY(cudaMemcpyAsync(g->h_pinned + 44, g->H + S.L.scal(), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (enqueued) {
+                *enqueued = 1;
+                return IIM_OK;
+            }
             IIM_TRY(cudaStreamSynchronize(s));
-            const double rel = g->h_pinned[40];
-            iim_status st = IIM_OK;
-            if (hi[DI_NONFIN]) {
-                st = IIM_ERR_NONFINITE;
-            } else if (hi[DI_LOOPERR] || hi[DI_CYCERR]) {
-                snprintf(g_last_error, sizeof(g_last_error), "GMRES loop ended by its iteration cap");
-                st = IIM_ERR_NOT_CONVERGED;
-            } else if (rel > opts.rtol) {
-                st = IIM_ERR_NOT_CONVERGED;
-            }
-            count_launches(G->k_top + (long long)hi[DI_REF] * G->k_ref + (long long)hi[DI_CYCS] * G->k_cyc +
-                           (long long)hi[DI_ITS] * G->k_it + (long long)hi[DI_RSS] * G->k_rs);
-            if (stats) {
-                stats->iters = hi[DI_ITS];
-                stats->refinements = hi[DI_REF];
-                stats->fallback = 0;
-                stats->status = st;
-                stats->rel_res = rel;
-                const double bn = g->h_pinned[44 + SC_TOL] / std::max(inner, 1e-300);
-                stats->gmres_rel_res = S.ns > 0 && bn > 0.0 ? g->h_pinned[44 + SC_RESID] / bn : 0.0;
-                stats->circ_err_max = g->h_pinned[41];
-                stats->seed_rel_res = 1.0;
-                stats->iters_first = hi[DI_FIRST];
-                cudaEventElapsedTime(&stats->ms, g->ev0, g->ev1);
-            }
-            return st;
+            return graph_finish(g, opts, stats);
         }
     }
     IIM_TRY(cudaEventRecord(g->ev0, s));
