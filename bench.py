@@ -33,7 +33,10 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
             "fixed-psibar body, solve to un-reduced FP64 relative residual 1e-10")
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2716464, "l2_bytes_per_launch": 17764531, "launches": 32,
+                                 "source_hash": "164b25de869fec34",
+                                 "note": "mean over the 32 column-pass launches of two profiled solves, caches "
+                                         "flushed by ncu before each launch"}}
 
 
 def kernel_source_hash():
@@ -571,9 +574,11 @@ def main():
         per_launch_s = dom["ms"] * 1e-3 / dom["launches"]
         achieved = dom["bytes"] / dom["launches"] / per_launch_s / 1e9
         tr = NCU_TRAFFIC.get(dom["name"])
-        traffic = tr["bytes_per_launch"] if tr and tr.get("source_hash") == kernel_source_hash() else None
+        valid = bool(tr) and tr.get("source_hash") == kernel_source_hash()
+        traffic = tr["bytes_per_launch"] if valid else None
+        l2_traffic = tr.get("l2_bytes_per_launch") if valid else None
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "l2_traffic": l2_traffic, "peak_source": src,
                 "alg_bytes_per_launch": dom["bytes"] / dom["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None,
                 "timing": "single-problem step, CUDA events around each launch on its stream"}
