@@ -33,8 +33,8 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
             "fixed-psibar body, solve to un-reduced FP64 relative residual 1e-10")
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
-NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2716464, "l2_bytes_per_launch": 17764531, "launches": 32,
-                                 "source_hash": "164b25de869fec34",
+NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722056, "l2_bytes_per_launch": 11776399, "launches": 32,
+                                 "tile_width": 8, "source_hash": "164b25de869fec34",
                                  "note": "mean over the 32 column-pass launches of two profiled solves, caches "
                                          "flushed by ncu before each launch"}}
 
@@ -66,6 +66,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess leg")
     ap.add_argument("--no-rk3", action="store_true", help="skip the RK3 step leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 multi-body leg")
+    ap.add_argument("--tiles", type=int, default=0, help="column-pass tile width (0: tuned on the batch)")
     return ap.parse_args()
 
 
@@ -536,7 +537,13 @@ def main():
     # ---- concurrency autotuning of the batched form (untimed)
     n_streams = B
     tuned = None
-    if B > 1:
+    tile_w, tiles_tuned = 4, None
+    if args.tiles:
+        tile_w = args.tiles
+        for gg in geos:
+            iim.iim_geometry_set_tiles(gg, tile_w)
+    elif B > 1:
+        tile_w, tiles_tuned = autotune.tune_tiles_batch(geos, lambda: solve_batch(B))
         n_streams, tuned = autotune.tune_streams(solve_batch, tuple(c for c in (1, 2, 4, 8, 12, 16) if c <= B))
     # ---- chosen form: B problems per step in flight (the timed region), clocks sampled
     with ClockSampler(local) as clk:
@@ -574,7 +581,7 @@ def main():
         per_launch_s = dom["ms"] * 1e-3 / dom["launches"]
         achieved = dom["bytes"] / dom["launches"] / per_launch_s / 1e9
         tr = NCU_TRAFFIC.get(dom["name"])
-        valid = bool(tr) and tr.get("source_hash") == kernel_source_hash()
+        valid = bool(tr) and tr.get("source_hash") == kernel_source_hash() and tr.get("tile_width") == tile_w
         traffic = tr["bytes_per_launch"] if valid else None
         l2_traffic = tr.get("l2_bytes_per_launch") if valid else None
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -660,6 +667,7 @@ def main():
                    "refinements": statistics.mean(s["refinements"] for s in stats),
                    "final_rel_res_max": max(s["rel_res"] for s in stats), "setup_s": t_setup,
                    "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms, "streams_tuning_ms": tuned,
+                   "tile_width": tile_w, "tile_tuning_ms": tiles_tuned,
                    "n_control": geo.n_control, "n_affected": geo.n_affected},
         "roofline": roof,
         "kernels": [{"name": r["name"], "launches_per_step": r["launches"] / kprof, "ms_per_step": r["ms"] / kprof,

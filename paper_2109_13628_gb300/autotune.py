@@ -42,6 +42,22 @@ def tune_tiles(geoms, solve_one, widths=(2, 4, 8), reps=2):
     return best
 
 
+def tune_tiles_batch(geoms, run_batch, widths=(4, 8), reps=2):
+    """One tile width for all geometries, chosen by timing the whole batch `run_batch()` (the
+    throughput mode: the best width for one solve alone need not be the best when many share
+    the GPU).  Applies the choice and returns (width, {width: ms})."""
+    times = {}
+    for w in widths:
+        for g in geoms:
+            B.iim_geometry_set_tiles(g, w)
+        run_batch()                     # the solve graphs are rebuilt for the new kernels
+        times[w] = _time(run_batch, reps)
+    best = min(times, key=times.get)
+    for g in geoms:
+        B.iim_geometry_set_tiles(g, best)
+    return best, times
+
+
 def tune_streams(run_batch, candidates=(1, 2, 4, 8, 12, 16, 24)):
     """The number of worker streams for which `run_batch(n_streams)` is fastest."""
     times = {c: _time(lambda: run_batch(c), 1) for c in candidates}
