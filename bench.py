@@ -34,14 +34,15 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
 NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722056, "l2_bytes_per_launch": 11776399, "launches": 32,
-                                 "tile_width": 8, "source_hash": "164b25de869fec34",
+                                 "tile_width": 8, "source_hash": "9127a99058e9074b",
                                  "note": "mean over the 32 column-pass launches of two profiled solves, caches "
                                          "flushed by ncu before each launch"}}
 
 
 def kernel_source_hash():
+    """Hash of the files holding the transform kernels and their launch configuration."""
     h = hashlib.sha256()
-    for f in ("dst.cuh", "solve.cu", "common.cuh"):
+    for f in ("dst.cuh", "solve.cu"):
         with open(os.path.join(ROOT, "paper_2109_13628_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -598,18 +599,22 @@ def main():
         h_out = [[torch.empty(NXY, dtype=torch.float64).pin_memory() for _ in range(3)] for _ in range(B)]
         d_in = [(torch.empty_like(omega), torch.empty_like(psi_b), torch.empty_like(ring)) for _ in range(B)]
 
+        h_pbar = [torch.zeros(1, dtype=torch.float64).pin_memory() for _ in range(B)]
+
         def e2e_step():
+            if B > 1:
+                # host buffers straight through the C ABI: per-problem copies overlap other solves
+                iim.iim_poisson_solve_batched_host(geos, [h_omega] * B, [h_psib] * B, [h_ring] * B, None, h_pbar,
+                                                   [h[0] for h in h_out], [h[1] for h in h_out],
+                                                   [h[2] for h in h_out], opts=opts_for(iim.IIM_MIXED),
+                                                   n_streams=n_streams)
+                return
             for d in d_in:
                 d[0].copy_(h_omega, non_blocking=True)
                 d[1].copy_(h_psib, non_blocking=True)
                 d[2].copy_(h_ring, non_blocking=True)
-            if B > 1:
-                iim.iim_poisson_solve_batched(geos, [d[0] for d in d_in], [d[1] for d in d_in], [d[2] for d in d_in],
-                                              None, psibars, psis, uxs, uys, opts=opts_for(iim.IIM_MIXED),
-                                              n_streams=n_streams)
-            else:
-                iim.iim_poisson_solve(geo, d_in[0][0], d_in[0][1], d_in[0][2], None, psibars[0], psis[0], uxs[0],
-                                      uys[0], opts=opts_for(iim.IIM_MIXED))
+            iim.iim_poisson_solve(geo, d_in[0][0], d_in[0][1], d_in[0][2], None, psibars[0], psis[0], uxs[0],
+                                  uys[0], opts=opts_for(iim.IIM_MIXED))
             for k in range(B):
                 for h, d in zip(h_out[k], (psis[k], uxs[k], uys[k])):
                     h.copy_(d, non_blocking=True)

@@ -183,6 +183,20 @@ iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const dou
                                      const iim_opts* opts, iim_stats* stats, int n_streams,
                                      iim_stream stream);
 
+/* iim_poisson_solve_batched on HOST buffers: every array argument (omega, psi_b, psi_box,
+ * gamma, psibar in/out, psi_out, ux_out, uy_out) is host memory, preferably page-locked so
+ * that the copies run asynchronously.  Each problem's inputs are copied to device staging
+ * arrays kept with its geometry (allocated on the first such call), solved, and its outputs
+ * copied back, all on the problem's stream, so the copies of some problems overlap the solves
+ * of others.  Returns when every output is in host memory.  Same errors as
+ * iim_poisson_solve_batched. */
+iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, const double* const* omega,
+                                          const double* const* psi_b, const double* const* psi_box,
+                                          const double* const* gamma, double* const* psibar,
+                                          double* const* psi_out, double* const* ux_out,
+                                          double* const* uy_out, const iim_opts* opts, iim_stats* stats,
+                                          int n_streams, iim_stream stream);
+
 /* Tile width of the column pass of the geometry's rectangular solves: 2, 4 or 8 columns per
  * block (FP32 transforms use 4 or 8, FP64 transforms 2 or 4; the nearest supported width is
  * taken).  Chosen per grid size by the autotuner of the Python package.  Errors:

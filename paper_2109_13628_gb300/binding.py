@@ -65,6 +65,8 @@ SIGNATURES = [
     ("iim_build_preconditioner", _i, [_vp, ctypes.POINTER(ctypes.c_float), _vp]),
     ("iim_poisson_solve_batched", _i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
                                        _vp, _i, _vp]),
+    ("iim_poisson_solve_batched_host", _i, [_i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                            ctypes.POINTER(iim_opts), _vp, _i, _vp]),
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
     ("iim_geometry_set_lines", _i, [_vp, _i]),
     ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
@@ -228,13 +230,29 @@ def iim_geometry_set_lines(g: "Geometry", threads_per_line: int):
     _check(load().iim_geometry_set_lines(g.handle, int(threads_per_line)), "iim_geometry_set_lines")
 
 
-def _ptr_array(tensors, dtype, sizes, name):
+def _host_ptr(t, dtype=None, numel=None, name="tensor"):
+    """Host pointer of a contiguous CPU tensor (or None); page-locked memory lets the copies run
+    asynchronously."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"{name} must be a CPU tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _ptr_array(tensors, dtype, sizes, name, host=False):
     """Host array of device pointers (NULL entries allowed) or None when every entry is None."""
     if tensors is None or all(t is None for t in tensors):
         return None
     arr = (_vp * len(tensors))()
     for k, (t, n) in enumerate(zip(tensors, sizes)):
-        p = _ptr(t, dtype, n, f"{name}[{k}]")
+        p = (_host_ptr if host else _ptr)(t, dtype, n, f"{name}[{k}]")
         arr[k] = p.value if p is not None else None
     return arr
 
@@ -258,6 +276,30 @@ def iim_poisson_solve_batched(geoms, omega, psi_b, psi_box, gamma, psibar, psi_o
         ctypes.byref(o), stats, int(n_streams), _stream(stream))
     if check:
         _check(st, "iim_poisson_solve_batched")
+    return st, [stats[k].as_dict() for k in range(n)]
+
+
+def iim_poisson_solve_batched_host(geoms, omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out=None, uy_out=None,
+                                   opts: "iim_opts | None" = None, n_streams=8, stream=None, check=True):
+    """iim_poisson_solve_batched on host (CPU, preferably pinned) tensors: copies in, solves and
+    copies out per problem on its stream; returns (status, [stats dicts])."""
+    n = len(geoms)
+    f64 = torch.float64
+    nxy = [(g.grid.nx - 1) * (g.grid.ny - 1) for g in geoms]
+    G = (_vp * n)(*[g.handle.value if isinstance(g.handle, ctypes.c_void_p) else g.handle for g in geoms])
+    stats = (iim_stats * n)()
+    o = opts if opts is not None else default_opts()
+    none = [None] * n
+    st = load().iim_poisson_solve_batched_host(
+        n, G, _ptr_array(omega, f64, nxy, "omega", True),
+        _ptr_array(psi_b, f64, [g.n_control for g in geoms], "psi_b", True),
+        _ptr_array(psi_box or none, f64, [2 * (g.grid.nx + g.grid.ny) for g in geoms], "psi_box", True),
+        _ptr_array(gamma or none, f64, [g.n_bodies for g in geoms], "gamma", True),
+        _ptr_array(psibar, f64, [g.n_bodies for g in geoms], "psibar", True),
+        _ptr_array(psi_out, f64, nxy, "psi_out", True), _ptr_array(ux_out or none, f64, nxy, "ux_out", True),
+        _ptr_array(uy_out or none, f64, nxy, "uy_out", True), ctypes.byref(o), stats, int(n_streams), _stream(stream))
+    if check:
+        _check(st, "iim_poisson_solve_batched_host")
     return st, [stats[k].as_dict() for k in range(n)]
 
 

@@ -110,3 +110,173 @@ extern "C" iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms
         if (status[k] != IIM_OK) return status[k];
     return IIM_OK;
 }
+
+// ---- the same on host buffers: each problem's inputs are copied in, solved and its outputs
+// copied back on the problem's stream, so the copies of some problems overlap the solves of
+// others.  Device staging arrays live in the geometry (allocated on first use).
+namespace {
+struct IoView {
+    double *omega, *psi_b, *ring, *gamma, *psibar, *psi, *ux, *uy;
+};
+iim_status io_view(iim_geometry g, IoView* v) {
+    const size_t nxy = (size_t)g->NX * g->NY, ncp = (size_t)std::max(g->ncp, 1), nring = 2 * (size_t)(g->nx + g->ny),
+                 nb = (size_t)std::max(g->nb, 1);
+    if (!g->io) IIM_TRY(cudaMalloc(&g->io, sizeof(double) * (4 * nxy + ncp + nring + 2 * nb)));
+    double* p = g->io;
+    v->omega = p; p += nxy;
+    v->psi = p; p += nxy;
+    v->ux = p; p += nxy;
+    v->uy = p; p += nxy;
+    v->psi_b = p; p += ncp;
+    v->ring = p; p += nring;
+    v->gamma = p; p += nb;
+    v->psibar = p;
+    return IIM_OK;
+}
+}  // namespace
+
+extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, const double* const* omega,
+                                                     const double* const* psi_b, const double* const* psi_box,
+                                                     const double* const* gamma, double* const* psibar,
+                                                     double* const* psi_out, double* const* ux_out,
+                                                     double* const* uy_out, const iim_opts* opts, iim_stats* stats,
+                                                     int n_streams, iim_stream stream) {
+    if (n < 0 || (n > 0 && (!geoms || !omega || !psi_out || !psibar || !psi_b))) return IIM_ERR_INVALID_ARG;
+    if (n == 0) return IIM_OK;
+    if (n_streams < 1) n_streams = 1;
+    n_streams = std::min(n_streams, std::min(n, 64));
+    for (int k = 0; k < n; ++k)
+        if (!geoms[k]) return IIM_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k)
+        for (int l = k + 1; l < n; ++l)
+            if (geoms[k] == geoms[l]) return IIM_ERR_INVALID_ARG;
+    std::vector<IoView> io(n);
+    for (int k = 0; k < n; ++k) IIM_CHECK(io_view(geoms[k], &io[k]));
+    int dev = 0;
+    IIM_TRY(cudaGetDevice(&dev));
+    cudaStream_t cs = (cudaStream_t)stream;
+    std::vector<int> order(n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (long)geoms[a]->nx * geoms[a]->ny > (long)geoms[b]->nx * geoms[b]->ny;
+    });
+    cudaEvent_t start = nullptr;
+    IIM_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    IIM_TRY(cudaEventRecord(start, cs));
+    std::vector<cudaStream_t> ws(n_streams, nullptr);
+    std::vector<cudaEvent_t> done(n_streams, nullptr);
+    iim_status setup_st = IIM_OK;
+    for (int t = 0; t < n_streams && setup_st == IIM_OK; ++t) {
+        if (cudaStreamCreateWithFlags(&ws[t], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done[t], cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamWaitEvent(ws[t], start, 0) != cudaSuccess)
+            setup_st = IIM_ERR_CUDA;
+    }
+    auto copy_in = [&](int k, cudaStream_t s) -> iim_status {
+        iim_geometry g = geoms[k];
+        const size_t nxy = (size_t)g->NX * g->NY;
+        IIM_TRY(cudaMemcpyAsync(io[k].omega, omega[k], sizeof(double) * nxy, cudaMemcpyHostToDevice, s));
+        if (g->ncp > 0)
+            IIM_TRY(cudaMemcpyAsync(io[k].psi_b, psi_b[k], sizeof(double) * g->ncp, cudaMemcpyHostToDevice, s));
+        if (psi_box && psi_box[k])
+            IIM_TRY(cudaMemcpyAsync(io[k].ring, psi_box[k], sizeof(double) * 2 * (g->nx + g->ny),
+                                    cudaMemcpyHostToDevice, s));
+        if (gamma && gamma[k] && g->nb > 0)
+            IIM_TRY(cudaMemcpyAsync(io[k].gamma, gamma[k], sizeof(double) * g->nb, cudaMemcpyHostToDevice, s));
+        if (g->nb > 0)
+            IIM_TRY(cudaMemcpyAsync(io[k].psibar, psibar[k], sizeof(double) * g->nb, cudaMemcpyHostToDevice, s));
+        return IIM_OK;
+    };
+    auto copy_out = [&](int k, cudaStream_t s) -> iim_status {
+        iim_geometry g = geoms[k];
+        const size_t nxy = (size_t)g->NX * g->NY;
+        IIM_TRY(cudaMemcpyAsync(psi_out[k], io[k].psi, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+        if (ux_out && ux_out[k])
+            IIM_TRY(cudaMemcpyAsync(ux_out[k], io[k].ux, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+        if (uy_out && uy_out[k])
+            IIM_TRY(cudaMemcpyAsync(uy_out[k], io[k].uy, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+        if (g->nb > 0)
+            IIM_TRY(cudaMemcpyAsync(psibar[k], io[k].psibar, sizeof(double) * g->nb, cudaMemcpyDeviceToHost, s));
+        return IIM_OK;
+    };
+    auto dev_args = [&](int k, const double** ring, const double** gam, double** ux, double** uy) {
+        *ring = (psi_box && psi_box[k]) ? io[k].ring : nullptr;
+        *gam = (gamma && gamma[k]) ? io[k].gamma : nullptr;
+        *ux = (ux_out && ux_out[k]) ? io[k].ux : nullptr;
+        *uy = (uy_out && uy_out[k]) ? io[k].uy : nullptr;
+    };
+    std::vector<iim_status> status(n, IIM_OK);
+    std::vector<int> enq(n, -1);
+    std::vector<iim_stats> stb(n);
+    for (int q = 0; q < n && setup_st == IIM_OK; ++q) {
+        const int k = order[q];
+        cudaStream_t s = ws[q % n_streams];
+        int e = -1;
+        const double* ring;
+        const double* gam;
+        double *ux, *uy;
+        dev_args(k, &ring, &gam, &ux, &uy);
+        // the graph path applies after a first solve on the geometry: ask before copying
+        iim_geometry g = geoms[k];
+        const bool graph_ready = g->host_solves > 0 && !g->solve_graph_failed;
+        if (!graph_ready) continue;
+        status[k] = copy_in(k, s);
+        if (status[k] == IIM_OK)
+            status[k] = solve_enqueue(g, io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, io[k].psi, ux, uy, opts,
+                                      &stb[k], s, &e);
+        if (status[k] == IIM_OK && e >= 0) status[k] = copy_out(k, s);
+        enq[k] = status[k] == IIM_OK ? e : 0;
+        if (enq[k] < 0) enq[k] = -2;   // copied in but not solved: solved by a worker below
+    }
+    std::vector<int> rest;
+    for (int q = 0; q < n; ++q)
+        if (enq[order[q]] < 0) rest.push_back(order[q]);
+    std::atomic<int> next{0};
+    auto worker = [&](int t) {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= (int)rest.size()) break;
+            const int k = rest[q];
+            const double* ring;
+            const double* gam;
+            double *ux, *uy;
+            dev_args(k, &ring, &gam, &ux, &uy);
+            iim_status st = enq[k] == -2 ? IIM_OK : copy_in(k, ws[t]);
+            iim_stats sk;
+            if (st == IIM_OK)
+                st = iim_poisson_solve(geoms[k], io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, io[k].psi, ux, uy,
+                                       nullptr, opts, &sk, (iim_stream)ws[t]);
+            if (st == IIM_OK) st = copy_out(k, ws[t]);
+            status[k] = st;
+            stb[k] = sk;
+        }
+        cudaEventRecord(done[t], ws[t]);
+    };
+    if (setup_st == IIM_OK) {
+        std::vector<std::thread> pool;
+        const int nthreads = rest.empty() ? 1 : n_streams;
+        for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+        worker(0);
+        for (auto& th : pool) th.join();
+        for (int t = 1; t < n_streams; ++t)
+            if (t >= nthreads) cudaEventRecord(done[t], ws[t]);
+        for (int t = 0; t < n_streams; ++t) {
+            cudaStreamSynchronize(ws[t]);
+            cudaStreamWaitEvent(cs, done[t], 0);
+        }
+        for (int k = 0; k < n; ++k)
+            if (enq[k] == 1) status[k] = solve_finish(geoms[k], opts, &stb[k]);
+        if (stats)
+            for (int k = 0; k < n; ++k) stats[k] = stb[k];
+    }
+    for (int t = 0; t < n_streams; ++t) {
+        if (done[t]) cudaEventDestroy(done[t]);
+        if (ws[t]) cudaStreamDestroy(ws[t]);
+    }
+    cudaEventDestroy(start);
+    if (setup_st != IIM_OK) return setup_st;
+    for (int k = 0; k < n; ++k)
+        if (status[k] != IIM_OK) return status[k];
+    return IIM_OK;
+}

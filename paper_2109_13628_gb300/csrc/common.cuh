@@ -170,6 +170,7 @@ struct iim_geometry_s {
     // the whole solve as one graph (device-driven refinement; see solve.cu), its key, and the
     // number of host-driven solves done on this geometry (the first solve always runs on the host)
     void* solve_graph = nullptr;
+    double* io = nullptr;        // device staging of the host-buffer batched solve (on first use)
     int host_solves = 0;
     int solve_graph_failed = 0;
     cudaStream_t cap_stream = nullptr;   // private stream used only to capture graphs
