@@ -153,7 +153,7 @@ struct iim_geometry_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // dense Schur-complement preconditioner: [S | S^-1] row-major ns x 2ns (FP32), scratch
     float* pc_aug = nullptr;
-    float* pc_f = nullptr;
+    float* pc_f = nullptr;   // Gauss-Jordan scratch (gj_scratch_floats)
     int* pc_info = nullptr;
     double* pc_z = nullptr;      // 2 ns
     int pc_ready = 0;
@@ -187,7 +187,9 @@ iim_status solve_enqueue(iim_geometry g, const double* omega, const double* psi_
                          const iim_opts* opts, iim_stats* stats, cudaStream_t s, int* enqueued);
 iim_status solve_finish(iim_geometry g, const iim_opts* opts, iim_stats* stats);
 // dense Schur-complement preconditioner (precond.cu)
-iim_status gj_invert_aug(float* A, int n, float* f, int* info, cudaStream_t s);
+// [S | I] -> [I | S^-1] in place; scratch holds gj_scratch_floats(n) floats
+size_t gj_scratch_floats(int n);
+iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_t s);
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
                         int accumulate, const int* stop, cudaStream_t s);
 __global__ void k_unit_vector(int n, int j, double* v);

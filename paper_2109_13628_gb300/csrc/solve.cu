@@ -1053,14 +1053,14 @@ struct Solver {
     }
 
     // ---- dense Schur-complement preconditioner: columns S e_j from FP32 operator applications,
-    // then [S | I] -> [I | S^-1] by Gauss-Jordan with partial pivoting (FP32)
+    // then [S | I] -> [I | S^-1] by blocked Gauss-Jordan with partial pivoting (FP32)
     iim_status build_precond() {
         if (g->pc_ready) return IIM_OK;
         const int n = ns;
         const long ld = ns;
         if (!g->pc_aug) {
             IIM_TRY(cudaMalloc(&g->pc_aug, sizeof(float) * 2 * (size_t)n * n));
-            IIM_TRY(cudaMalloc(&g->pc_f, sizeof(float) * (size_t)n));
+            IIM_TRY(cudaMalloc(&g->pc_f, sizeof(float) * gj_scratch_floats(n)));
             IIM_TRY(cudaMalloc(&g->pc_info, sizeof(int)));
             IIM_TRY(cudaMalloc(&g->pc_z, sizeof(double) * 2 * (size_t)n));
         }
