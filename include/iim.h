@@ -289,6 +289,21 @@ iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma, double* ps
                         double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
                         iim_stream stream);
 
+/* iim_rk3_step with a wall velocity that changes during the step, as for a body whose rotation
+ * rate follows a prescribed law (the Navier-Stokes convergence study of Sec. 6.1 drives the
+ * cylinder's wall with the Lamb-Oseen velocity at the current time).  Stage st (0, 1, 2) of the
+ * Williamson scheme sits at time t + c_st dt, c = (0, 1/3, 3/4), and uses
+ *   u_b + c_st dt u_b_rate.
+ *   u_b_rate       2 |C| values (du_b/dt, u_x then u_y), device; required
+ * Everything else as iim_rk3_step (u_b NULL = zero at the start of the step).  A wall velocity
+ * linear in time over one step keeps the scheme third order in time.
+ * Errors: those of iim_rk3_step; IIM_ERR_INVALID_ARG when u_b_rate is NULL. */
+iim_status iim_rk3_step_moving_wall(iim_geometry g, double* omega, double* gamma, double* psibar,
+                                    const double* u_b, const double* u_b_rate, const double* psi_b,
+                                    const double* psi_box, const double Uinf[2], double nu, double c_stab,
+                                    double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
+                                    iim_stream stream);
+
 /* ---- Learned initial guess (no counterpart in the paper).  A fully convolutional network of
  * 3x3 dilated convolutions (zero padding, ReLU between layers, BF16 weights, FP32 accumulation)
  * maps per-pixel inputs to one output channel; trained with a masked mean-squared error and

@@ -254,10 +254,12 @@ def region_flux(S: op.Setup, Fx, Fy, region):
 
 
 def rk3_step(T: TransportSetup, omega, gamma, u_b, Uinf, nu, c_stab, dt=None, psi_b=None, psi_box=None,
-             psibar=None):
+             psibar=None, u_b_rate=None):
     """One low-storage RK3 step (Sec. 5.5): per stage, velocity reconstruction (Sec. 4.2) with
     Gamma_k, vorticity BC, transport RHS and Kelvin RHS, then the Williamson update of (omega,
-    Gamma).  Returns (omega, gamma, dt, psibar)."""
+    Gamma).  With u_b_rate (du_b/dt, same layout as u_b) the wall velocity of stage s is
+    u_b + c_s dt u_b_rate at the stage time t + c_s dt (a wall driven by a law in time, as in
+    the convergence study of Sec. 6.1).  Returns (omega, gamma, dt, psibar)."""
     S = T.S
     P = S.prob
     fluid = P.phi[1:-1, 1:-1] >= 0
@@ -276,7 +278,10 @@ def rk3_step(T: TransportSetup, omega, gamma, u_b, Uinf, nu, c_stab, dt=None, ps
             ux, uy = op.velocity(S, psi, pb)
             if s == 0 and dt is None:
                 dt = c_stab * dt_max(ux, uy, nu, S.h, fluid)
-            rhs, Fx, Fy, _ = transport_rhs(T, w, ux, uy, u_b, Uinf, nu)
+            ub = u_b
+            if u_b_rate is not None:
+                ub = (u_b[0] + RK3_C[s] * dt * u_b_rate[0], u_b[1] + RK3_C[s] * dt * u_b_rate[1])
+            rhs, Fx, Fy, _ = transport_rhs(T, w, ux, uy, ub, Uinf, nu)
             grhs = kelvin_rhs(S, Fx, Fy)
             dw = RK3_A[s] * dw + dt * rhs
             dg = RK3_A[s] * dg + dt * grhs

@@ -82,6 +82,8 @@ SIGNATURES = [
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
     ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
                           ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
+    ("iim_rk3_step_moving_wall", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d,
+                                      ctypes.POINTER(_d), ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
     ("iim_last_error_message", ctypes.c_char_p, []),
     ("iim_launch_count", ctypes.c_longlong, []),
     ("iim_profile_begin", _i, []),
@@ -404,4 +406,24 @@ def iim_rk3_step(g: Geometry, omega, gamma, psibar, u_b, psi_b, psi_box, Uinf, n
                              ctypes.byref(dtc), ctypes.byref(o), stats, _stream(stream))
     if check:
         _check(st, "iim_rk3_step")
+    return dtc.value, [stats[k].as_dict() for k in range(3)], st
+
+
+def iim_rk3_step_moving_wall(g: Geometry, omega, gamma, psibar, u_b, u_b_rate, psi_b, psi_box, Uinf, nu, c_stab,
+                             dt=0.0, opts: iim_opts | None = None, stream=None, check=True):
+    """iim_rk3_step with the wall velocity u_b + c dt u_b_rate at each stage time t + c dt."""
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
+    dtc = _d(float(dt))
+    stats = (iim_stats * 3)()
+    o = opts if opts is not None else default_opts()
+    st = load().iim_rk3_step_moving_wall(
+        g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(gamma, f64, g.n_bodies, "gamma"),
+        _ptr(psibar, f64, g.n_bodies, "psibar"), _ptr(u_b, f64, 2 * g.n_control, "u_b"),
+        _ptr(u_b_rate, f64, 2 * g.n_control, "u_b_rate"), _ptr(psi_b, f64, g.n_control, "psi_b"),
+        _ptr(psi_box, f64, 2 * (g.grid.nx + g.grid.ny), "psi_box"), U, float(nu), float(c_stab), ctypes.byref(dtc),
+        ctypes.byref(o), stats, _stream(stream))
+    if check:
+        _check(st, "iim_rk3_step_moving_wall")
     return dtc.value, [stats[k].as_dict() for k in range(3)], st

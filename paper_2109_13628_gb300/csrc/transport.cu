@@ -321,13 +321,13 @@ __global__ void k_speed_max(long n, const double* __restrict__ ux, const double*
 
 // Transport workspace inside g->tr_buf (doubles).
 struct TrWork {
-    double *w, *ux, *uy, *dw, *g4, *g3, *g3n, *wb, *dG, *part, *psi, *vx, *vy, *zeros, *dgdt;
+    double *w, *ux, *uy, *dw, *g4, *g3, *g3n, *wb, *dG, *part, *psi, *vx, *vy, *zeros, *dgdt, *ub_stage;
 };
 
 static iim_status tr_work(iim_geometry g, TrWork* W) {
     const size_t npad = (size_t)g->nx * g->NY, n = (size_t)g->NX * g->NY, nm = (size_t)std::max(g->nminus, 1),
                  ncp = (size_t)std::max(g->ncp, 1);
-    const size_t total = 4 * npad + 3 * nm + ncp + 64 + 1024 + 3 * n + ncp + 64;
+    const size_t total = 4 * npad + 3 * nm + ncp + 64 + 1024 + 3 * n + ncp + 64 + 2 * ncp;
     if (!g->tr_buf) {
         IIM_TRY(cudaMalloc(&g->tr_buf, total * sizeof(double)));
         IIM_TRY(cudaMemset(g->tr_buf, 0, total * sizeof(double)));
@@ -348,6 +348,7 @@ static iim_status tr_work(iim_geometry g, TrWork* W) {
     W->vy = p; p += n;
     W->zeros = p; p += ncp;
     W->dgdt = p; p += 64;
+    W->ub_stage = p; p += 2 * ncp;
     return IIM_OK;
 }
 
@@ -411,10 +412,20 @@ extern "C" iim_status iim_transport_rhs(iim_geometry g, const double* omega, con
     return IIM_OK;
 }
 
-extern "C" iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma, double* psibar, const double* u_b,
-                                   const double* psi_b, const double* psi_box, const double Uinf[2], double nu,
-                                   double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
-                                   iim_stream stream) {
+// Stage times of the Williamson scheme: stage st sees the state at t + kRK3C[st] dt.
+static constexpr double kRK3C[3] = {0.0, 1.0 / 3.0, 3.0 / 4.0};
+
+// u_b at a stage time: u_b + c dt du_b/dt (u_b NULL = 0)
+__global__ void k_ub_stage(int m, const double* __restrict__ ub, const double* __restrict__ rate, double cdt,
+                           double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < m) out[e] = (ub ? ub[e] : 0.0) + cdt * rate[e];
+}
+
+static iim_status rk3_step(iim_geometry g, double* omega, double* gamma, double* psibar, const double* u_b,
+                           const double* u_b_rate, const double* psi_b, const double* psi_box, const double Uinf[2],
+                           double nu, double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
+                           iim_stream stream) {
     if (!g || !omega || !dt_inout || !(nu >= 0.0) || (g->nb > 0 && (!gamma || !psibar))) return IIM_ERR_INVALID_ARG;
     if (*dt_inout <= 0.0 && !(c_stab > 0.0)) return IIM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
@@ -443,7 +454,15 @@ extern "C" iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma,
             const double h = g->h;
             dt = c_stab / (U / (kStabC * h) + nu / (kStabR * h * h));
         }
-        IIM_CHECK(prepare_stage(g, W, v, omega, W.vx, W.vy, u_b, nullptr, nullptr, s));
+        const double* ub = u_b;
+        if (u_b_rate) {
+            const int m = 2 * g->ncp;
+            if (m > 0)
+                launch("tr_ub_stage", 0.0, 0.0, k_ub_stage, (unsigned)((m + 255) / 256), 256, 0, s, m, u_b, u_b_rate,
+                       kRK3C[st] * dt, W.ub_stage);
+            ub = W.ub_stage;
+        }
+        IIM_CHECK(prepare_stage(g, W, v, omega, W.vx, W.vy, ub, nullptr, nullptr, s));
         launch("tr_rhs", 40.0 * (double)n, 0.0, k_transport_rhs, (unsigned)((n + 255) / 256), 256, 0, s, v, nu, 1,
                kRK3A[st], dt, (double*)nullptr, W.dw);
         if (g->nb > 0)
@@ -456,4 +475,22 @@ extern "C" iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma,
     IIM_TRY(cudaStreamSynchronize(s));
     *dt_inout = dt;
     return IIM_OK;
+}
+
+extern "C" iim_status iim_rk3_step(iim_geometry g, double* omega, double* gamma, double* psibar, const double* u_b,
+                                   const double* psi_b, const double* psi_box, const double Uinf[2], double nu,
+                                   double c_stab, double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
+                                   iim_stream stream) {
+    return rk3_step(g, omega, gamma, psibar, u_b, nullptr, psi_b, psi_box, Uinf, nu, c_stab, dt_inout, opts, per_stage,
+                    stream);
+}
+
+extern "C" iim_status iim_rk3_step_moving_wall(iim_geometry g, double* omega, double* gamma, double* psibar,
+                                               const double* u_b, const double* u_b_rate, const double* psi_b,
+                                               const double* psi_box, const double Uinf[2], double nu, double c_stab,
+                                               double* dt_inout, const iim_opts* opts, iim_stats* per_stage,
+                                               iim_stream stream) {
+    if (!u_b_rate) return IIM_ERR_INVALID_ARG;
+    return rk3_step(g, omega, gamma, psibar, u_b, u_b_rate, psi_b, psi_box, Uinf, nu, c_stab, dt_inout, opts,
+                    per_stage, stream);
 }

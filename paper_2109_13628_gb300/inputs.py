@@ -110,6 +110,66 @@ def lamb_oseen(X, Y, x0, y0, gamma, nu_t):
     return w, -f * dy, f * dx
 
 
+def psi_lamb_oseen(X, Y, x0, y0, gamma, nu_t):
+    """Lamb-Oseen streamfunction for u = (d psi/dy, -d psi/dx), additive constant dropped:
+    psi = -(gamma / 4 pi) [ln r^2 + E1(r^2 / (4 nu t))] (r > 0)."""
+    from scipy.special import exp1
+    r2 = (X - x0) ** 2 + (Y - y0) ** 2
+    return -(gamma / (4.0 * math.pi)) * (np.log(r2) + exp1(r2 / (4.0 * nu_t)))
+
+
+def lamb_oseen_rate(X, Y, x0, y0, gamma, nu, t):
+    """Time derivative of the Lamb-Oseen velocity (Eq. lovelocity) at time t."""
+    dx, dy = X - x0, Y - y0
+    r2 = dx * dx + dy * dy
+    ft = -gamma * np.exp(-r2 / (4.0 * nu * t)) / (8.0 * math.pi * nu * t * t)
+    return -ft * dy, ft * dx
+
+
+def _rotated_cylinder_integral(kernel, t):
+    from scipy import integrate
+    from scipy import special as sp
+    x_max = math.sqrt(40.0 / t)   # e^-40 beyond
+
+    def f(x):
+        j1, y1 = sp.j1(x), sp.y1(x)
+        return kernel(x, j1, y1, sp) / (j1 * j1 + y1 * y1) * math.exp(-x * x * t)
+
+    v, _ = integrate.quad(f, 0.0, x_max, limit=4000, epsabs=1e-13, epsrel=1e-11)
+    return 2.0 / math.pi * v
+
+
+def rotated_cylinder_vorticity(r, t):
+    """Impulsively rotated cylinder (App. D, the real form of its vorticity integral), in the
+    units r* = r/R, t* = nu t / R^2, omega* = omega / Omega:
+    omega*(r, t) = (2/pi) int_0^inf (J0(xr) Y1(x) - J1(x) Y0(xr)) / (J1(x)^2 + Y1(x)^2) e^{-x^2 t} dx."""
+    return _rotated_cylinder_integral(lambda x, j1, y1, sp: sp.j0(x * r) * y1 - j1 * sp.y0(x * r), t)
+
+
+def rotated_cylinder_velocity(r, t):
+    """u_theta / (Omega R) of the same flow (App. D, real form):
+    u*(r, t) = 1/r + (2/pi) int_0^inf (J1(xr) Y1(x) - J1(x) Y1(xr)) / (J1(x)^2 + Y1(x)^2) e^{-x^2 t} / x dx."""
+    return 1.0 / r + _rotated_cylinder_integral(lambda x, j1, y1, sp: (sp.j1(x * r) * y1 - j1 * sp.y1(x * r)) / x, t)
+
+
+ROTATED_CYLINDER = dict(R=0.5, omega=1.0, re=50.0, xc=0.013, yc=0.007, half=2.0, c_stab=0.5)
+
+
+def rotated_cylinder(n: int) -> Problem:
+    """Impulsively rotated cylinder (Sec. 6.2): box [-2,2]^2 with n x n cells, cylinder R = 0.5
+    (centre slightly off the grid's symmetry lines), fluid at rest at t = 0, Re = R^2 Omega / nu
+    = 50; the body is in circulation mode with zero psi_b and zero initial circulation.  The box
+    is Dirichlet with psi = 0: the fluid's total circulation is zero at every t, so the flow at
+    the box is exponentially small while the vorticity stays within a few sqrt(nu t) of the wall."""
+    c = ROTATED_CYLINDER
+    g = square_grid(n, c["half"])
+    X, Y = g.nodes()
+    phi = phi_circle(X, Y, c["xc"], c["yc"], c["R"])
+    return Problem(grid=g, phi=phi, regions=[region_around(g, phi)], modes=[1], omega=np.zeros((n - 1, n - 1)),
+                   psi_box=np.zeros(4 * n), psi_b_fn=lambda x, y, body: np.zeros_like(x), psibar=np.zeros(1),
+                   gamma=np.zeros(1), exact=None, name=f"rotated_cylinder_{n}")
+
+
 # ----------------------------------------------------------------------------- manufactured
 def psi_c1(X, Y):
     """Streamfunction of the single-cylinder manufactured case: sin(pi x/2) sin(pi y/2) + 0.1 log r."""
@@ -294,6 +354,28 @@ def c2_cylinder_flow(nx: int = 1024, ny: int = 512, seed: int = 0) -> Problem:
     return Problem(grid=g, phi=phi, regions=[region_around(g, phi)], modes=[1], omega=omega,
                    psi_box=box_ring(g, 1.0 * Y), psi_b_fn=lambda x, y, body: np.zeros_like(x),
                    psibar=np.zeros(1), gamma=None, exact=None, name=f"c2_cylinder_flow_{nx}x{ny}")
+
+
+LAMB_OSEEN_CYLINDER = dict(gamma=math.pi, nu=1e-3, xc=0.507, yc=0.507, R=0.15, t0=1.0, c_stab=0.7)
+
+
+def lamb_oseen_cylinder(n: int, t: float | None = None) -> Problem:
+    """Navier-Stokes convergence workload (Sec. 6.1 and its parameter table): unit box with
+    n x n cells, cylinder R = 0.15 at (0.507, 0.507) whose wall moves with the velocity of a
+    Lamb-Oseen vortex (Gamma = pi, nu = 1e-3) centred on it, the vortex's vorticity at time t
+    (default t0 = 1) outside the cylinder.  The box is Dirichlet with the vortex streamfunction
+    (at the box the vortex is potential to e^-30, so this data does not change in time); the
+    body is in circulation mode with zero psi_b (the wall is a streamline)."""
+    c = LAMB_OSEEN_CYLINDER
+    t = c["t0"] if t is None else t
+    g = Grid(0.0, 1.0, 0.0, 1.0, n, n)
+    X, Y = g.nodes()
+    phi = phi_circle(X, Y, c["xc"], c["yc"], c["R"])
+    w, _, _ = lamb_oseen(X, Y, c["xc"], c["yc"], c["gamma"], c["nu"] * t)
+    psi = psi_lamb_oseen(X, Y, c["xc"], c["yc"], c["gamma"], c["nu"] * t)
+    return Problem(grid=g, phi=phi, regions=[region_around(g, phi)], modes=[1], omega=_mask_interior(g, phi, w),
+                   psi_box=box_ring(g, psi), psi_b_fn=lambda x, y, body: np.zeros_like(x), psibar=np.zeros(1),
+                   gamma=None, exact=psi, name=f"lamb_oseen_cylinder_{n}")
 
 
 def batched_c4(count: int = 96, seed: int = 2, sizes=(128, 256, 512, 1024)):

@@ -179,3 +179,27 @@ def test_rk3_third_order_in_time():
     errs = [np.abs(run(dt, steps) - ref).max() for dt, steps in ((0.04, 2), (0.02, 4), (0.01, 8))]
     orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(orders) > 2.6, (errs, orders)
+
+
+def test_rk3_stage_times_integrate_quadratics_exactly():
+    """The stage times c = (0, 1/3, 3/4) belong to the Williamson coefficients (Sec. 5.5): the
+    2N-storage update of y' = p(t), with p read at t + c_s dt, integrates every polynomial of
+    degree <= 2 exactly (third order) and misses t^3, and each stage's state is y at its stage
+    time for linear p (so a wall velocity linear in time is seen at the right time).  A wrong c
+    or a wrong A/B pairing breaks one of these."""
+    def integrate(p, t, dt):
+        y, dy, states = 0.0, 0.0, []
+        for s in range(3):
+            states.append(y)
+            dy = tr.RK3_A[s] * dy + dt * p(t + tr.RK3_C[s] * dt)
+            y += tr.RK3_B[s] * dy
+        return y, states
+
+    t, dt = 0.3, 0.7
+    for k in range(3):
+        y, _ = integrate(lambda x: (k + 1) * x ** k, t, dt)
+        assert abs(y - ((t + dt) ** (k + 1) - t ** (k + 1))) < 1e-14
+    y3, _ = integrate(lambda x: 4 * x ** 3, t, dt)
+    assert abs(y3 - ((t + dt) ** 4 - t ** 4)) > 1e-3
+    _, states = integrate(lambda x: 1.0, t, dt)
+    assert np.allclose(states, [c * dt for c in tr.RK3_C], atol=1e-15)
