@@ -177,6 +177,45 @@ def rotated_cylinder_run(n, t_stars, precond=1):
     return out
 
 
+TB = inputs.TRANSPORT_BODY
+
+
+def transport_run(n, nu, t_end):
+    """Transport only (Sec. 3.3, adapted): the library's transport right-hand side (conservative
+    fluxes, IIM boundary treatment with the exact omega_b and u_b on the non-convex body) for
+    the constant velocity (1, 2), advanced by the Williamson RK3 at 0.9 of the stable step;
+    errors of the Gaussian blob at t_end over the fluid nodes (Eqs. l2, linf)."""
+    P = inputs.transport_body(n, nu)
+    g = P.grid
+    h = g.h
+    u = TB["u"]
+    geo = gu.setup(P)
+    cp = iim.iim_geometry_control_points(geo)
+    cx, cy = cp["x"].cpu().numpy(), cp["y"].cpu().numpy()
+    NXY = (g.nx - 1) * (g.ny - 1)
+    ux = torch.full((NXY,), u[0], dtype=torch.float64, device=gu.dev())
+    uy = torch.full((NXY,), u[1], dtype=torch.float64, device=gu.dev())
+    ub = gu.T(np.concatenate([np.full(cx.size, u[0]), np.full(cx.size, u[1])]))
+    dt_max = 1.0 / ((abs(u[0]) + abs(u[1])) / (1.620 * h) + nu / (0.314 * h * h))
+    steps = max(1, math.ceil(t_end / (TB["c_stab"] * dt_max)))
+    dt = t_end / steps
+    w = gu.T(P.omega.ravel())
+    dw = torch.zeros_like(w)
+    rhs = torch.empty_like(w)
+    for k in range(steps):
+        for s in range(3):
+            wb = gu.T(inputs.transported_gaussian(cx, cy, nu, (k + tr.RK3_C[s]) * dt))
+            iim.iim_transport_rhs(geo, w, ux, uy, ub, u, nu, rhs, omega_b_in=wb)
+            dw.mul_(tr.RK3_A[s]).add_(rhs, alpha=dt)
+            w.add_(dw, alpha=tr.RK3_B[s])
+    X, Y = g.interior()
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    e = np.abs(w.cpu().numpy().reshape(X.shape) - inputs.transported_gaussian(X, Y, nu, t_end))[fl]
+    geo.close()
+    return {"n": n, "nu": nu, "re_h": (abs(u[0]) + abs(u[1])) * h / nu, "steps": steps, "w_inf": float(e.max()),
+            "w_l2": float(h * np.sqrt((e ** 2).sum()))}
+
+
 def orders(errs, key):
     return [math.log2(errs[i][key] / errs[i + 1][key]) for i in range(len(errs) - 1)]
 
@@ -204,9 +243,21 @@ def test_rotated_cylinder_moment_second_order():
     assert math.log2(rel[0] / rel[1]) > 1.8, rel
 
 
+def test_transport_third_order_advective_second_order_diffusive():
+    """Sec. 3.3: with Re_h > 1 the transport scheme's error falls at third order (dt ~ h makes
+    the RK3 error third order too); with Re_h < 1 at second order."""
+    adv = [transport_run(n, 0.002, 0.5) for n in (512, 1024)]
+    dif = [transport_run(n, 0.064, 0.1) for n in (512, 1024)]
+    assert min(orders(adv, "w_inf") + orders(adv, "w_l2")) > 2.5, adv
+    assert min(orders(dif, "w_inf") + orders(dif, "w_l2")) > 1.8, dif
+
+
 if __name__ == "__main__":
     # the convergence tables quoted in the design notes: python tests/test_gpu_navier_stokes.py
     import json
+    for nu, t_end in ((0.002, 0.5), (0.064, 0.1)):
+        for n in (512, 1024, 2048):
+            print(json.dumps({"case": "transport_body", **transport_run(n, nu, t_end)}), flush=True)
     for n in (128, 256, 512, 1024):
         print(json.dumps({"case": "lamb_oseen_cylinder", **lamb_oseen_run(n, 1.2)}), flush=True)
     ts = (0.005, 0.01, 0.02, 0.045)
