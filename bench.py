@@ -33,8 +33,8 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
             "fixed-psibar body, solve to un-reduced FP64 relative residual 1e-10")
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
-NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722056, "l2_bytes_per_launch": 11776399, "launches": 32,
-                                 "tile_width": 8, "source_hash": "9127a99058e9074b",
+NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2721928, "l2_bytes_per_launch": 11787382, "launches": 32,
+                                 "tile_width": 8, "source_hash": "f5b6f4b6eebfdd55",
                                  "note": "mean over the 32 column-pass launches of two profiled solves, caches "
                                          "flushed by ncu before each launch"}}
 
@@ -622,7 +622,9 @@ def main():
         ems, _ = timed(e2e_step, args.steps, args.warmup)
         e_total, e_solves = replica_totals(sum(ems), B * args.steps, dev)
         e2e = {"value": e_solves / (e_total * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": B * 8 * (NXY + psi_b.numel() + ring.numel()), "d2h_bytes_per_step": B * 8 * 3 * NXY}
+               "h2d_bytes_per_step": B * 8 * (NXY + psi_b.numel() + ring.numel()), "d2h_bytes_per_step": B * 8 * 3 * NXY,
+               "path": "inputs copied from pinned host memory per problem stream; psi, u_x, u_y written into the "
+                       "pinned host arrays by each solve's last kernel (B > 1) or copied back (B = 1)"}
     # ---- mixed-size batched workload (96 problems, 128^2 .. 1024^2)
     c4 = None
     if not args.no_c4:

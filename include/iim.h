@@ -188,7 +188,10 @@ iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const dou
  * that the copies run asynchronously.  Each problem's inputs are copied to device staging
  * arrays kept with its geometry (allocated on the first such call), solved, and its outputs
  * copied back, all on the problem's stream, so the copies of some problems overlap the solves
- * of others.  Returns when every output is in host memory.  Same errors as
+ * of others.  When a problem's psi_out (and ux_out, uy_out if given) are page-locked host
+ * memory the device can address at the same pointer (cudaHostAlloc / cudaHostRegister under
+ * unified addressing), the solve's last kernel writes them there directly instead (no staging
+ * or copy).  Returns when every output is in host memory.  Same errors as
  * iim_poisson_solve_batched. */
 iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, const double* const* omega,
                                           const double* const* psi_b, const double* const* psi_box,

@@ -135,6 +135,17 @@ iim_status io_view(iim_geometry g, IoView* v) {
 }
 }  // namespace
 
+// p lies in page-locked host memory that kernels can write through the same address
+static bool device_writable_host(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == p;
+}
+
 extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, const double* const* omega,
                                                      const double* const* psi_b, const double* const* psi_box,
                                                      const double* const* gamma, double* const* psibar,
@@ -152,6 +163,12 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
             if (geoms[k] == geoms[l]) return IIM_ERR_INVALID_ARG;
     std::vector<IoView> io(n);
     for (int k = 0; k < n; ++k) IIM_CHECK(io_view(geoms[k], &io[k]));
+    // Outputs in page-locked host memory that the device can address (mapped under unified
+    // addressing) are written there by the solve's last kernel; others are staged and copied.
+    std::vector<char> direct(n, 0);
+    for (int k = 0; k < n; ++k)
+        direct[k] = device_writable_host(psi_out[k]) && (!ux_out || !ux_out[k] || device_writable_host(ux_out[k])) &&
+                    (!uy_out || !uy_out[k] || device_writable_host(uy_out[k]));
     int dev = 0;
     IIM_TRY(cudaGetDevice(&dev));
     cudaStream_t cs = (cudaStream_t)stream;
@@ -190,20 +207,23 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
     auto copy_out = [&](int k, cudaStream_t s) -> iim_status {
         iim_geometry g = geoms[k];
         const size_t nxy = (size_t)g->NX * g->NY;
-        IIM_TRY(cudaMemcpyAsync(psi_out[k], io[k].psi, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
-        if (ux_out && ux_out[k])
-            IIM_TRY(cudaMemcpyAsync(ux_out[k], io[k].ux, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
-        if (uy_out && uy_out[k])
-            IIM_TRY(cudaMemcpyAsync(uy_out[k], io[k].uy, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+        if (!direct[k]) {
+            IIM_TRY(cudaMemcpyAsync(psi_out[k], io[k].psi, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+            if (ux_out && ux_out[k])
+                IIM_TRY(cudaMemcpyAsync(ux_out[k], io[k].ux, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+            if (uy_out && uy_out[k])
+                IIM_TRY(cudaMemcpyAsync(uy_out[k], io[k].uy, sizeof(double) * nxy, cudaMemcpyDeviceToHost, s));
+        }
         if (g->nb > 0)
             IIM_TRY(cudaMemcpyAsync(psibar[k], io[k].psibar, sizeof(double) * g->nb, cudaMemcpyDeviceToHost, s));
         return IIM_OK;
     };
-    auto dev_args = [&](int k, const double** ring, const double** gam, double** ux, double** uy) {
+    auto dev_args = [&](int k, const double** ring, const double** gam, double** psi, double** ux, double** uy) {
         *ring = (psi_box && psi_box[k]) ? io[k].ring : nullptr;
         *gam = (gamma && gamma[k]) ? io[k].gamma : nullptr;
-        *ux = (ux_out && ux_out[k]) ? io[k].ux : nullptr;
-        *uy = (uy_out && uy_out[k]) ? io[k].uy : nullptr;
+        *psi = direct[k] ? psi_out[k] : io[k].psi;
+        *ux = (ux_out && ux_out[k]) ? (direct[k] ? ux_out[k] : io[k].ux) : nullptr;
+        *uy = (uy_out && uy_out[k]) ? (direct[k] ? uy_out[k] : io[k].uy) : nullptr;
     };
     std::vector<iim_status> status(n, IIM_OK);
     std::vector<int> enq(n, -1);
@@ -214,16 +234,16 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
         int e = -1;
         const double* ring;
         const double* gam;
-        double *ux, *uy;
-        dev_args(k, &ring, &gam, &ux, &uy);
+        double *psi, *ux, *uy;
+        dev_args(k, &ring, &gam, &psi, &ux, &uy);
         // the graph path applies after a first solve on the geometry: ask before copying
         iim_geometry g = geoms[k];
         const bool graph_ready = g->host_solves > 0 && !g->solve_graph_failed;
         if (!graph_ready) continue;
         status[k] = copy_in(k, s);
         if (status[k] == IIM_OK)
-            status[k] = solve_enqueue(g, io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, io[k].psi, ux, uy, opts,
-                                      &stb[k], s, &e);
+            status[k] = solve_enqueue(g, io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, psi, ux, uy, opts, &stb[k],
+                                      s, &e);
         if (status[k] == IIM_OK && e >= 0) status[k] = copy_out(k, s);
         enq[k] = status[k] == IIM_OK ? e : 0;
         if (enq[k] < 0) enq[k] = -2;   // copied in but not solved: solved by a worker below
@@ -240,12 +260,12 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
             const int k = rest[q];
             const double* ring;
             const double* gam;
-            double *ux, *uy;
-            dev_args(k, &ring, &gam, &ux, &uy);
+            double *psi, *ux, *uy;
+            dev_args(k, &ring, &gam, &psi, &ux, &uy);
             iim_status st = enq[k] == -2 ? IIM_OK : copy_in(k, ws[t]);
             iim_stats sk;
             if (st == IIM_OK)
-                st = iim_poisson_solve(geoms[k], io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, io[k].psi, ux, uy,
+                st = iim_poisson_solve(geoms[k], io[k].omega, io[k].psi_b, ring, gam, io[k].psibar, psi, ux, uy,
                                        nullptr, opts, &sk, (iim_stream)ws[t]);
             if (st == IIM_OK) st = copy_out(k, ws[t]);
             status[k] = st;

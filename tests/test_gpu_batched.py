@@ -76,26 +76,37 @@ def test_autotuner_picks_supported_tiles():
 
 @pytest.mark.parametrize("precond", [0, 1])
 def test_batched_host_buffers_equal_device_batch(precond):
-    """iim_poisson_solve_batched_host on pinned host tensors gives exactly the device batch's
-    results, on a first call (host-driven solves) and on later calls (whole-solve graphs)."""
+    """iim_poisson_solve_batched_host on host tensors gives exactly the device batch's results
+    (psi, u, psibar), on a first call (host-driven solves) and on later calls (whole-solve
+    graphs); outputs in pinned memory are written there by the last kernel, pageable outputs
+    are staged and copied -- both paths are exercised."""
     problems = inputs.batched_c4(count=8, seed=5, sizes=(64, 128, 256))
     kept, geos, a = build_batch(problems)
     opts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11, precond=precond)
+    ux = [torch.empty_like(t) for t in a["psi"]]
+    uy = [torch.empty_like(t) for t in a["psi"]]
     st, ref_stats = iim.iim_poisson_solve_batched(geos, a["omega"], a["psi_b"], None, a["gamma"], a["psibar"],
-                                                  a["psi"], opts=opts, n_streams=3)
+                                                  a["psi"], ux, uy, opts=opts, n_streams=3)
     assert st == iim.IIM_OK
     pin = lambda t: t.cpu().pin_memory()
     h_om = [pin(t) for t in a["omega"]]
     h_pb = [pin(t) for t in a["psi_b"]]
     h_gm = [pin(t) for t in a["gamma"]]
-    for call in range(3):
+    for call in range(4):
+        pinned = call % 2 == 0
+        out = lambda t: (torch.full((t.numel(),), np.nan, dtype=torch.float64).pin_memory() if pinned
+                         else torch.full((t.numel(),), np.nan, dtype=torch.float64))
         h_pbar = [torch.zeros(t.numel(), dtype=torch.float64).pin_memory() for t in a["psibar"]]
-        h_psi = [torch.full((t.numel(),), np.nan, dtype=torch.float64).pin_memory() for t in a["psi"]]
-        st, stats = iim.iim_poisson_solve_batched_host(geos, h_om, h_pb, None, h_gm, h_pbar, h_psi, opts=opts,
-                                                       n_streams=3)
+        h_psi = [out(t) for t in a["psi"]]
+        h_ux = [out(t) for t in a["psi"]]
+        h_uy = [out(t) for t in a["psi"]]
+        st, stats = iim.iim_poisson_solve_batched_host(geos, h_om, h_pb, None, h_gm, h_pbar, h_psi, h_ux, h_uy,
+                                                       opts=opts, n_streams=3)
         assert st == iim.IIM_OK
         for k in range(len(kept)):
             assert torch.equal(h_psi[k], a["psi"][k].cpu()), (call, k)
+            assert torch.equal(h_ux[k], ux[k].cpu()), (call, k)
+            assert torch.equal(h_uy[k], uy[k].cpu()), (call, k)
             assert torch.equal(h_pbar[k], a["psibar"][k].cpu())
             assert stats[k]["iters"] == ref_stats[k]["iters"]
     for g in geos:
