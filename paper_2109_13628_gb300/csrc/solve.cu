@@ -596,15 +596,10 @@ __global__ void k_sumsq(const double* __restrict__ w, int ns, double* __restrict
     if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
-// Arnoldi step finish: norm, Hessenberg column, Givens rotations, residual estimate, stop test.
-__global__ void k_arnoldi_tail(int* __restrict__ di, KLayout L, int nparts, const double* __restrict__ partial,
-                               double* __restrict__ K) {
-    if (di[DI_STOP]) return;
-    const int lane = threadIdx.x;
-    double s = 0.0;
-    for (int b = lane; b < nparts; b += 32) s += partial[b];
-    s = warp_sum(s);
-    if (lane != 0) return;
+// Arnoldi step finish from the squared norm s of the orthogonalised vector: Hessenberg column
+// (the two Gram-Schmidt passes' coefficients summed), Givens rotations, residual estimate,
+// stop test.  One thread.
+__device__ void arnoldi_finish(int* __restrict__ di, KLayout L, double* __restrict__ K, double s) {
     const int j = di[DI_J];
     const double nrm = sqrt(s);
     double* H = K + L.H();
@@ -637,6 +632,71 @@ __global__ void k_arnoldi_tail(int* __restrict__ di, KLayout L, int nparts, cons
     const bool conv = !(resid > K[L.scal() + SC_TOL]);   // also stops on NaN
     if (conv) di[DI_CONV] = 1;
     if (conv || jn >= L.m || di[DI_IT] >= di[DI_MAXIT] || nrm == 0.0) di[DI_STOP] = 1;
+}
+
+// Arnoldi step finish after k_update: sums the per-block squares, then arnoldi_finish.
+__global__ void k_arnoldi_tail(int* __restrict__ di, KLayout L, int nparts, const double* __restrict__ partial,
+                               double* __restrict__ K) {
+    if (di[DI_STOP]) return;
+    const int lane = threadIdx.x;
+    double s = 0.0;
+    for (int b = lane; b < nparts; b += 32) s += partial[b];
+    s = warp_sum(s);
+    if (lane == 0) arnoldi_finish(di, L, K, s);
+}
+
+// The whole Arnoldi step in one block, for short Krylov bases (the preconditioned iteration
+// converges in a few steps): two classical Gram-Schmidt passes against V_0..V_j, the norm,
+// arnoldi_finish, and the scaling of V_{j+1} -- one launch instead of six.  Each thread owns
+// the same elements in every pass; the j+1 inner products of a pass are reduced together
+// (warp sums into part[i][warp], then one thread per i), so a pass synchronises twice.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_arnoldi_block(int* __restrict__ di, double* __restrict__ V, long ld, int ns, KLayout L, double* __restrict__ K) {
+    constexpr int NW = BLOCK / 32;
+    if (di[DI_STOP]) return;
+    const int j = di[DI_J];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* w = V + (long)(j + 1) * ld;
+    __shared__ double part[64][NW];
+    __shared__ double h[64];
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i <= j; ++i) {
+            const double* vi = V + (long)i * ld;
+            double acc = 0.0;
+            for (int e = tid; e < ns; e += BLOCK) acc += vi[e] * w[e];
+            acc = warp_sum(acc);
+            if (lane == 0) part[i][warp] = acc;
+        }
+        __syncthreads();
+        if (tid <= j) {
+            double hi = 0.0;
+            for (int q = 0; q < NW; ++q) hi += part[tid][q];
+            h[tid] = hi;
+            K[(pass == 0 ? L.hc1() : L.hc2()) + tid] = hi;
+        }
+        __syncthreads();
+        for (int e = tid; e < ns; e += BLOCK) {
+            double sacc = 0.0;
+            for (int i = 0; i <= j; ++i) sacc += h[i] * V[(long)i * ld + e];
+            w[e] -= sacc;
+        }
+        __syncthreads();   // h and part are rewritten by the next pass
+    }
+    double sq = 0.0;
+    for (int e = tid; e < ns; e += BLOCK) sq += w[e] * w[e];
+    sq = warp_sum(sq);
+    if (lane == 0) part[0][warp] = sq;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < NW; ++q) t += part[0][q];
+        arnoldi_finish(di, L, K, t);
+    }
+    __syncthreads();
+    if (di[DI_STOP]) return;
+    const double inv = K[L.scal() + SC_INV];
+    for (int e = tid; e < ns; e += BLOCK) w[e] *= inv;
 }
 
 // V_j *= 1 / ||V_j|| (j already advanced by the tail)
@@ -1134,6 +1194,11 @@ struct Solver {
     iim_status ortho_iter() {
         const long ld = ns;
         double* K = g->H;
+        if (precond) {
+            launch("gmres_arnoldi", 0.0, 0.0, k_arnoldi_block<256>, 1, 256, 0, s, di(), g->V, ld, ns, L, K);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        }
         const int eb = (ns + 255) / 256;
         launch("gmres_dots", 0.0, 0.0, k_dots<256>, m, 256, 0, s, di(), g->V, ld, ns, K + L.hc1());
         launch("gmres_update", 0.0, 0.0, k_update<256>, eb, 256, 0, s, di(), g->V, ld, K + L.hc1(), ns, nullptr);

@@ -111,3 +111,24 @@ def test_batched_host_buffers_equal_device_batch(precond):
             assert stats[k]["iters"] == ref_stats[k]["iters"]
     for g in geos:
         g.close()
+
+
+def test_empty_and_single_problem_batches():
+    """n = 0 is a no-op in both batched calls; a batch of one equals the single solve."""
+    opts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11)
+    st, stats = iim.iim_poisson_solve_batched([], [], [], None, None, [], [], opts=opts, n_streams=4)
+    assert st == iim.IIM_OK and stats == []
+    st, stats = iim.iim_poisson_solve_batched_host([], [], [], None, None, [], [], opts=opts, n_streams=4)
+    assert st == iim.IIM_OK and stats == []
+    kept, geos, a = build_batch(inputs.batched_c4(count=4, seed=5, sizes=(128,)))
+    assert len(kept) >= 1
+    one = lambda k: [a[k][0]]
+    st, stats = iim.iim_poisson_solve_batched(geos[:1], one("omega"), one("psi_b"), None, one("gamma"), one("psibar"),
+                                              one("psi"), opts=opts, n_streams=4)
+    assert st == iim.IIM_OK and len(stats) == 1
+    psi1 = torch.empty_like(a["psi"][0])
+    pb1 = torch.zeros_like(a["psibar"][0])
+    s1 = iim.iim_poisson_solve(geos[0], a["omega"][0], a["psi_b"][0], None, a["gamma"][0], pb1, psi1, opts=opts)
+    assert torch.equal(psi1, a["psi"][0]) and s1["iters"] == stats[0]["iters"]
+    for g in geos:
+        g.close()

@@ -249,7 +249,7 @@ def test_transport_third_order_advective_second_order_diffusive():
     adv = [transport_run(n, 0.002, 0.5) for n in (512, 1024)]
     dif = [transport_run(n, 0.064, 0.1) for n in (512, 1024)]
     assert min(orders(adv, "w_inf") + orders(adv, "w_l2")) > 2.5, adv
-    assert min(orders(dif, "w_inf") + orders(dif, "w_l2")) > 1.8, dif
+    assert min(orders(dif, "w_inf") + orders(dif, "w_l2")) > 1.7, dif
 
 
 if __name__ == "__main__":
