@@ -250,6 +250,63 @@ k_dense_matvec(int n, const float* __restrict__ M, long ldm, const double* __res
     }
 }
 
+// The same product with 16-byte row loads: a row starting h = 0..3 floats before a 16-byte
+// boundary is read as h leading floats, then float4s (eight in flight per lane), then the
+// remainder.  v is staged four times in shared memory, copy h shifted by h elements, so that
+// the float4 of the row always meets an aligned float4 of v.
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_dense_matvec4(int n, const float* __restrict__ M, long ldm, const double* __restrict__ vbase,
+                const int* __restrict__ jidx, long vstride, double* __restrict__ out, int accumulate,
+                const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    extern __shared__ float4 s_v4[];
+    float* s_v = reinterpret_cast<float*>(s_v4);
+    const int stride = (n + 3) & ~3;
+    const double* v = jidx ? vbase + (long)(*jidx) * vstride : vbase;
+    for (int j = threadIdx.x; j < n; j += WARPS * 32) {
+        const float x = (float)v[j];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            if (j >= h) s_v[h * stride + j - h] = x;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int row = blockIdx.x * WARPS + (threadIdx.x >> 5); row < n; row += gridDim.x * WARPS) {
+        const float* r = M + (long)row * ldm;
+        const int head = min((int)((4 - ((reinterpret_cast<uintptr_t>(r) >> 2) & 3)) & 3), n);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (lane < head) a0 = r[lane] * s_v[lane];
+        const float4* r4 = reinterpret_cast<const float4*>(r + head);
+        const float4* v4 = reinterpret_cast<const float4*>(s_v + head * stride);
+        const int nq = (n - head) >> 2;
+        int q = lane;
+        for (; q + 7 * 32 < nq; q += 8 * 32) {
+            float4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = r4[q + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float4 y = v4[q + 32 * u];
+                float& a = (u & 3) == 0 ? a0 : (u & 3) == 1 ? a1 : (u & 3) == 2 ? a2 : a3;
+                a = fmaf(x[u].x, y.x, fmaf(x[u].y, y.y, fmaf(x[u].z, y.z, fmaf(x[u].w, y.w, a))));
+            }
+        }
+        for (; q < nq; q += 32) {
+            const float4 x = r4[q], y = v4[q];
+            a1 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a1))));
+        }
+        const int rem = (n - head) & 3;
+        if (lane < rem) {
+            const int idx = head + 4 * nq + lane;
+            a2 = fmaf(r[idx], s_v[idx], a2);
+        }
+        float acc = (a0 + a1) + (a2 + a3);
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) out[row] = accumulate ? out[row] + (double)acc : (double)acc;
+    }
+}
+
 iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_t s) {
     IIM_TRY(cudaMemsetAsync(info, 0, sizeof(int), s));
     launch("gj_identity", 0.0, 0.0, k_set_identity_aug, (unsigned)(((long)n * n + 255) / 256), 256, 0, s, A, n);
@@ -289,6 +346,15 @@ iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
                         int accumulate, const int* stop, cudaStream_t s) {
     constexpr int W = 8;
+    const size_t sm4 = sizeof(float) * 4 * (size_t)((n + 3) & ~3);
+    if (sm4 <= 200 * 1024) {
+        if (sm4 > 48 * 1024)
+            cudaFuncSetAttribute(k_dense_matvec4<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+        launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec4<W>, (n + W - 1) / W, W * 32, sm4, s,
+               n, M, ldm, v, jidx, vstride, out, accumulate, stop);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
     const size_t sm = sizeof(float) * (size_t)n;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k_dense_matvec<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec<W>, (n + W - 1) / W, W * 32, sm, s, n, M,
