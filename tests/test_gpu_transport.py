@@ -166,3 +166,30 @@ def test_rk3_third_order_in_time_on_gpu():
     orders = [np.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert min(orders) > 2.6, (errs, orders)
     geo.close()
+
+
+def test_checkpoint_resume_repeats_next_step_bitwise(tmp_path):
+    """The integration state (Sec. 5.5: omega, Gamma_k, t; psibar_k kept as well) saved after
+    one RK3 step and loaded into a fresh geometry repeats the original run's next step bit for
+    bit."""
+    from paper_2109_13628_gb300 import checkpoint
+    P = inputs.c2_cylinder_flow(128, 64)
+    opts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11)
+    nu, Uinf, cst = 0.005, (1.0, 0.0), 0.5
+    ring = gu.T(P.psi_box)
+    geo = gu.setup(P)
+    w, gam = gu.T(P.omega.ravel()), gu.T(op.gamma_from_regions(P))
+    pbar = torch.zeros(1, dtype=torch.float64, device=gu.dev())
+    dt1, _, _ = iim.iim_rk3_step(geo, w, gam, pbar, None, None, ring, Uinf, nu, cst, opts=opts)
+    path = str(tmp_path / "flow")
+    checkpoint.save(path, {"omega": w, "gamma": gam, "psibar": pbar}, t=dt1, step=1, grid=P.grid, meta={"nu": nu})
+    dt2, _, _ = iim.iim_rk3_step(geo, w, gam, pbar, None, None, ring, Uinf, nu, cst, opts=opts)
+    geo.close()
+    state, hdr = checkpoint.load(path, device=gu.dev())
+    assert hdr["step"] == 1 and hdr["t"] == dt1
+    geo2 = gu.setup(P)
+    w2, gam2, pbar2 = state["omega"], state["gamma"], state["psibar"]
+    dt2b, _, _ = iim.iim_rk3_step(geo2, w2, gam2, pbar2, None, None, ring, Uinf, nu, cst, opts=opts)
+    assert dt2b == dt2
+    assert torch.equal(w2, w) and torch.equal(gam2, gam) and torch.equal(pbar2, pbar)
+    geo2.close()
