@@ -20,7 +20,9 @@ Modules
   transport      Sec. 3, Sec. 5.1, 5.3, 5.5, App. B: vorticity BC, conservative transport
                  RHS, Kelvin ODE, low-storage RK3, stable time step
 
-Parity status: every function is pinned by a test in tests/test_oracle_*.py except the
-vorticity boundary condition stencils (Sec. 5.3), whose figure is missing from the paper:
-parity unpinned (only its convergence order is checked).
+Parity status: every function is pinned by a test in tests/test_oracle_*.py.  The vorticity
+boundary condition stencils (Sec. 5.3) are a reading of a figure missing from the paper; they
+are pinned by what the paper does fix -- that they are second order: exact for quadratic
+velocity fields, and second-order convergent at every control point when fed the exact
+Lamb-Oseen velocity around the Sec. 6.1 cylinder.
 """

@@ -19,7 +19,8 @@ Readings of the paper used here (each listed in the design notes):
     (-3 u_b + 4 v1 - v2) / (2h) * s; both sides s = +1, -1 are averaged when both rows pairs
     are available (every node fluid, box or A-), one side is used when only it is; with
     neither, a first-order difference with one row, else 0.  y-lines: x and y swapped.
-    Parity unpinned against the paper (only polynomial exactness and convergence pin it).
+    Pinned by what the paper fixes, second order: exact for quadratic velocity, second-order
+    convergent at every control point on the exact Lamb-Oseen field (tests).
   * Box (the Dirichlet box replaces the paper's free-space / outflow conditions): velocity
     Uinf at and beyond the box; vorticity 0 at and beyond the box except at the right
     (outflow) edge, where it is copied from the last interior column (zero gradient).

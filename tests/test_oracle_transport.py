@@ -203,3 +203,24 @@ def test_rk3_stage_times_integrate_quadratics_exactly():
     assert abs(y3 - ((t + dt) ** 4 - t ** 4)) > 1e-3
     _, states = integrate(lambda x: 1.0, t, dt)
     assert np.allclose(states, [c * dt for c in tr.RK3_C], atol=1e-15)
+
+
+def test_vorticity_bc_second_order_with_exact_velocity():
+    """Sec. 5.3 stencils (this build's reading of the missing figure): fed the exact Lamb-Oseen
+    velocity around the Sec. 6.1 cylinder (extended into the body with u_b as the transport
+    step does), the wall vorticity converges at second order at every control point."""
+    c = inputs.LAMB_OSEEN_CYLINDER
+    errs = []
+    for n in (128, 256):
+        P = inputs.lamb_oseen_cylinder(n)
+        S = op.Setup(P)
+        T = tr.TransportSetup(S)
+        cp = S.geo["cp"]
+        X, Y = P.grid.nodes()
+        _, ux, uy = inputs.lamb_oseen(X, Y, c["xc"], c["yc"], c["gamma"], c["nu"] * c["t0"])
+        wex, bx, by = inputs.lamb_oseen(cp["x"], cp["y"], c["xc"], c["yc"], c["gamma"], c["nu"] * c["t0"])
+        uxb, uyb = tr.extended_velocity(T, ux[1:-1, 1:-1], uy[1:-1, 1:-1], (bx, by), (0.0, 0.0))
+        wb = tr.vorticity_bc(T, uxb, uyb, (bx, by))
+        errs.append(np.abs(wb - wex).max())
+    assert math.log2(errs[0] / errs[1]) > 1.8, errs
+    assert errs[1] < 0.1 * np.abs(wex).max(), errs
