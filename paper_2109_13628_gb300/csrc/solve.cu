@@ -727,6 +727,47 @@ __global__ void k_start_cycle(int ns, const double* __restrict__ r, double* __re
     }
 }
 
+// One block: beta = ||r||, V_0 = r / beta and the GMRES start state (k_start_cycle's work,
+// with the norm reduced inside the block instead of by k_sumsq's blocks).  With init_maxit >= 0
+// it first does what the norm / k_gmres_init launches do at the start of a correction: *norm2 =
+// ||r||^2, the counters reset, the tolerance set to tol * ||r||.  Five launches become one.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_start_block(int ns, const double* __restrict__ r, double* __restrict__ v0, KLayout L, double* __restrict__ K,
+              int* __restrict__ di, int init_maxit, double tol, double* __restrict__ norm2) {
+    __shared__ double s_inv;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) acc += r[e] * r[e];
+    acc = block_sum<BLOCK>(acc);
+    if (threadIdx.x == 0) {
+        if (init_maxit >= 0) {
+            *norm2 = acc;
+            di[DI_J] = 0;
+            di[DI_STOP] = 0;
+            di[DI_IT] = 0;
+            di[DI_MAXIT] = init_maxit;
+            di[DI_CONV] = 0;
+            di[DI_TMPJ] = 0;
+            di[DI_LOOP] = 0;
+            di[DI_LOOPERR] = 0;
+            K[L.scal() + SC_TOL] = tol * sqrt(acc);
+        }
+        const double beta = sqrt(acc);
+        double* gv = K + L.gv();
+        gv[0] = beta;
+        for (int i = 1; i <= L.m; ++i) gv[i] = 0.0;
+        K[L.scal() + SC_BETA] = beta;
+        K[L.scal() + SC_RESID] = beta;
+        di[DI_J] = 0;
+        di[DI_STOP] = (di[DI_IT] >= di[DI_MAXIT]) ? 1 : 0;
+        if (!(beta > K[L.scal() + SC_TOL])) { di[DI_CONV] = 1; di[DI_STOP] = 1; }
+        s_inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int e = threadIdx.x; e < ns; e += BLOCK) v0[e] = r[e] * inv;
+}
+
 // y = H^{-1} g over the first k = j columns (one warp)
 __global__ void k_backsolve(const int* __restrict__ di, KLayout L, double* __restrict__ K) {
     const int lane = threadIdx.x;
@@ -1335,11 +1376,18 @@ struct Solver {
         const long ld = ns_;
         const int eb = (ns_ + 255) / 256;
         IIM_TRY(cudaMemsetAsync(x, 0, (size_t)ns_ * sizeof(double), s));
-        launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
-        launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0, nullptr,
-               nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
-        launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), max_it, K, L, g->small + SM_NORM, tol);
         bool started = false;
+        if (!x0) {
+            // ||b||, counters, tolerance and V_0 = b / ||b|| in one block
+            launch("gmres_start", 0.0, 0.0, k_start_block<256>, 1, 256, 0, s, ns_, (const double*)g->bvec, V, L, K,
+                   di(), max_it, tol, g->small + SM_NORM);
+            started = true;
+        } else {
+            launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
+            launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0, nullptr,
+                   nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
+            launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), max_it, K, L, g->small + SM_NORM, tol);
+        }
         if (x0) {
             // r0 = b - S x0 (the restart path); kept only when ||r0|| < ||b||
             IIM_TRY(cudaMemcpyAsync(x, x0, (size_t)ns_ * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -1434,9 +1482,8 @@ struct Solver {
             launch("seed_scale", 0.0, 0.0, k_seed_scale<1024>, 1, 1024, 0, s, ns, (const double*)g->bvec, V + 2 * ld,
                    g->xsol, g->small + SM_SEED);
         launch("gmres_axpby", 0.0, 0.0, k_axpby, eb, 256, 0, s, ns, 1.0, g->bvec, -1.0, V + 2 * ld, V + 2 * ld);
-        launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, V + 2 * ld, ns, g->partial);
-        launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns, V + 2 * ld, V, L, K, kNormBlocks, g->partial,
-               di());
+        launch("gmres_start", 0.0, 0.0, k_start_block<256>, 1, 256, 0, s, ns, (const double*)(V + 2 * ld), V, L, K,
+               di(), -1, 0.0, (double*)nullptr);
         IIM_LAUNCHED();
         return IIM_OK;
     }
@@ -1509,14 +1556,8 @@ struct Solver {
             piece(ref_seg, [&]() -> iim_status {
                 IIM_CHECK(rhs<T>());
                 IIM_TRY(cudaMemsetAsync(x, 0, (size_t)ns_ * sizeof(double), s));
-                launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
-                launch("finish_norm", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kNormBlocks, g->partial, 0,
-                       nullptr, nullptr, 0.0, g->small, nullptr, nullptr, g->small + SM_NORM);
-                launch("gmres_init", 0.0, 0.0, k_gmres_init, 1, 1, 0, s, di(), o.max_iter, K, L, g->small + SM_NORM,
-                       inner);
-                launch("gmres_sumsq", 0.0, 0.0, k_sumsq<256>, kNormBlocks, 256, 0, s, g->bvec, ns_, g->partial);
-                launch("gmres_start", 0.0, 0.0, k_start_cycle, eb, 256, 0, s, ns_, g->bvec, g->V, L, K, kNormBlocks,
-                       g->partial, di());
+                launch("gmres_start", 0.0, 0.0, k_start_block<256>, 1, 256, 0, s, ns_, (const double*)g->bvec, g->V, L,
+                       K, di(), o.max_iter, inner, g->small + SM_NORM);
                 launch("cyc_begin", 0.0, 0.0, k_cyc_begin, 1, 1, 0, s, h_cyc, di(), o.max_iter);
                 IIM_LAUNCHED();
                 return IIM_OK;
