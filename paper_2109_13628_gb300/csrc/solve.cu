@@ -788,6 +788,39 @@ __global__ void k_backsolve(const int* __restrict__ di, KLayout L, double* __res
     }
 }
 
+// k_backsolve and the update in one block: warp 0 solves for y, then out = V y (accumulate 0)
+// or out += V y (accumulate 1) over the block -- the same operations in the same order as
+// k_backsolve followed by k_xupdate on a zeroed or the given out.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+k_backsolve_update(const int* __restrict__ di, KLayout L, double* __restrict__ K, const double* __restrict__ V,
+                   long ld, int ns, double* __restrict__ out, int accumulate) {
+    const int k = di[DI_J];
+    double* y = K + L.y();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const double* H = K + L.H();
+        const int ldh = L.m + 1;
+        const double* gv = K + L.gv();
+        for (int i = k - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int l = i + 1 + lane; l < k; l += 32) s += H[(long)l * ldh + i] * y[l];
+            s = warp_sum(s);
+            if (lane == 0) {
+                const double d = H[(long)i * ldh + i];
+                y[i] = d != 0.0 ? (gv[i] - s) / d : 0.0;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < ns; e += BLOCK) {
+        double s = 0.0;
+        for (int i = 0; i < k; ++i) s += y[i] * V[(long)i * ld + e];
+        out[e] = accumulate ? out[e] + s : 0.0 + s;
+    }
+}
+
 __global__ void k_xupdate(const int* __restrict__ di, const double* __restrict__ V, long ld, const double* __restrict__ y,
                           int ns, double* __restrict__ x) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1443,14 +1476,14 @@ struct Solver {
                     IIM_CHECK(read_state(st));
                 }
             }
-            launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
             if (precond) {
                 // x += M (V y)
                 double* t = g->pc_z + ns_;
-                IIM_TRY(cudaMemsetAsync(t, 0, (size_t)ns_ * sizeof(double), s));
-                launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, t);
+                launch("gmres_backsolve", 0.0, 0.0, k_backsolve_update<256>, 1, 256, 0, s, (const int*)di(), L, K,
+                       (const double*)V, ld, ns_, t, 0);
                 IIM_CHECK(dense_matvec(ns_, g->pc_aug + ns_, 2L * ns_, t, nullptr, 0, x, 1, nullptr, s));
             } else {
+                launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
                 launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), V, ld, K + L.y(), ns_, x);
             }
             IIM_LAUNCHED();
@@ -1580,13 +1613,13 @@ struct Solver {
                 return IIM_OK;
             });
             piece(cyc_seg, [&]() -> iim_status {
-                launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
                 if (precond) {
                     double* t = g->pc_z + ns_;
-                    IIM_TRY(cudaMemsetAsync(t, 0, (size_t)ns_ * sizeof(double), s));
-                    launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), g->V, ld, K + L.y(), ns_, t);
+                    launch("gmres_backsolve", 0.0, 0.0, k_backsolve_update<256>, 1, 256, 0, s, (const int*)di(), L, K,
+                           (const double*)g->V, ld, ns_, t, 0);
                     IIM_CHECK(dense_matvec(ns_, g->pc_aug + ns_, 2L * ns_, t, nullptr, 0, x, 1, nullptr, s));
                 } else {
+                    launch("gmres_backsolve", 0.0, 0.0, k_backsolve, 1, 32, 0, s, di(), L, K);
                     launch("gmres_xupdate", 0.0, 0.0, k_xupdate, eb, 256, 0, s, di(), g->V, ld, K + L.y(), ns_, x);
                 }
                 launch("cyc_ctl", 0.0, 0.0, k_cyc_ctl, 1, 1, 0, s, h_cyc, h_rs, di(), o.max_iter / m + 2);
