@@ -30,6 +30,10 @@ CASES = {
     # preconditioned mixed solve with a circulation body (capacitance correction in the graph)
     "precond_mixed_circulation": (lambda: inputs.c2_cylinder_flow(1024, 512),
                                   dict(prec=iim.IIM_MIXED, rtol=1e-10, precond=1), 1),
+    # preconditioned with restart 2: every correction runs several cycles, so the one-block
+    # GMRES start (restart residual) and back substitution run inside the cycle loop
+    "restarts_precond_mixed": (lambda: inputs.bicubic_bodies(128, seed=11, circulation=True),
+                               dict(prec=iim.IIM_MIXED, rtol=1e-11, restart=2, max_iter=4000, precond=1), 1),
     # no body: each refinement is one box solve
     "no_body": (lambda: _empty_box(128), dict(prec=iim.IIM_MIXED, rtol=1e-10), 0),
 }

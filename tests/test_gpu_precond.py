@@ -32,6 +32,11 @@ def test_preconditioned_solve_matches_oracle(n, prec):
     assert err < TOL[prec], (err, out["stats"])
     assert np.allclose(out["psibar"], pb_ref, rtol=TOL[prec], atol=TOL[prec] * np.abs(ref).max())
     assert out["stats"]["iters"] * 3 < plain["stats"]["iters"], (out["stats"], plain["stats"])
+    # restart 2: many cycles per correction (restart residuals, updates inside the cycle loop)
+    short = gu.solve_opts(P, geo, gamma=gam, opts=iim.default_opts(prec=prec, rtol=1e-13, max_iter=3000, restart=2,
+                                                                   precond=1))
+    err2 = np.abs(short["psi"] - ref[1:-1, 1:-1])[fl].max() / np.abs(ref).max()
+    assert err2 < TOL[prec], (err2, short["stats"])
     geo.close()
 
 
