@@ -349,14 +349,15 @@ iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const 
     const size_t sm4 = sizeof(float) * 4 * (size_t)((n + 3) & ~3);
     if (sm4 <= 200 * 1024) {
         if (sm4 > 48 * 1024)
-            cudaFuncSetAttribute(k_dense_matvec4<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4);
+            IIM_TRY(cudaFuncSetAttribute(k_dense_matvec4<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
         launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec4<W>, (n + W - 1) / W, W * 32, sm4, s,
                n, M, ldm, v, jidx, vstride, out, accumulate, stop);
         IIM_LAUNCHED();
         return IIM_OK;
     }
     const size_t sm = sizeof(float) * (size_t)n;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k_dense_matvec<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (sm > 48 * 1024)
+        IIM_TRY(cudaFuncSetAttribute(k_dense_matvec<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec<W>, (n + W - 1) / W, W * 32, sm, s, n, M,
            ldm, v, jidx, vstride, out, accumulate, stop);
     IIM_LAUNCHED();

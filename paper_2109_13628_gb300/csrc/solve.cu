@@ -120,20 +120,22 @@ static int tile_width(int requested) {
     return requested <= 2 ? 2 : 4;
 }
 
-// Raises a kernel's dynamic shared memory limit once per (device, kernel, size).
+// Raises a kernel's dynamic shared memory limit once per (device, kernel, size).  A failed
+// attribute call is reported (IIM_ERR_CUDA) and not recorded, so the next call tries again.
 static std::mutex g_attr_mutex;
 static std::vector<std::pair<std::pair<int, const void*>, size_t>> g_attr_done;
 
 template <typename KernelT>
-static void allow_smem(KernelT k, size_t bytes) {
+static iim_status allow_smem(KernelT k, size_t bytes) {
     int dev = 0;
-    cudaGetDevice(&dev);
+    IIM_TRY(cudaGetDevice(&dev));
     const void* key = (const void*)k;
     std::lock_guard<std::mutex> lock(g_attr_mutex);
     for (auto& e : g_attr_done)
-        if (e.first.first == dev && e.first.second == key && e.second >= bytes) return;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e.first.first == dev && e.first.second == key && e.second >= bytes) return IIM_OK;
+    IIM_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     g_attr_done.push_back({{dev, key}, bytes});
+    return IIM_OK;
 }
 
 static const VecArg kNoVec{nullptr, nullptr, 0, 0};
@@ -144,19 +146,20 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
                            double gsign, T* out, const int* stop, cudaStream_t s) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
-    auto go = [&](auto kern) {
-        allow_smem(kern, sm);
+    auto go = [&](auto kern) -> iim_status {
+        IIM_CHECK(allow_smem(kern, sm));
         launch(sizeof(T) == 8 ? "dst_rows_fwd_f64" : "dst_rows_fwd_f32",
                (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx), kern,
                (nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), kRowWarps * 32, sm, s, p.NX,
                p.NY, p.nx,
                p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
+        return IIM_OK;
     };
     const int fp = fft_path(p.nx, p.wide);
-    if (fp == 64) go(k_rows_fwd<T, kRowWarps, 64>);
-    else if (fp == 16) go(k_rows_fwd<T, kRowWarps, 16>);
-    else if (fp == 8) go(k_rows_fwd<T, kRowWarps, 8>);
-    else go(k_rows_fwd<T, kRowWarps, 0>);
+    if (fp == 64) IIM_CHECK(go(k_rows_fwd<T, kRowWarps, 64>));
+    else if (fp == 16) IIM_CHECK(go(k_rows_fwd<T, kRowWarps, 16>));
+    else if (fp == 8) IIM_CHECK(go(k_rows_fwd<T, kRowWarps, 8>));
+    else IIM_CHECK(go(k_rows_fwd<T, kRowWarps, 0>));
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -179,19 +182,20 @@ template <typename T, int C>
 static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
                             cudaStream_t s, int batch, long fstride) {
     const size_t sm = cols_smem<T>(p.ny, C);
-    auto go = [&](auto kern) {
-        allow_smem(kern, sm);
+    auto go = [&](auto kern) -> iim_status {
+        IIM_CHECK(allow_smem(kern, sm));
         launch(sizeof(T) == 8 ? "dst_cols_f64" : "dst_cols_f32",
                (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
                (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), kern, dim3(p.nx / C, batch),
                C * line_threads(fft_path(p.ny, p.wide)), sm, s,
                p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
+        return IIM_OK;
     };
     const int fp = fft_path(p.ny, p.wide);
-    if (fp == 64) go(k_cols<T, C, 64>);
-    else if (fp == 16) go(k_cols<T, C, 16>);
-    else if (fp == 8) go(k_cols<T, C, 8>);
-    else go(k_cols<T, C, 0>);
+    if (fp == 64) IIM_CHECK(go(k_cols<T, C, 64>));
+    else if (fp == 16) IIM_CHECK(go(k_cols<T, C, 16>));
+    else if (fp == 8) IIM_CHECK(go(k_cols<T, C, 8>));
+    else IIM_CHECK(go(k_cols<T, C, 0>));
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -202,8 +206,8 @@ static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T
                            long fstride = 0) {
     if (nrows <= 0) return IIM_OK;
     const size_t sm = rows_smem<T>(p.nx);
-    auto go = [&](auto kern) {
-        allow_smem(kern, sm);
+    auto go = [&](auto kern) -> iim_status {
+        IIM_CHECK(allow_smem(kern, sm));
         launch(sizeof(T) == 8 ? "dst_rows_inv_f64" : "dst_rows_inv_f32",
                (double)batch * nrows * p.NX *
                    (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
@@ -211,12 +215,13 @@ static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T
                dim3((nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), batch),
                kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw,
                stop, fstride);
+        return IIM_OK;
     };
     const int fp = fft_path(p.nx, p.wide);
-    if (fp == 64) go(k_rows_inv<T, kRowWarps, MODE, 64>);
-    else if (fp == 16) go(k_rows_inv<T, kRowWarps, MODE, 16>);
-    else if (fp == 8) go(k_rows_inv<T, kRowWarps, MODE, 8>);
-    else go(k_rows_inv<T, kRowWarps, MODE, 0>);
+    if (fp == 64) IIM_CHECK(go(k_rows_inv<T, kRowWarps, MODE, 64>));
+    else if (fp == 16) IIM_CHECK(go(k_rows_inv<T, kRowWarps, MODE, 16>));
+    else if (fp == 8) IIM_CHECK(go(k_rows_inv<T, kRowWarps, MODE, 8>));
+    else IIM_CHECK(go(k_rows_inv<T, kRowWarps, MODE, 0>));
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -2214,33 +2219,44 @@ __global__ void k_box_eigs(int NX, int NY, int nx, int ny, double h, int as_floa
 // Shared-memory limits of every transform kernel the allocation-free solve may launch (all
 // FFT paths), sized for the largest supported line.
 template <typename T>
-static void allow_noalloc_smem() {
+static iim_status allow_noalloc_smem() {
     const size_t rs = rows_smem<T>(kNoAllocMaxN), cs = cols_smem<T>(kNoAllocMaxN, 4);
-    allow_smem(k_rows_fwd<T, kRowWarps, 0>, rs);
-    allow_smem(k_rows_fwd<T, kRowWarps, 8>, rs);
-    allow_smem(k_rows_fwd<T, kRowWarps, 16>, rs);
-    allow_smem(k_cols<T, 4, 0>, cs);
-    allow_smem(k_cols<T, 4, 8>, cs);
-    allow_smem(k_cols<T, 4, 16>, cs);
-    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 0>, rs);
-    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 8>, rs);
-    allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 16>, rs);
+    IIM_CHECK(allow_smem(k_rows_fwd<T, kRowWarps, 0>, rs));
+    IIM_CHECK(allow_smem(k_rows_fwd<T, kRowWarps, 8>, rs));
+    IIM_CHECK(allow_smem(k_rows_fwd<T, kRowWarps, 16>, rs));
+    IIM_CHECK(allow_smem(k_cols<T, 4, 0>, cs));
+    IIM_CHECK(allow_smem(k_cols<T, 4, 8>, cs));
+    IIM_CHECK(allow_smem(k_cols<T, 4, 16>, cs));
+    IIM_CHECK(allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 0>, rs));
+    IIM_CHECK(allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 8>, rs));
+    IIM_CHECK(allow_smem(k_rows_inv<T, kRowWarps, INV_STORE_F64, 16>, rs));
+    return IIM_OK;
 }
 
 // Once per device, with that device current: twiddle tables, the device address of the
 // static scratch, and the shared-memory limits of the transform kernels for the largest
-// supported line, so that later calls touch nothing but their stream.
-static iim_status noalloc_setup(double** out) {
+// supported line, so that later calls touch nothing but their stream.  The set-up copies
+// tables to the device, which a stream capture in progress would not allow: a first call on
+// a device whose stream is capturing is refused (IIM_ERR_INVALID_ARG) before anything runs.
+static iim_status noalloc_setup(cudaStream_t s, double** out) {
     int dev = 0;
     IIM_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return IIM_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
     if (!g_noalloc_ptr[dev]) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        IIM_TRY(cudaStreamIsCapturing(s, &cs));
+        if (cs != cudaStreamCaptureStatusNone) {
+            snprintf(g_last_error, sizeof(g_last_error),
+                     "iim_box_poisson_noalloc: the first call on device %d must come before any stream capture "
+                     "(it sets up tables on the device)", dev);
+            return IIM_ERR_INVALID_ARG;
+        }
         IIM_CHECK(ensure_twiddles());
         void* p = nullptr;
         IIM_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        allow_noalloc_smem<double>();
-        allow_noalloc_smem<float>();
+        IIM_CHECK(allow_noalloc_smem<double>());
+        IIM_CHECK(allow_noalloc_smem<float>());
         g_noalloc_ptr[dev] = (double*)p;
     }
     *out = g_noalloc_ptr[dev];
@@ -2262,9 +2278,9 @@ extern "C" iim_status iim_box_poisson_noalloc(const iim_grid* grid, const double
     if (prec != IIM_FP64 && prec != IIM_MIXED) return IIM_ERR_INVALID_ARG;
     const double h = (grid->x1 - grid->x0) / nx;
     if (!(h > 0.0)) return IIM_ERR_INVALID_ARG;
-    double* scratch = nullptr;
-    IIM_CHECK(noalloc_setup(&scratch));
     cudaStream_t s = (cudaStream_t)stream;
+    double* scratch = nullptr;
+    IIM_CHECK(noalloc_setup(s, &scratch));
     const int NX = nx - 1, NY = ny - 1;
     double* buf = scratch;                          // padded transform buffer, nx * NY
     double* lam = scratch + (size_t)nx * NY;        // NX + NY eigenvalues
