@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-rk3", action="store_true", help="skip the RK3 step leg")
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 multi-body leg")
     ap.add_argument("--tiles", type=int, default=0, help="column-pass tile width (0: tuned on the batch)")
+    ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT box-solve cross-check")
     return ap.parse_args()
 
 
@@ -395,6 +396,117 @@ def rk3_c2(iim, inputs, dev, steps=3):
                            "vorticity flux through the box edges"}
 
 
+PLAIN_INNER = (1e-10, 5e-11, 2e-11, 1e-11, 5e-12)
+
+
+def calibrate_inner(solve_at, candidates, reps=2):
+    """The Krylov tolerance (of `candidates`) whose solve reaches the FP64 residual target in
+    the fewest milliseconds; each candidate is solved once untimed, then `reps` times under
+    CUDA events.  Returns (tolerance, [per-candidate record])."""
+    import torch
+    rows, best = [], None
+    for inner in candidates:
+        solve_at(inner)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            st = solve_at(inner)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        ok = st["rel_res"] <= RTOL
+        rows.append({"inner_rtol": inner, "ms": ms, "krylov_iters": st["iters"], "refinements": st["refinements"],
+                     "rel_res": st["rel_res"], "reaches_target": ok})
+        if ok and (best is None or ms < best[1]):
+            best = (inner, ms)
+    return (best[0] if best else candidates[-1]), rows
+
+
+def cufft_dst1(x, dim):
+    """DST-I along `dim` by cuFFT (torch.fft): X_k = sum_j x_j sin(pi j k / n), j, k = 1..n-1,
+    from the real FFT of the odd extension (0, x, 0, -x reversed) of length 2n, X_k = -Im Y_k / 2.
+    The library's own transforms never call this: it is the timed library cross-check."""
+    import torch
+    n = x.shape[dim] + 1
+    shape = list(x.shape)
+    shape[dim] = 1
+    z = torch.zeros(shape, dtype=x.dtype, device=x.device)
+    y = torch.cat([z, x, z, -x.flip(dim)], dim)
+    return torch.fft.rfft(y, dim=dim).imag.narrow(dim, 1, n - 1) * -0.5
+
+
+def cufft_box_poisson(f, h):
+    """Dirichlet-box solve -lap_h u = f (zero box data) on an (ny-1) x (nx-1) interior array by
+    cuFFT DST-I along both axes, division by lam_x(k) + lam_y(l), lam(k) = (2 - 2 cos(pi k/n))/h^2,
+    and the inverse DST-I (the same transform times 2/n per axis)."""
+    import math
+    import torch
+    ny, nx = f.shape[0] + 1, f.shape[1] + 1
+    kx = torch.arange(1, nx, dtype=torch.float64, device=f.device)
+    ky = torch.arange(1, ny, dtype=torch.float64, device=f.device)
+    lam = ((2 - 2 * torch.cos(math.pi * ky / ny))[:, None] + (2 - 2 * torch.cos(math.pi * kx / nx))[None, :]) / h**2
+    scale = (2.0 / nx) * (2.0 / ny) / lam
+    F = cufft_dst1(cufft_dst1(f, 1), 0) * scale.to(f.dtype)
+    return cufft_dst1(cufft_dst1(F, 0), 1)
+
+
+def gpu_ms_per_call(fn, reps, dev):
+    """Device milliseconds per call of `fn`: the stream is first held by a sleep kernel long
+    enough for the host to queue all `reps` calls, so the events bracket device time only."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda._sleep(int(2e8))   # ~0.1 s at 2 GHz
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def cufft_crosscheck(iim, dev, sizes=(1024, 2048), reps=20):
+    """The library's DST-I box solve (FP64 and FP32 transforms) against a cuFFT-based box solve
+    on the same seeded fields: agreement and device time per solve."""
+    import numpy as np
+    import torch
+    out = {}
+    for n in sizes:
+        h = 4.0 / n
+        g = iim.make_grid(-2, 2, -2, 2, n, n)
+        NXY = (n - 1) ** 2
+        rng = np.random.default_rng(n)
+        f64 = torch.as_tensor(rng.normal(size=(n - 1, n - 1)), dtype=torch.float64, device=dev)
+        f32 = f64.float()
+        work = torch.empty(2 * NXY, dtype=torch.float64, device=dev)
+        u = {p: torch.empty(NXY, dtype=torch.float64, device=dev) for p in (iim.IIM_FP64, iim.IIM_MIXED)}
+        ref = cufft_box_poisson(f64, h)
+        r32 = cufft_box_poisson(f32, h)
+        fl = f64.reshape(-1)
+        row = {}
+        scale = ref.abs().max().item()
+        for prec, tag in ((iim.IIM_FP64, "f64"), (iim.IIM_MIXED, "f32")):
+            iim.iim_box_poisson(g, fl, None, u[prec], prec, work)
+            torch.cuda.synchronize()
+            err = (u[prec].reshape(n - 1, n - 1) - ref).abs().max().item() / scale
+            ms = gpu_ms_per_call(lambda: iim.iim_box_poisson(g, fl, None, u[prec], prec, work), reps, dev)
+            row[f"ours_{tag}"] = {"ms": ms, "rel_linf_vs_cufft_f64": err}
+        row["cufft_f64"] = {"ms": gpu_ms_per_call(lambda: cufft_box_poisson(f64, h), reps, dev)}
+        row["cufft_f32"] = {"ms": gpu_ms_per_call(lambda: cufft_box_poisson(f32, h), reps, dev),
+                            "rel_linf_vs_cufft_f64": (r32.double() - ref).abs().max().item() / scale}
+        xs = torch.zeros((n - 1, 2 * n), dtype=torch.float32, device=dev)
+        row["cufft_f32_rfft_only"] = {"ms": 4 * gpu_ms_per_call(lambda: torch.fft.rfft(xs, dim=1), reps, dev),
+                                      "note": "four batched real FFTs of 2n points over n-1 lines, no packing"}
+        row["speedup_ours_f32_vs_cufft_f32"] = row["cufft_f32"]["ms"] / row["ours_f32"]["ms"]
+        row["speedup_ours_f64_vs_cufft_f64"] = row["cufft_f64"]["ms"] / row["ours_f64"]["ms"]
+        out[f"{n}x{n}"] = row
+    out["note"] = ("cuFFT (through torch.fft) DST-I by the real FFT of the odd extension, zero box data; the "
+                   "library's solve includes its box-data step; device time per solve with the host queued ahead")
+    return out
+
+
 def c3_multibody(iim, inputs, dev, steps=3):
     """The 2048^2 multi-body workload (three circles, an annulus, a five-petal star; 50 Gaussian
     vortices; circulation mode): plain FP64 solve and mixed solve to 1e-10, their difference,
@@ -581,10 +693,22 @@ def main():
     # ---- the same form one problem at a time (latency view)
     ms1, outs1 = timed(lambda: solve(iim.IIM_MIXED), args.steps, 2)
     single = args.steps / (sum(ms1) * 1e-3)
-    # ---- plain FP64 iteration (the comparator: unpreconditioned, one problem at a time)
+    # ---- plain FP64 iteration (the comparator: unpreconditioned, one problem at a time), at its
+    # loosest Krylov tolerance that still ends at the same FP64 residual target (no over-solve)
+    inner64, calib64 = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 0), PLAIN_INNER)
     k64 = max(3, args.steps // 5)
-    ms64, stats64 = timed(lambda: solve(iim.IIM_FP64), k64, 2)
+    ms64, stats64 = timed(lambda: solve(iim.IIM_FP64, inner64, 0), k64, 2)
     plain = k64 / (sum(ms64) * 1e-3)
+    # ---- FP64 transforms with the same dense preconditioner (isolates the mixed-precision gain)
+    inner64p, calib64p = (None, None)
+    fp64_pc = None
+    if precond:
+        inner64p, calib64p = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 1), PLAIN_INNER)
+        msp, statsp = timed(lambda: solve(iim.IIM_FP64, inner64p, 1), k64, 2)
+        fp64_pc = {"value": k64 / (sum(msp) * 1e-3), "unit": UNIT, "ms_per_solve": sum(msp) / k64,
+                   "inner_rtol": inner64p, "krylov_iters": statistics.mean(s["iters"] for s in statsp),
+                   "refinements": statistics.mean(s["refinements"] for s in statsp),
+                   "final_rel_res": max(s["rel_res"] for s in statsp), "calibration": calib64p}
     # ---- per-kernel timing of the single-problem step (second pass, CUDA events around kernels)
     kprof = min(args.steps, 10)
     iim.iim_profile_begin()
@@ -693,6 +817,7 @@ def main():
             gg.close()
     rk3 = None if args.no_rk3 else rk3_c2(iim, inputs, dev)
     c3 = None if args.no_c3 else c3_multibody(iim, inputs, dev)
+    cufft = None if args.no_cufft else cufft_crosscheck(iim, dev)
     c5 = None
     if not args.no_learned:
         c5 = learned_c5(iim, dev, opts_for)
@@ -713,8 +838,15 @@ def main():
         "single_problem": {"value": single, "unit": UNIT, "ms_per_solve": sum(ms1) / len(ms1)},
         "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": sum(ms64) / k64,
                        "krylov_iters": statistics.mean(s["iters"] for s in stats64),
-                       "final_rel_res": max(s["rel_res"] for s in stats64)},
+                       "refinements": statistics.mean(s["refinements"] for s in stats64),
+                       "final_rel_res": max(s["rel_res"] for s in stats64), "inner_rtol": inner64,
+                       "calibration": calib64,
+                       "rule": "the paper's iteration (FP64 transforms, unpreconditioned GMRES), stopped as soon as "
+                               "the un-reduced FP64 residual is <= 1e-10, at the loosest Krylov tolerance of "
+                               f"{list(PLAIN_INNER)} that reaches it in the fewest milliseconds"},
+        "fp64_precond": fp64_pc,
         "speedup_vs_plain_fp64": value / plain / ws,
+        "speedup_single_vs_plain_fp64": single / plain,
         "solver": {"krylov_iters": statistics.mean(s["iters"] for s in stats),
                    "refinements": statistics.mean(s["refinements"] for s in stats),
                    "final_rel_res_max": max(s["rel_res"] for s in stats), "setup_s": t_setup,
@@ -733,6 +865,7 @@ def main():
         "learned_c5": c5,
         "rk3_c2": rk3,
         "multibody_c3": c3,
+        "cufft_crosscheck": cufft,
         "cpu_baseline": cpu,
     }
     if rank == 0:
