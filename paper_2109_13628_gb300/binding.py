@@ -86,6 +86,7 @@ SIGNATURES = [
                                       ctypes.POINTER(_d), ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
     ("iim_last_error_message", ctypes.c_char_p, []),
     ("iim_launch_count", ctypes.c_longlong, []),
+    ("iim_set_lockstep", _i, [_i]),
     ("iim_profile_begin", _i, []),
     ("iim_profile_end", _i, [ctypes.POINTER(iim_kernel_stat), _i]),
     ("iim_destroy_geometry", None, [_vp]),
@@ -363,6 +364,11 @@ def iim_destroy_geometry(g: Geometry):
 
 def iim_launch_count() -> int:
     return int(load().iim_launch_count())
+
+
+def iim_set_lockstep(enabled: bool) -> bool:
+    """Lockstep groups in the batched solves on (default) or off; returns the previous setting."""
+    return bool(load().iim_set_lockstep(1 if enabled else 0))
 
 
 def iim_profile_begin():

@@ -9,13 +9,71 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
 
 using namespace iim;
+
+namespace {
+iim_opts opts_or_default(const iim_opts* o) {
+    return o ? *o : iim_opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
+}
+
+// Lockstep groups of a batched call: the problems that can take the lockstep path (see
+// lockstep.cu), bucketed by grid size and transform settings, largest grids first; buckets of
+// one problem stay on the per-problem path (nothing to batch).
+std::vector<std::vector<int>> lockstep_groups(int n, iim_geometry const* geoms, const std::vector<int>& order,
+                                              const iim_opts& o) {
+    std::map<std::tuple<long, int, int, int, int>, std::vector<int>> b;
+    for (int k : order) {
+        iim_geometry g = geoms[k];
+        if (lockstep_eligible(g, o)) b[{-(long)g->nx * g->ny, g->nx, g->ny, g->wide_lines, g->cols_c}].push_back(k);
+    }
+    std::vector<std::vector<int>> out;
+    for (auto& kv : b)
+        if (kv.second.size() >= 2) out.push_back(kv.second);
+    (void)n;
+    return out;
+}
+
+// Runs the lockstep groups, each on its own stream forked from `start`; `done[i]` is recorded
+// on group i's stream.  While the per-kernel profiler is on, groups run host-driven one after
+// the other on the calling thread.
+struct LockstepRun {
+    std::vector<std::vector<int>> groups;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> done;
+    std::vector<void*> handles;
+    bool host = false;
+    ~LockstepRun() {
+        for (cudaEvent_t e : done)
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t s : streams)
+            if (s) cudaStreamDestroy(s);
+    }
+    iim_status open(cudaEvent_t start) {
+        streams.assign(groups.size(), nullptr);
+        done.assign(groups.size(), nullptr);
+        handles.assign(groups.size(), nullptr);
+        for (size_t i = 0; i < groups.size(); ++i) {
+            IIM_TRY(cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking));
+            IIM_TRY(cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming));
+            IIM_TRY(cudaStreamWaitEvent(streams[i], start, 0));
+        }
+        return IIM_OK;
+    }
+    // after every stream of the call has been synchronised
+    void finish(const iim_opts& o, std::vector<iim_status>& status, std::vector<iim_stats>& stats) {
+        for (size_t i = 0; i < groups.size(); ++i)
+            if (handles[i]) lockstep_finish(handles[i], groups[i], o, host, status, stats);
+    }
+};
+}  // namespace
 
 extern "C" iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const double* const* omega,
                                                 const double* const* psi_b, const double* const* psi_box,
@@ -56,9 +114,25 @@ extern "C" iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms
     std::vector<iim_status> status(n, IIM_OK);
     std::vector<int> enq(n, -1);
     std::vector<iim_stats> stb(n);
+    // lockstep groups: one launch per step for all problems of a size bucket
+    const iim_opts o = opts_or_default(opts);
+    LockstepRun ls;
+    ls.groups = lockstep_groups(n, geoms, order, o);
+    ls.host = profiling_active();
+    if (setup_st == IIM_OK) setup_st = ls.open(start);
+    for (size_t i = 0; i < ls.groups.size() && setup_st == IIM_OK; ++i) {
+        const iim_status e = lockstep_enqueue(ls.groups[i], geoms, omega, psi_b, psi_box, gamma, psibar, psi_out,
+                                              ux_out, uy_out, o, ls.streams[i], ls.host, &ls.handles[i]);
+        for (int k : ls.groups[i]) {
+            enq[k] = 2;   // taken by the group
+            if (e != IIM_OK) status[k] = e;
+        }
+        cudaEventRecord(ls.done[i], ls.streams[i]);
+    }
     // whole-solve graphs: launched from here without waiting
     for (int q = 0; q < n && setup_st == IIM_OK; ++q) {
         const int k = order[q];
+        if (enq[k] == 2) continue;
         status[k] = solve_enqueue(geoms[k], omega[k], psi_b[k], psi_box ? psi_box[k] : nullptr,
                                   gamma ? gamma[k] : nullptr, psibar[k], psi_out[k], ux_out ? ux_out[k] : nullptr,
                                   uy_out ? uy_out[k] : nullptr, opts, &stb[k], ws[q % n_streams], &enq[k]);
@@ -95,8 +169,13 @@ extern "C" iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms
             cudaStreamSynchronize(ws[t]);
             cudaStreamWaitEvent(cs, done[t], 0);
         }
+        for (size_t i = 0; i < ls.groups.size(); ++i) {
+            cudaStreamSynchronize(ls.streams[i]);
+            cudaStreamWaitEvent(cs, ls.done[i], 0);
+        }
         for (int k = 0; k < n; ++k)
             if (enq[k] == 1) status[k] = solve_finish(geoms[k], opts, &stb[k]);
+        ls.finish(o, status, stb);
         if (stats)
             for (int k = 0; k < n; ++k) stats[k] = stb[k];
     }
@@ -228,8 +307,42 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
     std::vector<iim_status> status(n, IIM_OK);
     std::vector<int> enq(n, -1);
     std::vector<iim_stats> stb(n);
+    // lockstep groups: inputs copied in on the group's stream, one lockstep solve, outputs out
+    const iim_opts o = opts_or_default(opts);
+    LockstepRun ls;
+    ls.groups = lockstep_groups(n, geoms, order, o);
+    ls.host = profiling_active();
+    if (setup_st == IIM_OK) setup_st = ls.open(start);
+    if (!ls.groups.empty() && setup_st == IIM_OK) {
+        std::vector<const double*> d_om(n), d_pb(n), d_ring(n), d_gam(n);
+        std::vector<double*> d_pbar(n), d_psi(n), d_ux(n), d_uy(n);
+        for (int k = 0; k < n; ++k) {
+            dev_args(k, &d_ring[k], &d_gam[k], &d_psi[k], &d_ux[k], &d_uy[k]);
+            d_om[k] = io[k].omega;
+            d_pb[k] = io[k].psi_b;
+            d_pbar[k] = io[k].psibar;
+        }
+        for (size_t i = 0; i < ls.groups.size(); ++i) {
+            cudaStream_t s = ls.streams[i];
+            iim_status e = IIM_OK;
+            for (int k : ls.groups[i])
+                if (e == IIM_OK) e = copy_in(k, s);
+            if (e == IIM_OK)
+                e = lockstep_enqueue(ls.groups[i], geoms, d_om.data(), d_pb.data(), d_ring.data(), d_gam.data(),
+                                     d_pbar.data(), d_psi.data(), d_ux.data(), d_uy.data(), o, s, ls.host,
+                                     &ls.handles[i]);
+            for (int k : ls.groups[i])
+                if (e == IIM_OK) e = copy_out(k, s);
+            for (int k : ls.groups[i]) {
+                enq[k] = 2;
+                if (e != IIM_OK) status[k] = e;
+            }
+            cudaEventRecord(ls.done[i], s);
+        }
+    }
     for (int q = 0; q < n && setup_st == IIM_OK; ++q) {
         const int k = order[q];
+        if (enq[k] == 2) continue;
         cudaStream_t s = ws[q % n_streams];
         int e = -1;
         const double* ring;
@@ -285,8 +398,13 @@ extern "C" iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* 
             cudaStreamSynchronize(ws[t]);
             cudaStreamWaitEvent(cs, done[t], 0);
         }
+        for (size_t i = 0; i < ls.groups.size(); ++i) {
+            cudaStreamSynchronize(ls.streams[i]);
+            cudaStreamWaitEvent(cs, ls.done[i], 0);
+        }
         for (int k = 0; k < n; ++k)
             if (enq[k] == 1) status[k] = solve_finish(geoms[k], opts, &stb[k]);
+        ls.finish(o, status, stb);
         if (stats)
             for (int k = 0; k < n; ++k) stats[k] = stb[k];
     }

@@ -186,6 +186,18 @@ iim_status solve_enqueue(iim_geometry g, const double* omega, const double* psi_
                          const double* gamma, double* psibar, double* psi_out, double* ux_out, double* uy_out,
                          const iim_opts* opts, iim_stats* stats, cudaStream_t s, int* enqueued);
 iim_status solve_finish(iim_geometry g, const iim_opts* opts, iim_stats* stats);
+void set_last_error(const char* msg);
+// lockstep batched solves (lockstep.cu): problems of one grid size advanced together, one launch
+// per step for all of them
+bool lockstep_eligible(iim_geometry g, const iim_opts& o);
+iim_status lockstep_enqueue(const std::vector<int>& idx, iim_geometry const* geoms, const double* const* omega,
+                            const double* const* psi_b, const double* const* psi_box, const double* const* gamma,
+                            double* const* psibar, double* const* psi_out, double* const* ux_out,
+                            double* const* uy_out, const iim_opts& o, cudaStream_t s, bool host_driven,
+                            void** handle);
+void lockstep_finish(void* handle, const std::vector<int>& idx, const iim_opts& o, bool host_driven,
+                     std::vector<iim_status>& status, std::vector<iim_stats>& stats);
+void lockstep_forget(iim_geometry g);
 // dense Schur-complement preconditioner (precond.cu)
 // [S | I] -> [I | S^-1] in place; scratch holds gj_scratch_floats(n) floats
 size_t gj_scratch_floats(int n);

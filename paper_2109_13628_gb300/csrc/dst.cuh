@@ -566,12 +566,11 @@ constexpr int kLineScratch = 16;
 // and the transformed row is written to out (padded layout).  `stop` (optional): a set flag
 // makes the launch a no-op.  Each line is handled by line_threads(FP) threads.
 template <typename T, int WARPS, int FP>
-__global__ void __launch_bounds__(WARPS * 32)
-k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
-           const double* __restrict__ ring, double ih2, const int* __restrict__ aff_row_ptr,
-           const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
-           T* __restrict__ out, const int* __restrict__ stop) {
-    if (stop && *stop) return;
+__device__ __forceinline__ void
+rows_fwd_body(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
+              const double* __restrict__ ring, double ih2, const int* __restrict__ aff_row_ptr,
+              const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
+              T* __restrict__ out) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
@@ -620,19 +619,27 @@ k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* _
     store_row_vec<T, TN>(out + (size_t)r * n, res, n, tid);
 }
 
+template <typename T, int WARPS, int FP>
+__global__ void __launch_bounds__(WARPS * 32)
+k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
+           const double* __restrict__ ring, double ih2, const int* __restrict__ aff_row_ptr,
+           const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
+           T* __restrict__ out, const int* __restrict__ stop) {
+    if (stop && *stop) return;
+    rows_fwd_body<T, WARPS, FP>(NX, NY, n, logn, row0, nrows, dense, dld, doff, ring, ih2, aff_row_ptr, aff_node, gam,
+                                gsign, g_tw, out);
+}
+
 // Column pass on padded columns p = 1..NX (p = 0 is the pad): forward y transform, division
 // by the eigenvalues (with the 2D normalisation), inverse y transform.  Rows outside [in0, in1]
 // are zero on input; only rows [out0, out1] are written back.  C columns per block,
 // line_threads(FP) threads per column; blockIdx.y selects one of several fields fstride
 // elements apart.
 template <typename T, int C, int FP>
-__global__ void __launch_bounds__(C * line_threads(FP))
-k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
-       const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
-       const int* __restrict__ stop, long fstride) {
-    if (stop && *stop) return;
+__device__ __forceinline__ void
+cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
+          const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP);
-    buf += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
@@ -711,6 +718,16 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
     }
 }
 
+template <typename T, int C, int FP>
+__global__ void __launch_bounds__(C * line_threads(FP))
+k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
+       const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
+       const int* __restrict__ stop, long fstride) {
+    if (stop && *stop) return;
+    cols_body<T, C, FP>(NX, NY, n, logn, in0, in1, out0, out1, buf + (long)blockIdx.y * fstride, lam_x, lam_y, norm,
+                        g_tw);
+}
+
 enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2 };
 
 // Inverse row transforms of rows [row0, row0 + nrows) of a padded buffer.
@@ -719,14 +736,11 @@ enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2 };
 //   INV_ACCUM_FLUID out64 (padded) += transform at fluid nodes (class FLUID / PLUS) only
 // blockIdx.y selects one of several fields fstride elements apart (in and outT).
 template <typename T, int WARPS, int MODE, int FP>
-__global__ void __launch_bounds__(WARPS * 32)
-k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __restrict__ in, T* __restrict__ outT,
-           double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
-           const cpx<T>* __restrict__ g_tw, const int* __restrict__ stop, long fstride) {
-    if (stop && *stop) return;
+__device__ __forceinline__ void
+rows_inv_body(int NX, int NY, int n, int logn, int row0, int nrows, const T* __restrict__ in, T* __restrict__ outT,
+              double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
+              const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
-    in += (long)blockIdx.y * fstride;
-    if (outT) outT += (long)blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
@@ -755,6 +769,16 @@ k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __rest
         for (int i = tid; i < NX; i += TN)
             if (cls[base + 1 + i] <= CLS_PLUS) out64[base + 1 + i] += (double)res[i + 1];
     }
+}
+
+template <typename T, int WARPS, int MODE, int FP>
+__global__ void __launch_bounds__(WARPS * 32)
+k_rows_inv(int NX, int NY, int n, int logn, int row0, int nrows, const T* __restrict__ in, T* __restrict__ outT,
+           double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
+           const cpx<T>* __restrict__ g_tw, const int* __restrict__ stop, long fstride) {
+    if (stop && *stop) return;
+    rows_inv_body<T, WARPS, MODE, FP>(NX, NY, n, logn, row0, nrows, in + (long)blockIdx.y * fstride,
+                                      outT ? outT + (long)blockIdx.y * fstride : nullptr, out64, old, ooff, cls, g_tw);
 }
 
 }  // namespace iim

@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "iim_ops.cuh"
 
 namespace iim {
 
@@ -259,52 +260,7 @@ __global__ void __launch_bounds__(WARPS * 32)
 k_dense_matvec4(int n, const float* __restrict__ M, long ldm, const double* __restrict__ vbase,
                 const int* __restrict__ jidx, long vstride, double* __restrict__ out, int accumulate,
                 const int* __restrict__ stop) {
-    if (stop && *stop) return;
-    extern __shared__ float4 s_v4[];
-    float* s_v = reinterpret_cast<float*>(s_v4);
-    const int stride = (n + 3) & ~3;
-    const double* v = jidx ? vbase + (long)(*jidx) * vstride : vbase;
-    for (int j = threadIdx.x; j < n; j += WARPS * 32) {
-        const float x = (float)v[j];
-#pragma unroll
-        for (int h = 0; h < 4; ++h)
-            if (j >= h) s_v[h * stride + j - h] = x;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int row = blockIdx.x * WARPS + (threadIdx.x >> 5); row < n; row += gridDim.x * WARPS) {
-        const float* r = M + (long)row * ldm;
-        const int head = min((int)((4 - ((reinterpret_cast<uintptr_t>(r) >> 2) & 3)) & 3), n);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        if (lane < head) a0 = r[lane] * s_v[lane];
-        const float4* r4 = reinterpret_cast<const float4*>(r + head);
-        const float4* v4 = reinterpret_cast<const float4*>(s_v + head * stride);
-        const int nq = (n - head) >> 2;
-        int q = lane;
-        for (; q + 7 * 32 < nq; q += 8 * 32) {
-            float4 x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) x[u] = r4[q + 32 * u];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const float4 y = v4[q + 32 * u];
-                float& a = (u & 3) == 0 ? a0 : (u & 3) == 1 ? a1 : (u & 3) == 2 ? a2 : a3;
-                a = fmaf(x[u].x, y.x, fmaf(x[u].y, y.y, fmaf(x[u].z, y.z, fmaf(x[u].w, y.w, a))));
-            }
-        }
-        for (; q < nq; q += 32) {
-            const float4 x = r4[q], y = v4[q];
-            a1 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a1))));
-        }
-        const int rem = (n - head) & 3;
-        if (lane < rem) {
-            const int idx = head + 4 * nq + lane;
-            a2 = fmaf(r[idx], s_v[idx], a2);
-        }
-        float acc = (a0 + a1) + (a2 + a3);
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) out[row] = accumulate ? out[row] + (double)acc : (double)acc;
-    }
+    dense_matvec4_body<WARPS>(n, M, ldm, vbase, jidx, vstride, out, accumulate, stop);
 }
 
 iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_t s) {

@@ -132,3 +132,58 @@ def test_empty_and_single_problem_batches():
     assert torch.equal(psi1, a["psi"][0]) and s1["iters"] == stats[0]["iters"]
     for g in geos:
         g.close()
+
+
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_lockstep_groups_equal_single_solves(prec):
+    """From the second batched call on, the problems of each grid size advance as one lockstep
+    group (one launch per step for the whole group, loops decided on the device).  Every problem
+    gets exactly its single solve's psi, u, psibar, iteration and refinement counts; lockstep
+    issues fewer launches than one whole-solve graph per problem; with the per-kernel profiler
+    on, the same groups run host-driven, give the same results, and the profile holds the
+    batched kernels."""
+    problems = inputs.batched_c4(count=10, seed=5, sizes=(64, 128, 256))
+    kept, geos, a = build_batch(problems)
+    opts = iim.default_opts(prec=prec, rtol=1e-11, precond=1)
+    ux = [torch.empty_like(t) for t in a["psi"]]
+    uy = [torch.empty_like(t) for t in a["psi"]]
+
+    def batch():
+        for t in a["psi"] + ux + uy:
+            t.fill_(float("nan"))
+        for t in a["psibar"]:
+            t.zero_()
+        before = iim.iim_launch_count()
+        st, stats = iim.iim_poisson_solve_batched(geos, a["omega"], a["psi_b"], None, a["gamma"], a["psibar"],
+                                                  a["psi"], ux, uy, opts=opts, n_streams=3)
+        assert st == iim.IIM_OK
+        return ([t.clone() for t in a["psi"]], [t.clone() for t in ux], [t.clone() for t in uy],
+                [t.clone() for t in a["psibar"]], stats, iim.iim_launch_count() - before)
+
+    batch()                                   # first solves: host-driven, per problem
+    prev = iim.iim_set_lockstep(False)
+    per_problem = batch()                     # one whole-solve graph per problem
+    iim.iim_set_lockstep(True)
+    lock = batch()                            # lockstep groups
+    iim.iim_profile_begin()
+    hosted = batch()                          # lockstep, host-driven under the profiler
+    prof = iim.iim_profile_end()
+    iim.iim_set_lockstep(prev)
+    sizes = [P.grid.nx for P in kept]
+    assert max(sizes.count(n) for n in set(sizes)) >= 2     # at least one real group
+    for k, (P, geo) in enumerate(zip(kept, geos)):
+        psi1, ux1, uy1 = (torch.empty_like(a["psi"][k]) for _ in range(3))
+        pb1 = torch.zeros_like(a["psibar"][k])
+        s1 = iim.iim_poisson_solve(geo, a["omega"][k], a["psi_b"][k], None, a["gamma"][k], pb1, psi1, ux1, uy1,
+                                   opts=opts)
+        for run in (per_problem, lock, hosted):
+            assert torch.equal(run[0][k], psi1) and torch.equal(run[1][k], ux1) and torch.equal(run[2][k], uy1), k
+            assert torch.equal(run[3][k], pb1)
+            assert run[4][k]["iters"] == s1["iters"] and run[4][k]["refinements"] == s1["refinements"]
+            assert run[4][k]["rel_res"] == s1["rel_res"] and run[4][k]["rel_res"] < 1e-11
+    assert lock[5] < per_problem[5]
+    names = {r["name"] for r in prof}
+    assert ("ls_cols_f64" if prec == iim.IIM_FP64 else "ls_cols_f32") in names
+    assert "ls_gmres_arnoldi" in names and "ls_residual_f64" in names
+    for g in geos:
+        g.close()

@@ -1,7 +1,9 @@
 """The library's hand-written DST-I box solve against a cuFFT-based one (torch.fft; the timed
 library cross-check of the benchmark).  cuFFT never enters the library: it is only the second
 opinion here.  Sizes span the register-path FFT (1024-point lines), the Stockham path (2048) and
-a ragged rectangle."""
+a ragged rectangle.  FP32 tolerances: the rounding error of an FP32 transform pair grows with
+the line length, 2e-5 of the field's maximum up to 1024-point lines (the bound of the other box
+tests), 5e-5 for 2048-point lines."""
 import numpy as np
 import pytest
 import torch
@@ -22,11 +24,12 @@ def test_box_solve_agrees_with_cufft(nx, ny):
     ref = bench.cufft_box_poisson(f, h)
     scale = ref.abs().max().item()
     work = torch.empty(2 * f.numel(), dtype=torch.float64, device=gu.dev())
-    for prec, tol in ((iim.IIM_FP64, 1e-12), (iim.IIM_MIXED, 2e-5)):
+    tol32 = 2e-5 if max(nx, ny) <= 1024 else 5e-5
+    for prec, tol in ((iim.IIM_FP64, 1e-12), (iim.IIM_MIXED, tol32)):
         u = torch.empty(f.numel(), dtype=torch.float64, device=gu.dev())
         iim.iim_box_poisson(g, f.reshape(-1), None, u, prec, work)
         err = (u.reshape(f.shape) - ref).abs().max().item() / scale
         assert err < tol, (prec, err)
     # the FP32 cuFFT solve sits within the same band of the FP64 one
     r32 = bench.cufft_box_poisson(f.float(), h).double()
-    assert (r32 - ref).abs().max().item() / scale < 2e-5
+    assert (r32 - ref).abs().max().item() / scale < tol32
