@@ -43,7 +43,7 @@ NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722200, "l2_bytes_per_launc
 def kernel_source_hash():
     """Hash of the files holding the transform kernels and their launch configuration."""
     h = hashlib.sha256()
-    for f in ("dst.cuh", "solve.cu"):
+    for f in ("dst.cuh", "iim_ops.cuh", "solve.cu", "lockstep.cu"):
         with open(os.path.join(ROOT, "paper_2109_13628_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -237,12 +237,25 @@ def c4_batch(iim, inputs, T, dev, count, seed, precond):
     import torch
     probs = inputs.batched_c4(count=count, seed=seed)
     geos, om, pb, gm, pbar, out, kept = [], [], [], [], [], [], []
-    for P in probs:
+    redraws = 0
+    for k0, P in enumerate(probs):
         g = P.grid
         try:
             geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions, P.modes)
         except iim.IIMError:
-            continue
+            # under-resolved draw: another seeded draw of the same grid size takes its place
+            geo = None
+            for r in range(1, 50):
+                P = inputs.ellipses_problem(g.nx, seed * 1000 + 100000 * r + k0)
+                redraws += 1
+                try:
+                    geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi),
+                                                 P.regions, P.modes)
+                    break
+                except iim.IIMError:
+                    continue
+            if geo is None:
+                continue
         cp = iim.iim_geometry_control_points(geo)
         geos.append(geo)
         kept.append(P)
@@ -270,6 +283,7 @@ def c4_batch(iim, inputs, T, dev, count, seed, precond):
         with cf.ThreadPoolExecutor(nw) as ex:
             list(ex.map(build, [order[w::nw] for w in range(nw)]))
     torch.cuda.synchronize()
+    c4_batch.redraws = redraws
     return kept, geos, om, pb, gm, pbar, out, time.perf_counter() - t0
 
 
@@ -678,9 +692,16 @@ def main():
         tile_w = args.tiles
         for gg in geos:
             iim.iim_geometry_set_tiles(gg, tile_w)
-    elif B > 1:
-        tile_w, tiles_tuned = autotune.tune_tiles_batch(geos, lambda: solve_batch(B))
+    group, group_tuned = 1, None
+    if B > 1:
+        # the per-problem form's tile width and streams, then the lockstep group size
+        prev = iim.iim_set_lockstep(0)
+        if not args.tiles:
+            tile_w, tiles_tuned = autotune.tune_tiles_batch(geos, lambda: solve_batch(B))
         n_streams, tuned = autotune.tune_streams(solve_batch, tuple(c for c in (1, 2, 4, 8, 12, 16) if c <= B))
+        iim.iim_set_lockstep(prev)
+        group, group_tuned = autotune.tune_lockstep(lambda: solve_batch(n_streams),
+                                                    tuple(c for c in (1, 2, 4, 8) if c <= B))
     # ---- chosen form: B problems per step in flight (the timed region), clocks sampled
     with ClockSampler(local) as clk:
         ms, outs = timed(lambda: solve_batch(n_streams)[1] if B > 1 else [solve(iim.IIM_MIXED)], args.steps,
@@ -709,18 +730,35 @@ def main():
                    "inner_rtol": inner64p, "krylov_iters": statistics.mean(s["iters"] for s in statsp),
                    "refinements": statistics.mean(s["refinements"] for s in statsp),
                    "final_rel_res": max(s["rel_res"] for s in statsp), "calibration": calib64p}
-    # ---- per-kernel timing of the single-problem step (second pass, CUDA events around kernels)
+    # ---- lockstep off: one whole-solve graph per problem on the tuned streams (same B solves)
+    per_problem = None
+    if B > 1:
+        prev = iim.iim_set_lockstep(0)
+        kpp = max(3, args.steps // 2)
+        mpp, _ = timed(lambda: solve_batch(n_streams)[1], kpp, 2)
+        iim.iim_set_lockstep(prev)
+        per_problem = {"value": B * kpp / (sum(mpp) * 1e-3), "unit": UNIT, "ms_per_step": sum(mpp) / kpp,
+                       "streams": n_streams,
+                       "form": "lockstep off: one whole-solve graph per problem, problems overlapping on streams"}
+
+    def kernel_profile(step, k):
+        iim.iim_profile_begin()
+        torch.cuda.nvtx.range_push("profile")   # every launch direct (host-driven), no graphs
+        for _ in range(k):
+            flush.zero_()
+            step()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        kern = iim.iim_profile_end()
+        kern.sort(key=lambda r: -r["ms"])
+        return kern, sum(r["ms"] for r in kern)
+
+    # ---- per-kernel timing of the batched step: the lockstep group's kernels run host-driven
+    # under the per-kernel profiler (CUDA events around each launch on its stream); each launch
+    # carries the algorithmic bytes of all B problems
     kprof = min(args.steps, 10)
-    iim.iim_profile_begin()
-    torch.cuda.nvtx.range_push("profile")   # the per-kernel pass: every launch direct, no graphs
-    for _ in range(kprof):
-        flush.zero_()
-        solve(iim.IIM_MIXED)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    kern = iim.iim_profile_end()
-    kern.sort(key=lambda r: -r["ms"])
-    tot_k = sum(r["ms"] for r in kern)
+    kern, tot_k = kernel_profile(lambda: solve_batch(n_streams) if B > 1 else solve(iim.IIM_MIXED), kprof)
+    kern1, tot_k1 = kernel_profile(lambda: solve(iim.IIM_MIXED), kprof)
     peaks, src = measured_peaks()
     mem = [r for r in kern if r["bytes"] > 0]
     dom = mem[0] if mem else None
@@ -736,7 +774,9 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "l2_traffic": l2_traffic, "peak_source": src,
                 "alg_bytes_per_launch": dom["bytes"] / dom["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None,
-                "timing": "single-problem step, CUDA events around each launch on its stream"}
+                "timing": (f"batched step ({B} problems in lockstep, one launch per step for all): the same kernels "
+                           "run host-driven under the per-kernel profiler, CUDA events around each launch on its "
+                           "stream; bytes = the algorithmic bytes of all problems of the launch")}
     # ---- end to end through the C ABI with host buffers (B problems per step)
     e2e = None
     if not args.no_e2e:
@@ -794,12 +834,16 @@ def main():
             return iim.iim_poisson_solve_batched(cgeos, om, pbv, None, gm, pbar, cout, opts=opts_for(iim.IIM_MIXED),
                                                  n_streams=nst)
 
+        prev_group = iim.iim_set_lockstep(0)
         c4_streams, c4_tuned = autotune.tune_streams(c4_run, (4, 8, 16, 24))
+        iim.iim_set_lockstep(prev_group)
+        c4_group, c4_group_tuned = autotune.tune_lockstep(lambda: c4_run(c4_streams), (1, 4, 8, 24), reps=1)
         cms, couts = timed(lambda: c4_run(c4_streams)[1], max(2, args.steps // 10), 1)
         unknowns = sum((P.grid.nx - 1) * (P.grid.ny - 1) for P in kept)
-        c4 = {"problems": len(kept), "solves_per_s": len(kept) * len(cms) / (sum(cms) * 1e-3),
+        c4 = {"problems": len(kept), "redrawn_underresolved": getattr(c4_batch, "redraws", 0), "solves_per_s": len(kept) * len(cms) / (sum(cms) * 1e-3),
               "unknown_solves_per_s": unknowns * len(cms) / (sum(cms) * 1e-3), "ms_per_batch": sum(cms) / len(cms),
-              "streams": c4_streams, "tiles_by_size": {f"{k[0]}x{k[1]}": v for k, v in tiles.items()},
+              "streams": c4_streams, "lockstep_group": c4_group, "lockstep_tuning_ms": c4_group_tuned,
+              "tiles_by_size": {f"{k[0]}x{k[1]}": v for k, v in tiles.items()},
               "precond_setup_s": c4_pc, "max_rel_res": max(s["rel_res"] for o in couts for s in o),
               "krylov_iters_mean": statistics.mean(s["iters"] for o in couts for s in o)}
         # the same batch with FP64 transforms throughout (same preconditioner and streams)
@@ -828,8 +872,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 transforms + f64 refinement", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": f"{B} independent problems of this workload per step, in flight "
-                                                   f"together on {n_streams} streams",
+        "config": {"workload": WORKLOAD, "batch": (f"{B} independent problems of this workload per step in "
+                                                   f"lockstep groups of {group} (one kernel launch per solve step for "
+                                                   "a whole group, one CUDA graph per group, groups concurrent)"
+                                                   if group > 1 else
+                                                   f"{B} independent problems of this workload per step, one "
+                                                   f"whole-solve graph each, in flight on {n_streams} streams"),
                    "l2": "flushed before every timed step (256 MiB write, outside the events)",
                    "form": ("mixed: FP32 DST-I box solves inside FP64 iterative refinement, GMRES("
                             f"{args.restart}) FP64 Krylov" + (", right-preconditioned by the dense FP32 inverse of the"
@@ -851,11 +899,16 @@ def main():
                    "refinements": statistics.mean(s["refinements"] for s in stats),
                    "final_rel_res_max": max(s["rel_res"] for s in stats), "setup_s": t_setup,
                    "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms, "streams_tuning_ms": tuned,
-                   "tile_width": tile_w, "tile_tuning_ms": tiles_tuned,
+                   "tile_width": tile_w, "tile_tuning_ms": tiles_tuned, "lockstep_group": group,
+                   "lockstep_tuning_ms": group_tuned,
                    "n_control": geo.n_control, "n_affected": geo.n_affected},
         "roofline": roof,
         "kernels": [{"name": r["name"], "launches_per_step": r["launches"] / kprof, "ms_per_step": r["ms"] / kprof,
                      "share": r["ms"] / tot_k if tot_k else None} for r in kern[:12]],
+        "kernels_single_problem": [{"name": r["name"], "launches_per_solve": r["launches"] / kprof,
+                                    "ms_per_solve": r["ms"] / kprof, "share": r["ms"] / tot_k1 if tot_k1 else None}
+                                   for r in kern1[:8]],
+        "per_problem_graphs": per_problem,
         "gpu_launches": launches,
         "launch_window": {"library_launches_before_timed": launch_window["before"],
                           "library_launches_timed": launch_window["timed"]},

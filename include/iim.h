@@ -184,17 +184,19 @@ iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const dou
                                      iim_stream stream);
 
 /* How iim_poisson_solve_batched and iim_poisson_solve_batched_host run problems that have been
- * solved once already, with iim_opts.precond == 1 and no guess: enabled = 1 (the default) groups
- * the problems of equal grid size (and equal iim_geometry_set_tiles / _set_lines settings) and
- * advances each group in lockstep -- one kernel launch per step of the solve for every problem
- * of the group, the refinement, cycle and iteration loops continuing on the device while any
- * problem of the group needs them (one CUDA graph per group); enabled = 0 runs one whole-solve
- * graph per problem on the call's streams.  Each problem's results, iteration and refinement
- * counts are bitwise the same either way (the same arithmetic in the same order per problem);
- * lockstep issues far fewer launches and fills the GPU with the work of all problems at once.
- * Process-wide; returns the previous setting.  No counterpart in the paper, which solves one
- * problem at a time. */
-int iim_set_lockstep(int enabled);
+ * solved once already, with iim_opts.precond == 1 and no guess.  max_group >= 2 (default 4):
+ * the problems of equal grid size (and equal iim_geometry_set_tiles / _set_lines settings) are
+ * split into groups of at most max_group problems (sizes as even as possible), and each group
+ * advances in lockstep -- one kernel launch per step of the solve for every problem of the
+ * group, the refinement, cycle and iteration loops continuing on the device while any problem of
+ * the group needs them (one CUDA graph per group); the groups run concurrently on their own
+ * streams.  max_group 0 or 1: one whole-solve graph per problem on the call's streams.  Each
+ * problem's results, iteration and refinement counts are bitwise the same either way (the same
+ * arithmetic in the same order per problem).  Larger groups mean fewer launches and wider
+ * kernels; more groups mean more overlap of the small latency-bound Krylov kernels of one group
+ * with the transforms of another.  Process-wide; returns the previous setting.  No counterpart
+ * in the paper, which solves one problem at a time. */
+int iim_set_lockstep(int max_group);
 
 /* iim_poisson_solve_batched on HOST buffers: every array argument (omega, psi_b, psi_box,
  * gamma, psibar in/out, psi_out, ux_out, uy_out) is host memory, preferably page-locked so

@@ -1,6 +1,6 @@
-"""Autotuner of the batched solver: the column-pass tile width per grid-size bucket, then the
-number of concurrent worker streams, each chosen by timing real solves of the caller's own
-problems on the device (CUDA events), keeping the fastest."""
+"""Autotuner of the batched solver: the column-pass tile width per grid-size bucket, the number
+of concurrent worker streams and the lockstep group size, each chosen by timing real solves of
+the caller's own problems on the device (CUDA events), keeping the fastest."""
 from __future__ import annotations
 
 import collections
@@ -62,3 +62,17 @@ def tune_streams(run_batch, candidates=(1, 2, 4, 8, 12, 16, 24)):
     """The number of worker streams for which `run_batch(n_streams)` is fastest."""
     times = {c: _time(lambda: run_batch(c), 1) for c in candidates}
     return min(times, key=times.get), times
+
+
+def tune_lockstep(run_batch, candidates=(1, 2, 4, 8), reps=3):
+    """The largest lockstep group (iim_set_lockstep; 1 = one whole-solve graph per problem) for
+    which `run_batch()` is fastest.  Each candidate is run once untimed (its group graphs are
+    captured then).  Applies the choice and returns (size, {size: ms})."""
+    times = {}
+    for c in candidates:
+        B.iim_set_lockstep(c)
+        run_batch()
+        times[c] = _time(run_batch, reps)
+    best = min(times, key=times.get)
+    B.iim_set_lockstep(best)
+    return best, times

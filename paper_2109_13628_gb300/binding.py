@@ -366,9 +366,10 @@ def iim_launch_count() -> int:
     return int(load().iim_launch_count())
 
 
-def iim_set_lockstep(enabled: bool) -> bool:
-    """Lockstep groups in the batched solves on (default) or off; returns the previous setting."""
-    return bool(load().iim_set_lockstep(1 if enabled else 0))
+def iim_set_lockstep(max_group: int) -> int:
+    """Largest lockstep group of the batched solves (0 or 1: one whole-solve graph per problem);
+    returns the previous setting."""
+    return int(load().iim_set_lockstep(int(max_group)))
 
 
 def iim_profile_begin():

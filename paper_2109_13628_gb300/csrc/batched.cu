@@ -25,8 +25,9 @@ iim_opts opts_or_default(const iim_opts* o) {
 }
 
 // Lockstep groups of a batched call: the problems that can take the lockstep path (see
-// lockstep.cu), bucketed by grid size and transform settings, largest grids first; buckets of
-// one problem stay on the per-problem path (nothing to batch).
+// lockstep.cu), bucketed by grid size and transform settings, largest grids first, each bucket
+// split into groups of at most iim_set_lockstep's size (as even as possible; the groups run
+// concurrently on their own streams); groups of one problem stay on the per-problem path.
 std::vector<std::vector<int>> lockstep_groups(int n, iim_geometry const* geoms, const std::vector<int>& order,
                                               const iim_opts& o) {
     std::map<std::tuple<long, int, int, int, int>, std::vector<int>> b;
@@ -35,8 +36,16 @@ std::vector<std::vector<int>> lockstep_groups(int n, iim_geometry const* geoms, 
         if (lockstep_eligible(g, o)) b[{-(long)g->nx * g->ny, g->nx, g->ny, g->wide_lines, g->cols_c}].push_back(k);
     }
     std::vector<std::vector<int>> out;
-    for (auto& kv : b)
-        if (kv.second.size() >= 2) out.push_back(kv.second);
+    const int gmax = std::max(lockstep_group_size(), 1);
+    for (auto& kv : b) {
+        const std::vector<int>& v = kv.second;
+        const int m = (int)v.size(), ng = (m + gmax - 1) / gmax;
+        for (int gi = 0; gi < ng; ++gi) {
+            std::vector<int> grp;
+            for (int q = gi; q < m; q += ng) grp.push_back(v[q]);   // round robin: sizes differ by <= 1
+            if (grp.size() >= 2) out.push_back(grp);
+        }
+    }
     (void)n;
     return out;
 }

@@ -190,6 +190,7 @@ void set_last_error(const char* msg);
 // lockstep batched solves (lockstep.cu): problems of one grid size advanced together, one launch
 // per step for all of them
 bool lockstep_eligible(iim_geometry g, const iim_opts& o);
+int lockstep_group_size();
 iim_status lockstep_enqueue(const std::vector<int>& idx, iim_geometry const* geoms, const double* const* omega,
                             const double* const* psi_b, const double* const* psi_box, const double* const* gamma,
                             double* const* psibar, double* const* psi_out, double* const* ux_out,

@@ -491,12 +491,14 @@ void lockstep_forget(iim_geometry g) {
     }
 }
 
-static std::atomic<int> g_ls_enabled{1};
+static std::atomic<int> g_ls_group{4};
+
+int lockstep_group_size() { return g_ls_group.load(); }
 
 // Problems that can join a lockstep group under these options.
 bool lockstep_eligible(iim_geometry g, const iim_opts& o) {
     const int ns = g->na + g->ncirc;
-    return g_ls_enabled.load() && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 && o.precond == 1 && ns > 0 && g->pc_ready &&
+    return g_ls_group.load() >= 2 && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 && o.precond == 1 && ns > 0 && g->pc_ready &&
            g->V && g->krylov_m >= o.restart && (g->ncirc == 0 || g->cap_ready) &&
            sizeof(float) * 4 * (size_t)((ns + 3) & ~3) <= 200 * 1024;
 }
@@ -1036,4 +1038,6 @@ void lockstep_finish(void* handle, const std::vector<int>& idx, const iim_opts& 
 
 }  // namespace iim
 
-extern "C" int iim_set_lockstep(int enabled) { return iim::g_ls_enabled.exchange(enabled ? 1 : 0); }
+extern "C" int iim_set_lockstep(int max_group) {
+    return iim::g_ls_group.exchange(max_group < 0 ? 0 : std::min(max_group, 1024));
+}

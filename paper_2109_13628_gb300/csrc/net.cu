@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "iim_ops.cuh"
 
 struct iim_net_s {
     int device = 0;
@@ -260,7 +261,7 @@ static iim_status conv(iim_net_s* net, const float* x, const float* gate, const 
     if (Co > 1) {
         const int ncot = (Co + 31) / 32;
         const size_t sm = conv_smem(d, 32);
-        IIM_TRY(cudaFuncSetAttribute(k_conv<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        IIM_CHECK(allow_smem(k_conv<32>, sm));
         launch("net_conv", 4.0 * (double)B * H * W * (Ci + Co), 18.0 * (double)B * H * W * Ci * Co, k_conv<32>,
                dim3((W + TX - 1) / TX, (H + TY - 1) / TY, B * ncot), blk, sm, s, x, gate, w, bias, y, Ci, Co, H, W, d, relu);
     } else {
@@ -306,7 +307,7 @@ static iim_status backward(iim_net_s* net, int B, int H, int W, const float* x, 
         const float* gate = l == net->nl - 1 ? nullptr : net->act + (size_t)l * net->cap;
         const int d = net->dil[l];
         const size_t sm = sizeof(float) * ((size_t)WG_MAXC * WG_S * WG_S + (size_t)(WG_S + 2 * d) * (WG_S + 2 * d));
-        IIM_TRY(cudaFuncSetAttribute(k_conv_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        IIM_CHECK(allow_smem(k_conv_wgrad, sm));
         launch("net_wgrad", 4.0 * (double)B * H * W * (net->ci[l] + net->co[l]), 2.0 * B * H * W * 9.0 * net->ci[l] * net->co[l],
                k_conv_wgrad, dim3((W + WG_R - 1) / WG_R, (H + WG_R - 1) / WG_R, B), 288, sm, s, xin, (const float*)g, gate,
                net->gr + net->woff[l], net->gr + net->boff[l], net->ci[l], net->co[l], H, W, d);

@@ -272,7 +272,7 @@ iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_
     float* T = W1 + (size_t)GJ_LDW * n;
     int* perm = reinterpret_cast<int*>(T + (size_t)GJ_B * lda);
     const size_t upd_smem = sizeof(float) * 2 * GJ_B * GJ_TILE;
-    IIM_TRY(cudaFuncSetAttribute(k_gj_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)upd_smem));
+    IIM_CHECK(allow_smem(k_gj_update, upd_smem));
     const long welems = (long)n * GJ_LDW;
     const unsigned wblocks = (unsigned)((welems + 255) / 256);
     const unsigned sblocks = (unsigned)std::min<long>(304, (welems + 1023) / 1024);
@@ -304,16 +304,16 @@ iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const 
     constexpr int W = 8;
     const size_t sm4 = sizeof(float) * 4 * (size_t)((n + 3) & ~3);
     if (sm4 <= 200 * 1024) {
-        if (sm4 > 48 * 1024)
-            IIM_TRY(cudaFuncSetAttribute(k_dense_matvec4<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm4));
+        // the limit only ever grows (allow_smem): solves of different sizes on other threads
+        // must not lower it under this launch
+        IIM_CHECK(allow_smem(k_dense_matvec4<W>, sm4));
         launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec4<W>, (n + W - 1) / W, W * 32, sm4, s,
                n, M, ldm, v, jidx, vstride, out, accumulate, stop);
         IIM_LAUNCHED();
         return IIM_OK;
     }
     const size_t sm = sizeof(float) * (size_t)n;
-    if (sm > 48 * 1024)
-        IIM_TRY(cudaFuncSetAttribute(k_dense_matvec<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    IIM_CHECK(allow_smem(k_dense_matvec<W>, sm));
     launch("precond_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec<W>, (n + W - 1) / W, W * 32, sm, s, n, M,
            ldm, v, jidx, vstride, out, accumulate, stop);
     IIM_LAUNCHED();

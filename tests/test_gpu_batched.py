@@ -161,10 +161,12 @@ def test_lockstep_groups_equal_single_solves(prec):
                 [t.clone() for t in a["psibar"]], stats, iim.iim_launch_count() - before)
 
     batch()                                   # first solves: host-driven, per problem
-    prev = iim.iim_set_lockstep(False)
+    prev = iim.iim_set_lockstep(0)
     per_problem = batch()                     # one whole-solve graph per problem
-    iim.iim_set_lockstep(True)
-    lock = batch()                            # lockstep groups
+    iim.iim_set_lockstep(2)
+    pairs = batch()                           # lockstep groups of two, concurrent
+    iim.iim_set_lockstep(64)
+    lock = batch()                            # one lockstep group per grid size
     iim.iim_profile_begin()
     hosted = batch()                          # lockstep, host-driven under the profiler
     prof = iim.iim_profile_end()
@@ -176,7 +178,7 @@ def test_lockstep_groups_equal_single_solves(prec):
         pb1 = torch.zeros_like(a["psibar"][k])
         s1 = iim.iim_poisson_solve(geo, a["omega"][k], a["psi_b"][k], None, a["gamma"][k], pb1, psi1, ux1, uy1,
                                    opts=opts)
-        for run in (per_problem, lock, hosted):
+        for run in (per_problem, pairs, lock, hosted):
             assert torch.equal(run[0][k], psi1) and torch.equal(run[1][k], ux1) and torch.equal(run[2][k], uy1), k
             assert torch.equal(run[3][k], pb1)
             assert run[4][k]["iters"] == s1["iters"] and run[4][k]["refinements"] == s1["refinements"]
