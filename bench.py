@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--restart", type=int, default=64)
     ap.add_argument("--sweep", action="store_true", help="print iterations/time for a grid of inner tolerances and exit")
     ap.add_argument("--no-precond", action="store_true", help="chosen form without the dense Schur preconditioner")
+    ap.add_argument("--precond", type=int, default=3,
+                    help="chosen form's iim_opts.precond: 1 dense inverse as right preconditioner of the transform "
+                         "operator, 3 the same with the dense Schur matrix as the inner operator")
     ap.add_argument("--batch", type=int, default=8, help="independent problems in flight per step")
     ap.add_argument("--no-c4", action="store_true", help="skip the mixed-size batched workload")
     ap.add_argument("--c4-count", type=int, default=96)
@@ -373,7 +376,7 @@ def rk3_c2(iim, inputs, dev, steps=3):
     # the geometry does not move, so the dense Schur preconditioner is built once for all steps
     pc_ms = iim.iim_build_preconditioner(geo)
     for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed", iim.IIM_MIXED, 0),
-                           ("mixed_precond", iim.IIM_MIXED, 1)):
+                           ("mixed_precond", iim.IIM_MIXED, 1), ("mixed_dense_op", iim.IIM_MIXED, 3)):
         w, gam, pbar = T(P.omega.ravel()), T(gam0), torch.zeros(1, dtype=torch.float64, device=dev)
         opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc)
 
@@ -397,13 +400,14 @@ def rk3_c2(iim, inputs, dev, steps=3):
                      "krylov_iters_per_stage": [s["iters"] for s in stats],
                      "circ_err_max": max(s["circ_err_max"] for s in stats),
                      "kelvin_invariant_drift": float(abs(kelvin)), "omega": w1}
-    w64, w32, wpc = (out[k].pop("omega") for k in ("fp64", "mixed", "mixed_precond"))
+    w64, w32, wpc, wdo = (out[k].pop("omega") for k in ("fp64", "mixed", "mixed_precond", "mixed_dense_op"))
     geo.close()
     rel = lambda a: float(np.abs(a - w64).max() / np.abs(w64).max())
     return {"config": "flow past a cylinder R 0.5, [-2,6]x[-2,2], 1024 x 512, U 1, Re 200, CFL 0.5, noise 1e-3 seed 0; "
                       "64 threads per 1024-point line",
             **out, "precond_setup_ms": pc_ms, "mixed_vs_fp64_rel_linf": rel(w32),
-            "mixed_precond_vs_fp64_rel_linf": rel(wpc),
+            "mixed_precond_vs_fp64_rel_linf": rel(wpc), "mixed_dense_op_vs_fp64_rel_linf": rel(wdo),
+            "speedup_mixed_dense_op_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed_dense_op"]["ms_per_step"],
             "speedup_mixed_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed"]["ms_per_step"],
             "speedup_mixed_precond_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed_precond"]["ms_per_step"],
             "kelvin_note": "box-wide invariant (Gamma + h^2 sum omega off the bodies' regions) also moves by the "
@@ -536,10 +540,15 @@ def c3_multibody(iim, inputs, dev, steps=3):
     gam = T([h * h * P.omega[r[2] - 1:r[3], r[0] - 1:r[1]].sum() for r in P.regions])
     om, pb = T(P.omega.ravel()), T(np.zeros(geo.n_control))
     out, res = {}, {}
-    for name, prec in (("fp64", iim.IIM_FP64), ("mixed", iim.IIM_MIXED)):
+    t0 = time.perf_counter()
+    pc_ms = iim.iim_build_preconditioner(geo)
+    out["precond_setup_s"] = time.perf_counter() - t0
+    out["precond_setup_gpu_ms"] = pc_ms
+    for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed", iim.IIM_MIXED, 0),
+                           ("mixed_precond", iim.IIM_MIXED, 1), ("mixed_dense_op", iim.IIM_MIXED, 3)):
         psi = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
         pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
-        opts = iim.default_opts(prec=prec, rtol=1e-10, max_iter=4000)
+        opts = iim.default_opts(prec=prec, rtol=1e-10, max_iter=4000, precond=pc)
         iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, opts=opts)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -551,8 +560,9 @@ def c3_multibody(iim, inputs, dev, steps=3):
         res[name] = psi
         out[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "krylov_iters": st["iters"],
                      "refinements": st["refinements"], "rel_res": st["rel_res"], "circ_err_max": st["circ_err_max"]}
-    out["mixed_vs_fp64_rel_linf"] = float((res["mixed"] - res["fp64"]).abs().max() / res["fp64"].abs().max())
-    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    for k in ("mixed", "mixed_precond", "mixed_dense_op"):
+        out[f"{k}_vs_fp64_rel_linf"] = float((res[k] - res["fp64"]).abs().max() / res["fp64"].abs().max())
+        out[f"speedup_{k}_vs_fp64"] = out["fp64"]["ms_per_solve"] / out[k]["ms_per_solve"]
     iim.iim_profile_begin()
     psi = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
     pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
@@ -604,7 +614,7 @@ def main():
     g = P.grid
     T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
     grid = iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny)
-    precond = 0 if args.no_precond else 1
+    precond = 0 if args.no_precond else args.precond
     NXY = (g.nx - 1) * (g.ny - 1)
     B = max(1, args.batch)
     # B independent problems (each its own geometry workspace) on the same cylinder workload
@@ -640,7 +650,8 @@ def main():
                                              opts=opts_for(iim.IIM_MIXED), n_streams=n_streams)
 
     if args.sweep:
-        for prec, pc in ((iim.IIM_MIXED, 1), (iim.IIM_FP64, 1), (iim.IIM_MIXED, 0), (iim.IIM_FP64, 0)):
+        for prec, pc in ((iim.IIM_MIXED, 3), (iim.IIM_MIXED, 1), (iim.IIM_FP64, 3), (iim.IIM_FP64, 1),
+                         (iim.IIM_MIXED, 0), (iim.IIM_FP64, 0)):
             if pc and not precond:
                 continue
             for inner in ((1e-3, 1e-4, 1e-5, 1e-6, 3e-7) if prec == iim.IIM_MIXED else (5e-12, 5e-11)):
@@ -753,11 +764,12 @@ def main():
         kern.sort(key=lambda r: -r["ms"])
         return kern, sum(r["ms"] for r in kern)
 
-    # ---- per-kernel timing of the batched step: the lockstep group's kernels run host-driven
-    # under the per-kernel profiler (CUDA events around each launch on its stream); each launch
-    # carries the algorithmic bytes of all B problems
+    # ---- per-kernel timing of the timed form: with lockstep groups, the group's kernels run
+    # host-driven under the per-kernel profiler (CUDA events around each launch on its stream,
+    # each launch carrying the algorithmic bytes of the whole group); with one whole-solve graph
+    # per problem, the same solve's kernels one problem at a time
     kprof = min(args.steps, 10)
-    kern, tot_k = kernel_profile(lambda: solve_batch(n_streams) if B > 1 else solve(iim.IIM_MIXED), kprof)
+    kern, tot_k = kernel_profile(lambda: solve_batch(n_streams) if group > 1 else solve(iim.IIM_MIXED), kprof)
     kern1, tot_k1 = kernel_profile(lambda: solve(iim.IIM_MIXED), kprof)
     peaks, src = measured_peaks()
     mem = [r for r in kern if r["bytes"] > 0]
@@ -774,9 +786,11 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "l2_traffic": l2_traffic, "peak_source": src,
                 "alg_bytes_per_launch": dom["bytes"] / dom["launches"], "avg_launch_us": per_launch_s * 1e6,
                 "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None,
-                "timing": (f"batched step ({B} problems in lockstep, one launch per step for all): the same kernels "
-                           "run host-driven under the per-kernel profiler, CUDA events around each launch on its "
-                           "stream; bytes = the algorithmic bytes of all problems of the launch")}
+                "timing": (f"batched step (lockstep groups of {group}, one launch per step for a group): the same "
+                           "kernels run host-driven under the per-kernel profiler, CUDA events around each launch on "
+                           "its stream; bytes = the algorithmic bytes of all problems of the launch" if group > 1 else
+                           "timed form = one whole-solve graph per problem: the same solve's kernels one problem at "
+                           "a time under the per-kernel profiler, CUDA events around each launch on its stream")}
     # ---- end to end through the C ABI with host buffers (B problems per step)
     e2e = None
     if not args.no_e2e:
@@ -881,7 +895,9 @@ def main():
                    "l2": "flushed before every timed step (256 MiB write, outside the events)",
                    "form": ("mixed: FP32 DST-I box solves inside FP64 iterative refinement, GMRES("
                             f"{args.restart}) FP64 Krylov" + (", right-preconditioned by the dense FP32 inverse of the"
-                                                             " Schur matrix" if precond else "")),
+                                                             " Schur matrix" if precond else "") +
+                            (", inner operator the dense FP32 Schur matrix (transforms for each correction's "
+                             "right-hand side and recovery)" if precond == 3 else "")),
                    "parallelism": f"replicas x{ws}"},
         "single_problem": {"value": single, "unit": UNIT, "ms_per_solve": sum(ms1) / len(ms1)},
         "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": sum(ms64) / k64,

@@ -85,7 +85,14 @@ typedef struct {
                           the Schur matrix (built on first use, see iim_build_preconditioner);
                           2: each correction applies that inverse once, x = M b, with no Krylov
                           iterations; when a correction fails to halve the FP64 residual the
-                          remaining corrections use mode 1 (stats fallback bit 1) */
+                          remaining corrections use mode 1 (stats fallback bit 1);
+                          3: mode 1 with the inner Krylov operator S applied as the dense FP32
+                          matrix formed with the inverse (one matrix-vector product instead of
+                          three transform passes and a gather per iteration); the transforms
+                          remain for each correction's right-hand side and recovery, and the
+                          FP64 residual of the un-reduced system still decides convergence.
+                          Falls back to mode 1 when 4 (|A| + circulation bodies) floats exceed
+                          200 KB */
 } iim_opts;
 
 typedef struct {
@@ -184,7 +191,7 @@ iim_status iim_poisson_solve_batched(int n, iim_geometry const* geoms, const dou
                                      iim_stream stream);
 
 /* How iim_poisson_solve_batched and iim_poisson_solve_batched_host run problems that have been
- * solved once already, with iim_opts.precond == 1 and no guess.  max_group >= 2 (default 4):
+ * solved once already, with iim_opts.precond 1 or 3 and no guess.  max_group >= 2 (default 4):
  * the problems of equal grid size (and equal iim_geometry_set_tiles / _set_lines settings) are
  * split into groups of at most max_group problems (sizes as even as possible), and each group
  * advances in lockstep -- one kernel launch per step of the solve for every problem of the

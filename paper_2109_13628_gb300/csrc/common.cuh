@@ -153,6 +153,7 @@ struct iim_geometry_s {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // dense Schur-complement preconditioner: [S | S^-1] row-major ns x 2ns (FP32), scratch
     float* pc_aug = nullptr;
+    float* pc_S = nullptr;   // copy of S itself (ns x ns, FP32) kept before the inversion
     float* pc_f = nullptr;   // Gauss-Jordan scratch (gj_scratch_floats)
     int* pc_info = nullptr;
     double* pc_z = nullptr;      // 2 ns
@@ -205,6 +206,9 @@ size_t gj_scratch_floats(int n);
 iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_t s);
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
                         int accumulate, const int* stop, cudaStream_t s);
+bool dense_matvec_fits(int n);
+iim_status dense_matvec_to(int n, const float* M, long ldm, const double* v, double* outb, const int* ojidx,
+                           long ostride, const int* stop, cudaStream_t s);
 __global__ void k_unit_vector(int n, int j, double* v);
 __global__ void k_store_column(int n, int j, const double* v, float* A);
 }

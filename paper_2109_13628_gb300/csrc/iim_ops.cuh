@@ -509,8 +509,9 @@ template <int WARPS>
 __device__ __forceinline__ void
 dense_matvec4_body(int n, const float* __restrict__ M, long ldm, const double* __restrict__ vbase,
                    const int* __restrict__ jidx, long vstride, double* __restrict__ out, int accumulate,
-                   const int* __restrict__ stop) {
+                   const int* __restrict__ stop, const int* __restrict__ ojidx = nullptr, long ostride = 0) {
     if (stop && *stop) return;
+    if (ojidx) out += (long)(*ojidx + 1) * ostride;   // out = column j + 1 of a Krylov basis
     extern __shared__ float4 s_v4[];
     float* s_v = reinterpret_cast<float*>(s_v4);
     const int stride = (n + 3) & ~3;

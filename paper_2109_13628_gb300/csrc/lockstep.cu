@@ -15,8 +15,8 @@
 // the arithmetic, in the same order, of its own solve: the results are bitwise equal.
 //
 // Scope: problems whose geometry has had one solve already (preconditioner, capacitance
-// responses and Krylov buffers in place), right-preconditioned GMRES (iim_opts.precond == 1),
-// no initial guess.  Other problems take the per-problem path of batched.cu.
+// responses and Krylov buffers in place), right-preconditioned GMRES (iim_opts.precond 1, or 3
+// with the dense Schur matrix as the inner operator), no initial guess.  Other problems take the per-problem path of batched.cu.
 //
 // The same step sequence also runs host-driven (each loop decision read back by the host),
 // which is how the per-kernel profiler times the batched kernels one launch at a time.
@@ -54,6 +54,7 @@ struct LsProb {
     void* tbuf;
     void* psiT;
     const float* pc_inv;   // right half of [S | S^-1], leading dimension 2 ns
+    const float* pc_S;     // S itself (ns x ns), the inner operator of iim_opts.precond == 3
     int* di;
     const double *cap_psi, *cap_dev;
     const double *omega, *psi_b, *ring, *gamma;
@@ -148,15 +149,23 @@ __global__ void __launch_bounds__(BLOCK) kb_gather(const LsProb* __restrict__ P,
                           p.aff_body, ls_vec(p, mode), 1, p.V, jidx, (long)p.ns, nullptr);
 }
 
-// z = M V_j (iteration, skipped once the problem's GMRES stopped) or x += M t (cycle end)
+// Dense products: z = M V_j (iteration, skipped once the problem's GMRES stopped), x += M t
+// (cycle end), and with the dense inner operator V_{j+1} = S z (iteration) or V_2 = S V_1
+// (restart).
+enum { MV_PRECOND = 0, MV_XUPDATE = 1, MV_S_ITER = 2, MV_S_RESTART = 3 };
 template <int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) kb_matvec(const LsProb* __restrict__ P, int xupdate, int gate) {
+__global__ void __launch_bounds__(WARPS * 32) kb_matvec(const LsProb* __restrict__ P, int op, int gate) {
     const LsProb& p = P[blockIdx.z];
     if (ls_off(p, gate) || p.ns == 0) return;
-    if (!xupdate)
-        dense_matvec4_body<WARPS>(p.ns, p.pc_inv, 2L * p.ns, p.V, p.di + DI_J, (long)p.ns, p.pc_z, 0, p.di + DI_STOP);
+    const long ns = p.ns;
+    if (op == MV_PRECOND)
+        dense_matvec4_body<WARPS>(p.ns, p.pc_inv, 2L * ns, p.V, p.di + DI_J, ns, p.pc_z, 0, p.di + DI_STOP);
+    else if (op == MV_XUPDATE)
+        dense_matvec4_body<WARPS>(p.ns, p.pc_inv, 2L * ns, p.pc_z + ns, nullptr, 0L, p.xsol, 1, nullptr);
+    else if (op == MV_S_ITER)
+        dense_matvec4_body<WARPS>(p.ns, p.pc_S, ns, p.pc_z, nullptr, 0L, p.V, 0, p.di + DI_STOP, p.di + DI_J, ns);
     else
-        dense_matvec4_body<WARPS>(p.ns, p.pc_inv, 2L * p.ns, p.pc_z + p.ns, nullptr, 0L, p.xsol, 1, nullptr);
+        dense_matvec4_body<WARPS>(p.ns, p.pc_S, ns, p.V + ns, nullptr, 0L, p.V, 0, nullptr, p.di + DI_TMPJ, ns);
 }
 
 // ------------------------------------------------------------------------- Krylov kernels
@@ -443,7 +452,7 @@ __global__ void kb_ref_ctl(const LsProb* __restrict__ P, int n, double rtol, int
 // ------------------------------------------------------------------------- the group
 struct LsGroup {
     std::vector<iim_geometry> geos;
-    int prec = 0, m = 0, max_refine = 0, max_iter = 0, cap = 0;
+    int prec = 0, m = 0, max_refine = 0, max_iter = 0, cap = 0, dense = 0;
     double rtol = 0.0, inner = 0.0;
     int nx = 0, ny = 0, NX = 0, NY = 0, wide = 0, cols_c = 4;
     // launch extents: maxima over the group
@@ -498,7 +507,8 @@ int lockstep_group_size() { return g_ls_group.load(); }
 // Problems that can join a lockstep group under these options.
 bool lockstep_eligible(iim_geometry g, const iim_opts& o) {
     const int ns = g->na + g->ncirc;
-    return g_ls_group.load() >= 2 && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 && o.precond == 1 && ns > 0 && g->pc_ready &&
+    return g_ls_group.load() >= 2 && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 &&
+           (o.precond == 1 || (o.precond == 3 && g->pc_S)) && ns > 0 && g->pc_ready &&
            g->V && g->krylov_m >= o.restart && (g->ncirc == 0 || g->cap_ready) &&
            sizeof(float) * 4 * (size_t)((ns + 3) & ~3) <= 200 * 1024;
 }
@@ -520,6 +530,7 @@ static void fill_prob(LsProb& q, iim_geometry g, int prec, const double* omega, 
     q.psi_ext = g->psi_ext; q.res = g->res; q.partial = g->partial; q.small = g->small; q.V = g->V; q.H = g->H;
     q.xsol = g->xsol; q.bvec = g->bvec; q.pc_z = g->pc_z; q.tbuf = g->tbuf; q.psiT = g->psiT;
     q.pc_inv = g->pc_aug + (q.ns);
+    q.pc_S = g->pc_S;
     q.di = g->d_int;
     q.cap_psi = g->cap_psi; q.cap_dev = g->cap_dev;
     q.omega = omega; q.psi_b = psi_b; q.ring = ring; q.gamma = gamma; q.psibar = psibar; q.psi_out = psi_out;
@@ -633,14 +644,14 @@ struct LsEmit {
         return IIM_OK;
     }
 
-    iim_status matvec(int xupdate, int gate) {
+    iim_status matvec(int op, int gate) {
         constexpr int W = 8;
         const size_t sm4 = sizeof(float) * 4 * (size_t)((G->max_ns + 3) & ~3);
         IIM_CHECK(allow_smem(kb_matvec<W>, sm4));
         double bytes = 0.0;
         for (iim_geometry g : G->geos) bytes += 4.0 * (double)(g->na + g->ncirc) * (g->na + g->ncirc);
-        launch("ls_precond_matvec", bytes, 0.0, kb_matvec<W>, grid((G->max_ns + W - 1) / W), W * 32, sm4, s,
-               (const LsProb*)G->d_probs, xupdate, gate);
+        launch(op >= MV_S_ITER ? "ls_dense_schur_matvec" : "ls_precond_matvec", bytes, 0.0, kb_matvec<W>,
+               grid((G->max_ns + W - 1) / W), W * 32, sm4, s, (const LsProb*)G->d_probs, op, gate);
         IIM_LAUNCHED();
         return IIM_OK;
     }
@@ -708,11 +719,15 @@ struct LsEmit {
     // one preconditioned GMRES iteration: z = M v_j, v_{j+1} = S z, Arnoldi step
     template <typename T>
     iim_status iteration(cudaGraphConditionalHandle h_it) {
-        IIM_CHECK(matvec(0, G_IT));
-        IIM_CHECK(rows_fwd<T>(M_APPLY_PCZ, G_IT));
-        IIM_CHECK(cols<T>(M_APPLY_PCZ, G_IT));
-        IIM_CHECK((rows_inv<T, INV_STORE_T>(G_IT)));
-        IIM_CHECK(gather<T>(M_APPLY_PCZ, G_IT));
+        IIM_CHECK(matvec(MV_PRECOND, G_IT));
+        if (G->dense) {
+            IIM_CHECK(matvec(MV_S_ITER, G_IT));
+        } else {
+            IIM_CHECK(rows_fwd<T>(M_APPLY_PCZ, G_IT));
+            IIM_CHECK(cols<T>(M_APPLY_PCZ, G_IT));
+            IIM_CHECK((rows_inv<T, INV_STORE_T>(G_IT)));
+            IIM_CHECK(gather<T>(M_APPLY_PCZ, G_IT));
+        }
         launch("ls_gmres_arnoldi", 0.0, 0.0, kb_arnoldi<256>, grid(1), 256, 0, s, (const LsProb*)G->d_probs,
                KLayout{G->m});
         launch("ls_loop_ctl", 0.0, 0.0, kb_loop_ctl, 1, 256, 0, s, (const LsProb*)G->d_probs, G->n(), G->m + 2, h_it,
@@ -726,7 +741,7 @@ struct LsEmit {
         launch("ls_gmres_backsolve", 0.0, 0.0, kb_backsolve<256>, grid(1), 256, 0, s, (const LsProb*)G->d_probs,
                KLayout{G->m});
         IIM_LAUNCHED();
-        IIM_CHECK(matvec(1, G_CYC));
+        IIM_CHECK(matvec(MV_XUPDATE, G_CYC));
         launch("ls_cyc_ctl", 0.0, 0.0, kb_cyc_ctl, 1, 256, 0, s, (const LsProb*)G->d_probs, G->n(),
                G->max_iter / G->m + 2, h_cyc, h_rs, flag(), cnt());
         IIM_LAUNCHED();
@@ -737,10 +752,14 @@ struct LsEmit {
     template <typename T>
     iim_status restart() {
         IIM_CHECK(vec(V_RESTART_PREP, G_CYC));
-        IIM_CHECK(rows_fwd<T>(M_APPLY_VTMP, G_CYC));
-        IIM_CHECK(cols<T>(M_APPLY_VTMP, G_CYC));
-        IIM_CHECK((rows_inv<T, INV_STORE_T>(G_CYC)));
-        IIM_CHECK(gather<T>(M_APPLY_VTMP, G_CYC));
+        if (G->dense) {
+            IIM_CHECK(matvec(MV_S_RESTART, G_CYC));
+        } else {
+            IIM_CHECK(rows_fwd<T>(M_APPLY_VTMP, G_CYC));
+            IIM_CHECK(cols<T>(M_APPLY_VTMP, G_CYC));
+            IIM_CHECK((rows_inv<T, INV_STORE_T>(G_CYC)));
+            IIM_CHECK(gather<T>(M_APPLY_VTMP, G_CYC));
+        }
         IIM_CHECK(vec(V_RESTART_RES, G_CYC));
         launch("ls_gmres_start", 0.0, 0.0, kb_start<256>, grid(1), 256, 0, s, (const LsProb*)G->d_probs, KLayout{G->m},
                1, 0, 0.0);
@@ -893,7 +912,7 @@ static iim_status make_group(const std::vector<iim_geometry>& geos, const iim_op
     LsGroup* G = new LsGroup();
     G->geos = geos;
     G->prec = o.prec; G->m = o.restart; G->max_refine = o.max_refine; G->max_iter = o.max_iter;
-    G->rtol = o.rtol; G->inner = inner;
+    G->rtol = o.rtol; G->inner = inner; G->dense = o.precond == 3;
     iim_geometry g0 = geos[0];
     G->nx = g0->nx; G->ny = g0->ny; G->NX = g0->NX; G->NY = g0->NY; G->wide = g0->wide_lines; G->cols_c = g0->cols_c;
     for (iim_geometry g : geos) {
@@ -934,7 +953,8 @@ static iim_status make_group(const std::vector<iim_geometry>& geos, const iim_op
 
 static LsGroup* find_group(const std::vector<iim_geometry>& geos, const iim_opts& o, double inner) {
     for (LsGroup* G : g_ls_groups) {
-        if (G->geos != geos || G->prec != o.prec || G->m != o.restart || G->max_refine != o.max_refine ||
+        if (G->geos != geos || G->prec != o.prec || G->dense != (o.precond == 3) || G->m != o.restart ||
+            G->max_refine != o.max_refine ||
             G->max_iter != o.max_iter || G->rtol != o.rtol || G->inner != inner)
             continue;
         bool same = true;

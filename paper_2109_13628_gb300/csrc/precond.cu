@@ -299,6 +299,31 @@ iim_status gj_invert_aug(float* A, int n, float* scratch, int* info, cudaStream_
     return IIM_OK;
 }
 
+// out_{j+1} = M v for the Krylov basis column after *ojidx (the dense Schur operator of the
+// inner iteration, iim_opts.precond == 3); M must fit the staged-vector kernel (4 n floats of
+// shared memory <= 200 KB).
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_dense_matvec4_to(int n, const float* __restrict__ M, long ldm, const double* __restrict__ v,
+                   double* __restrict__ outb, const int* __restrict__ ojidx, long ostride,
+                   const int* __restrict__ stop) {
+    dense_matvec4_body<WARPS>(n, M, ldm, v, nullptr, 0L, outb, 0, stop, ojidx, ostride);
+}
+
+bool dense_matvec_fits(int n) { return sizeof(float) * 4 * (size_t)((n + 3) & ~3) <= 200 * 1024; }
+
+iim_status dense_matvec_to(int n, const float* M, long ldm, const double* v, double* outb, const int* ojidx,
+                           long ostride, const int* stop, cudaStream_t s) {
+    constexpr int W = 8;
+    const size_t sm4 = sizeof(float) * 4 * (size_t)((n + 3) & ~3);
+    if (!dense_matvec_fits(n)) return IIM_ERR_INVALID_ARG;
+    IIM_CHECK(allow_smem(k_dense_matvec4_to<W>, sm4));
+    launch("dense_schur_matvec", (double)n * n * 4.0, 2.0 * n * n, k_dense_matvec4_to<W>, (n + W - 1) / W, W * 32,
+           sm4, s, n, M, ldm, v, outb, ojidx, ostride, stop);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
 iim_status dense_matvec(int n, const float* M, long ldm, const double* v, const int* jidx, long vstride, double* out,
                         int accumulate, const int* stop, cudaStream_t s) {
     constexpr int W = 8;

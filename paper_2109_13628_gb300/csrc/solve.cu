@@ -820,6 +820,10 @@ struct Solver {
             launch("pc_column", 0.0, 0.0, k_store_column, eb, 256, 0, s, n, j, (const double*)(g->V + ld), g->pc_aug);
             IIM_LAUNCHED();
         }
+        // keep S (the left half) for the dense inner operator before it is reduced to I
+        if (!g->pc_S) IIM_TRY(cudaMalloc(&g->pc_S, sizeof(float) * (size_t)n * n));
+        IIM_TRY(cudaMemcpy2DAsync(g->pc_S, sizeof(float) * (size_t)n, g->pc_aug, sizeof(float) * 2 * (size_t)n,
+                                  sizeof(float) * (size_t)n, (size_t)n, cudaMemcpyDeviceToDevice, s));
         IIM_CHECK(gj_invert_aug(g->pc_aug, n, g->pc_f, g->pc_info, s));
         int info = 0;
         IIM_TRY(cudaMemcpyAsync(&info, g->pc_info, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -864,7 +868,10 @@ struct Solver {
         if (precond) {
             // right preconditioning: z = M v_j, v_{j+1} = S z
             IIM_CHECK(dense_matvec(ns, g->pc_aug + ns, 2L * ns, g->V, di() + DI_J, (long)ns, g->pc_z, 0, di() + DI_STOP, s));
-            IIM_CHECK(apply_vec<T>(VecArg{g->pc_z, nullptr, 0, 0}, di() + DI_J, di() + DI_STOP));
+            if (dense_op)
+                IIM_CHECK(dense_matvec_to(ns, g->pc_S, (long)ns, g->pc_z, g->V, di() + DI_J, (long)ns, di() + DI_STOP, s));
+            else
+                IIM_CHECK(apply_vec<T>(VecArg{g->pc_z, nullptr, 0, 0}, di() + DI_J, di() + DI_STOP));
         } else {
             IIM_CHECK(apply_at<T>(DI_J, di() + DI_STOP));
         }
@@ -873,7 +880,7 @@ struct Solver {
 
     template <typename T>
     iim_status ensure_graph(IterGraph& G) {
-        if (G.exec && G.prec == (int)sizeof(T) && G.m == m && G.pc == (int)precond) return IIM_OK;
+        if (G.exec && G.prec == (int)sizeof(T) && G.m == m && G.pc == pc_mode()) return IIM_OK;
         if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
         // capture on the geometry's private stream (the caller's may be the legacy stream,
         // which cannot be captured); the graph is then launched on the caller's stream
@@ -927,7 +934,7 @@ struct Solver {
         if (e != cudaSuccess) { G.exec = nullptr; record_cuda_error(e, "cudaGraphInstantiate", __FILE__, __LINE__); return IIM_ERR_CUDA; }
         G.prec = (int)sizeof(T);
         G.m = m;
-        G.pc = (int)precond;
+        G.pc = pc_mode();
         G.stream = s;
         G.nodes = (int)nn;
         return IIM_OK;
@@ -1085,7 +1092,10 @@ struct Solver {
         double* K = g->H;
         const int eb = (ns + 255) / 256;
         launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 1);
-        IIM_CHECK(apply_at<T>(DI_TMPJ, nullptr));
+        if (dense_op)
+            IIM_CHECK(dense_matvec_to(ns, g->pc_S, (long)ns, V + ld, V, di() + DI_TMPJ, ld, nullptr, s));
+        else
+            IIM_CHECK(apply_at<T>(DI_TMPJ, nullptr));
         if (seed)
             launch("seed_scale", 0.0, 0.0, k_seed_scale<1024>, 1, 1024, 0, s, ns, (const double*)g->bvec, V + 2 * ld,
                    g->xsol, g->small + SM_SEED);
@@ -1110,6 +1120,10 @@ struct Solver {
         return IIM_OK;
     }
     int direct = 0;   // corrections by one application of the dense inverse (opts.precond == 2)
+    // the inner Krylov operator is the dense FP32 Schur matrix formed for the preconditioner
+    // (opts.precond == 3) instead of the transforms
+    bool dense_op = false;
+    int pc_mode() const { return precond ? (dense_op ? 2 : 1) : 0; }
 
     // ---- the whole solve as one graph (SolveGraph); built on the private capture stream
     template <typename T>
@@ -1504,7 +1518,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     if (opts.restart < 1 || opts.restart > 64 || !(opts.rtol > 0.0) || opts.max_iter < 1 || opts.max_refine < 1)
         return IIM_ERR_INVALID_ARG;
     if ((opts.guess == 1 || opts.guess == 2) && !psi_guess) return IIM_ERR_INVALID_ARG;
-    if (opts.guess < 0 || opts.guess > 2 || opts.precond < 0 || opts.precond > 2) return IIM_ERR_INVALID_ARG;
+    if (opts.guess < 0 || opts.guess > 2 || opts.precond < 0 || opts.precond > 3) return IIM_ERR_INVALID_ARG;
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
     if (g->ncirc > 0)
@@ -1515,6 +1529,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     S.psibar = psibar; S.ns = g->na + g->ncirc; S.m = opts.restart; S.L = KLayout{opts.restart};
     S.precond = opts.precond != 0 && S.ns > 0;
     S.direct = opts.precond == 2 && S.ns > 0;
+    S.dense_op = opts.precond == 3 && S.ns > 0 && dense_matvec_fits(S.ns);
     if (S.precond && !g->pc_ready) IIM_CHECK(S.build_precond());
     const bool use_cap = capacitance && g->ncirc > 0;
     if (use_cap && !g->cap_ready) {
@@ -1533,14 +1548,14 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         g->host_solves > 0 && !g->solve_graph_failed) {
         const void* key[9] = {omega, psi_b, psi_box, gamma, psibar, psi_out, ux_out, uy_out, g->V};
         SolveGraph* G = (SolveGraph*)g->solve_graph;
-        const bool match = G && G->exec && G->prec == opts.prec && G->m == opts.restart && G->pc == (int)S.precond &&
+        const bool match = G && G->exec && G->prec == opts.prec && G->m == opts.restart && G->pc == S.pc_mode() &&
                            G->max_refine == opts.max_refine && G->max_iter == opts.max_iter &&
                            G->cap == (int)use_cap && G->inner == inner && G->rtol == opts.rtol &&
                            std::memcmp(G->ptrs, key, sizeof(key)) == 0;
         if (!match) {
             drop_solve_graph(g);
             G = new SolveGraph();
-            G->prec = opts.prec; G->m = opts.restart; G->pc = (int)S.precond; G->max_refine = opts.max_refine;
+            G->prec = opts.prec; G->m = opts.restart; G->pc = S.pc_mode(); G->max_refine = opts.max_refine;
             G->max_iter = opts.max_iter; G->cap = (int)use_cap; G->inner = inner; G->rtol = opts.rtol;
             std::memcpy(G->ptrs, key, sizeof(key));
             const iim_status bs =

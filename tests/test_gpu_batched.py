@@ -134,8 +134,8 @@ def test_empty_and_single_problem_batches():
         g.close()
 
 
-@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
-def test_lockstep_groups_equal_single_solves(prec):
+@pytest.mark.parametrize("prec,precond", [(iim.IIM_FP64, 1), (iim.IIM_MIXED, 1), (iim.IIM_MIXED, 3)])
+def test_lockstep_groups_equal_single_solves(prec, precond):
     """From the second batched call on, the problems of each grid size advance as one lockstep
     group (one launch per step for the whole group, loops decided on the device).  Every problem
     gets exactly its single solve's psi, u, psibar, iteration and refinement counts; lockstep
@@ -144,7 +144,7 @@ def test_lockstep_groups_equal_single_solves(prec):
     batched kernels."""
     problems = inputs.batched_c4(count=10, seed=5, sizes=(64, 128, 256))
     kept, geos, a = build_batch(problems)
-    opts = iim.default_opts(prec=prec, rtol=1e-11, precond=1)
+    opts = iim.default_opts(prec=prec, rtol=1e-11, precond=precond)
     ux = [torch.empty_like(t) for t in a["psi"]]
     uy = [torch.empty_like(t) for t in a["psi"]]
 
@@ -186,6 +186,7 @@ def test_lockstep_groups_equal_single_solves(prec):
     assert lock[5] < per_problem[5]
     names = {r["name"] for r in prof}
     assert ("ls_cols_f64" if prec == iim.IIM_FP64 else "ls_cols_f32") in names
+    assert ("ls_dense_schur_matvec" in names) == (precond == 3)
     assert "ls_gmres_arnoldi" in names and "ls_residual_f64" in names
     for g in geos:
         g.close()

@@ -72,3 +72,33 @@ def test_direct_corrections_match_oracle(prec):
     if not out["stats"]["fallback"] & 2:
         assert out["stats"]["iters"] == 0
     geo.close()
+
+
+@pytest.mark.parametrize("n", [64, 256])
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_dense_inner_operator_matches_oracle(n, prec):
+    """precond = 3: the inner Krylov operator is the dense FP32 Schur matrix (formed with the
+    preconditioner) instead of the transforms; the FP64 un-reduced residual still decides
+    convergence, so the solution is the same discrete solution within the stated tolerances,
+    with restart 64 and with restart 2 (restart residuals through the dense operator), and the
+    graph-driven solve equals the host-driven one bit for bit."""
+    P = inputs.bicubic_bodies(n, seed=n + 9, circulation=True)
+    w = inputs.vortex_field(P.grid, 31, count=20, sigma=0.2)
+    P.omega = np.where(P.phi >= 0, w, 0.0)[1:-1, 1:-1]
+    S = op.Setup(P)
+    gam = op.gamma_from_regions(P) + np.array([0.05, -0.1, 0.02])
+    ref, pb_ref = op.solve_unreduced(S, gamma=gam)
+    geo = gu.setup(P)
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    for restart in (64, 2):
+        opts = iim.default_opts(prec=prec, rtol=1e-13, max_iter=3000, restart=restart, precond=3)
+        first = gu.solve_opts(P, geo, gamma=gam, opts=opts)     # host-driven (first solve with these options)
+        again = gu.solve_opts(P, geo, gamma=gam, opts=opts)     # whole-solve graph
+        for out in (first, again):
+            err = np.abs(out["psi"] - ref[1:-1, 1:-1])[fl].max() / np.abs(ref).max()
+            assert err < TOL[prec], (restart, err, out["stats"])
+            assert np.allclose(out["psibar"], pb_ref, rtol=TOL[prec], atol=TOL[prec] * np.abs(ref).max())
+            assert out["stats"]["rel_res"] <= 1e-13
+        assert np.array_equal(first["psi"], again["psi"])
+        assert first["stats"]["iters"] == again["stats"]["iters"]
+    geo.close()
