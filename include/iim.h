@@ -228,6 +228,16 @@ iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, cons
  * IIM_ERR_INVALID_ARG. */
 iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
 
+/* How the column pass of the geometry's FP32 rectangular solves works: 0 (default) uses the
+ * column DST pair with the eigenvalue division; 1 solves, for every x mode of the row transform,
+ * the tridiagonal system that the 5-point operator becomes along the column (Thomas algorithm
+ * with tabulated elimination factors; O(ny) work per column, one thread per column).  Both
+ * compute the same discrete inverse (the FFT / tridiagonal form of the rectangular solve of
+ * Sec. 4.2) to FP32 rounding; the tridiagonal form's rounding is larger and its sequential
+ * recurrence slower on the GPU, so it is an alternative, not the default.  FP64 transforms
+ * always use the DST pair; grids with nx < 32 too.  Errors: IIM_ERR_INVALID_ARG. */
+iim_status iim_geometry_set_column_solver(iim_geometry g, int mode);
+
 /* Threads per transformed line for 1024-point lines: 32 (default: one warp, fewest
  * instructions, best when many solves share the GPU) or 64 (two warps per line: lower latency
  * of one solve, about 6 % more instructions).  Other line lengths use one warp.  Errors:

@@ -69,6 +69,7 @@ SIGNATURES = [
                                             ctypes.POINTER(iim_opts), _vp, _i, _vp]),
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
     ("iim_geometry_set_lines", _i, [_vp, _i]),
+    ("iim_geometry_set_column_solver", _i, [_vp, _i]),
     ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
     ("iim_net_num_params", ctypes.c_longlong, [_vp]),
     ("iim_net_get_params", _i, [_vp, _vp, ctypes.c_longlong]),
@@ -231,6 +232,12 @@ def iim_geometry_set_tiles(g: "Geometry", cols_per_block: int):
 def iim_geometry_set_lines(g: "Geometry", threads_per_line: int):
     """32 (one warp per 1024-point line, the default) or 64 (lower single-solve latency)."""
     _check(load().iim_geometry_set_lines(g.handle, int(threads_per_line)), "iim_geometry_set_lines")
+
+
+def iim_geometry_set_column_solver(g: "Geometry", mode: int):
+    """Column pass of the FP32 rectangular solves: 1 tridiagonal solves per x mode (default),
+    0 the column DST pair."""
+    _check(load().iim_geometry_set_column_solver(g.handle, int(mode)), "iim_geometry_set_column_solver")
 
 
 def _host_ptr(t, dtype=None, numel=None, name="tensor"):

@@ -30,10 +30,11 @@ iim_opts opts_or_default(const iim_opts* o) {
 // concurrently on their own streams); groups of one problem stay on the per-problem path.
 std::vector<std::vector<int>> lockstep_groups(int n, iim_geometry const* geoms, const std::vector<int>& order,
                                               const iim_opts& o) {
-    std::map<std::tuple<long, int, int, int, int>, std::vector<int>> b;
+    std::map<std::tuple<long, int, int, int, int, int>, std::vector<int>> b;
     for (int k : order) {
         iim_geometry g = geoms[k];
-        if (lockstep_eligible(g, o)) b[{-(long)g->nx * g->ny, g->nx, g->ny, g->wide_lines, g->cols_c}].push_back(k);
+        if (lockstep_eligible(g, o))
+            b[{-(long)g->nx * g->ny, g->nx, g->ny, g->wide_lines, g->cols_c, g->col_solver}].push_back(k);
     }
     std::vector<std::vector<int>> out;
     const int gmax = std::max(lockstep_group_size(), 1);

@@ -134,6 +134,12 @@ struct iim_geometry_s {
     // eigenvalues of the 1D three-point operators, x modes (NX) and y modes (NY)
     double *lam_x64 = nullptr, *lam_y64 = nullptr;
     float *lam_x32 = nullptr, *lam_y32 = nullptr;
+    // factor table of the tridiagonal column pass (FP32 transforms; tri.cuh): factors, per-column
+    // offsets, lengths and limits; col_solver 1 = tridiagonal column pass, 0 = column transforms
+    float* tri_e = nullptr;
+    int *tri_off = nullptr, *tri_len = nullptr;
+    float* tri_estar = nullptr;
+    int col_solver = 0;
 
     // ---- solver workspace
     double* psi_ext = nullptr;   // NY*NX FP64: fluid values, ghosts at A-, 0 elsewhere

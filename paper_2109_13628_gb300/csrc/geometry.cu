@@ -545,6 +545,31 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
         SETUP_CUDA(cudaMemcpy(g->lam_y64, ly.data(), NY * sizeof(double), cudaMemcpyHostToDevice));
         SETUP_CUDA(cudaMemcpy(g->lam_x32, fx.data(), NX * sizeof(float), cudaMemcpyHostToDevice));
         SETUP_CUDA(cudaMemcpy(g->lam_y32, fy.data(), NY * sizeof(float), cudaMemcpyHostToDevice));
+        // Thomas factors of the per-mode tridiagonal column systems (tri.cuh): for x mode c + 1,
+        // b = 2 + h^2 lam_x = 4 - 2 cos(pi (c + 1) / nx), e_0 = 1/b, e_j = 1/(b - e_{j-1}), kept
+        // (FP64 recurrence, stored in FP32) until they reach e* = (b - sqrt(b^2 - 4)) / 2 to within
+        // 2.5e-8 relative; later rows use e*
+        std::vector<float> te, tes(NX);
+        std::vector<int> toff(NX), tlen(NX);
+        for (int c = 0; c < NX; ++c) {
+            const double b = 4.0 - 2.0 * std::cos(M_PI * (c + 1) / nx);
+            const double es = 0.5 * (b - std::sqrt(b * b - 4.0));
+            toff[c] = (int)te.size();
+            double e = 1.0 / b;
+            for (int j = 0; j < NY; ++j) {
+                if (j > 0) e = 1.0 / (b - e);
+                if (std::fabs(e - es) <= 2.5e-8 * es) break;
+                te.push_back((float)e);
+            }
+            tlen[c] = (int)te.size() - toff[c];
+            tes[c] = (float)es;
+        }
+        SETUP_TRY(dalloc(&g->tri_e, te.size()));
+        SETUP_TRY(dalloc(&g->tri_off, NX)); SETUP_TRY(dalloc(&g->tri_len, NX)); SETUP_TRY(dalloc(&g->tri_estar, NX));
+        if (!te.empty()) SETUP_CUDA(cudaMemcpy(g->tri_e, te.data(), te.size() * sizeof(float), cudaMemcpyHostToDevice));
+        SETUP_CUDA(cudaMemcpy(g->tri_off, toff.data(), NX * sizeof(int), cudaMemcpyHostToDevice));
+        SETUP_CUDA(cudaMemcpy(g->tri_len, tlen.data(), NX * sizeof(int), cudaMemcpyHostToDevice));
+        SETUP_CUDA(cudaMemcpy(g->tri_estar, tes.data(), NX * sizeof(float), cudaMemcpyHostToDevice));
     }
     // solver workspace
     SETUP_TRY(dalloc(&g->psi_ext, npad));
@@ -577,7 +602,7 @@ void free_geometry(iim_geometry g) {
     void* ptrs[] = {g->cp_x, g->cp_y, g->cp_t, g->cp_body, g->cp_axis, g->cp_ei, g->cp_ej, g->aff_node, g->aff_body,
                     g->aff_row_ptr, g->aff_solid, g->gop_ptr, g->gop_idx, g->gop_w, g->minus_node, g->gh_ptr,
                     g->gh_idx, g->gh_w, g->node_class, g->body_circ, g->d_regions, g->lam_x64, g->lam_y64,
-                    g->lam_x32, g->lam_y32, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
+                    g->lam_x32, g->lam_y32, g->tri_e, g->tri_off, g->tri_len, g->tri_estar, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
                     g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf,
                     g->pc_aug, g->pc_S, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
     for (void* p : ptrs) cudaFree(p);

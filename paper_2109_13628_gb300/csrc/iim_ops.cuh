@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "dst.cuh"
+#include "tri.cuh"
 
 namespace iim {
 
@@ -24,6 +25,7 @@ struct Plan {
     T norm;
     int cols_c = 4;   // columns per block of the column pass (tile width)
     int wide = 0;     // 64 threads per 1024-point line instead of one warp
+    TriTab tri{};     // FP32 only: factor table of the tridiagonal column pass (e == nullptr: transforms)
 };
 
 // Algorithmic flops of one DST-I of n - 1 points through an n/2-point complex FFT

@@ -55,6 +55,7 @@ struct LsProb {
     void* psiT;
     const float* pc_inv;   // right half of [S | S^-1], leading dimension 2 ns
     const float* pc_S;     // S itself (ns x ns), the inner operator of iim_opts.precond == 3
+    TriTab tri;            // factor table of the tridiagonal column pass (FP32)
     int* di;
     const double *cap_psi, *cap_dev;
     const double *omega, *psi_b, *ring, *gamma;
@@ -115,6 +116,15 @@ kb_cols(const LsProb* __restrict__ P, int mode, int gate, T norm, const cpx<T>* 
     if (mode == M_RECOVER) { out0 = 0; out1 = p.NY - 1; }
     cols_body<T, C, FP>(p.NX, p.NY, p.NY + 1, __ffs(p.NY + 1) - 1, in0, in1, out0, out1, (T*)p.tbuf,
                         (const T*)p.lam_x, (const T*)p.lam_y, norm, tw);
+}
+
+__global__ void __launch_bounds__(32) kb_cols_tri(const LsProb* __restrict__ P, int mode, int gate) {
+    const LsProb& p = P[blockIdx.z];
+    if (ls_off(p, gate) || (mode != M_RECOVER && p.na == 0)) return;
+    int in0 = 0, in1 = p.NY - 1, out0 = p.jo0, out1 = p.jo1;
+    if (mode == M_APPLY_PCZ || mode == M_APPLY_VTMP) { in0 = p.ja0; in1 = p.ja1; }
+    if (mode == M_RECOVER) { out0 = 0; out1 = p.NY - 1; }
+    cols_tri_body(p.NX, p.NY, p.nx, in0, in1, out0, out1, (float*)p.tbuf, p.tri);
 }
 
 template <typename T, int WARPS, int MODE, int FP>
@@ -454,7 +464,7 @@ struct LsGroup {
     std::vector<iim_geometry> geos;
     int prec = 0, m = 0, max_refine = 0, max_iter = 0, cap = 0, dense = 0;
     double rtol = 0.0, inner = 0.0;
-    int nx = 0, ny = 0, NX = 0, NY = 0, wide = 0, cols_c = 4;
+    int nx = 0, ny = 0, NX = 0, NY = 0, wide = 0, cols_c = 4, tri = 0;
     // launch extents: maxima over the group
     int max_na = 0, max_ns = 0, max_nminus = 0, max_ncirc = 0, max_ja_rows = 0, max_jo_rows = 0;
     LsProb* d_probs = nullptr;
@@ -531,6 +541,8 @@ static void fill_prob(LsProb& q, iim_geometry g, int prec, const double* omega, 
     q.xsol = g->xsol; q.bvec = g->bvec; q.pc_z = g->pc_z; q.tbuf = g->tbuf; q.psiT = g->psiT;
     q.pc_inv = g->pc_aug + (q.ns);
     q.pc_S = g->pc_S;
+    if (prec != IIM_FP64 && g->col_solver == 1 && g->nx >= 32 && g->tri_e)
+        q.tri = TriTab{g->tri_e, g->tri_off, g->tri_len, g->tri_estar, (float)(g->h * g->h * (2.0 / g->nx))};
     q.di = g->d_int;
     q.cap_psi = g->cap_psi; q.cap_dev = g->cap_dev;
     q.omega = omega; q.psi_b = psi_b; q.ring = ring; q.gamma = gamma; q.psibar = psibar; q.psi_out = psi_out;
@@ -607,6 +619,20 @@ struct LsEmit {
 
     template <typename T>
     iim_status cols(int mode, int gate) {
+        if (sizeof(T) == 4 && G->tri) {
+            double bytes = 0.0;
+            for (iim_geometry g : G->geos) {
+                int in = g->NY, out = g->jo1 - g->jo0 + 1;
+                if (mode == M_APPLY_PCZ || mode == M_APPLY_VTMP) in = g->ja1 - g->ja0 + 1;
+                if (mode == M_RECOVER) out = g->NY;
+                bytes += (double)(in + out) * g->NX * sizeof(float);
+            }
+            IIM_CHECK(allow_smem(kb_cols_tri, kTriSmem));
+            launch("ls_tri_cols_f32", bytes, 0.0, kb_cols_tri, dim3(G->nx / 32, 1, G->n()), 32, kTriSmem, s,
+                   (const LsProb*)G->d_probs, mode, gate);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        }
         const int C = tile_width<T>(G->cols_c);
         if (C == 8) return cols_c<T, (sizeof(T) == 4 ? 8 : 4)>(mode, gate);
         if (C == 2) return cols_c<T, (sizeof(T) == 8 ? 2 : 4)>(mode, gate);
@@ -915,6 +941,7 @@ static iim_status make_group(const std::vector<iim_geometry>& geos, const iim_op
     G->rtol = o.rtol; G->inner = inner; G->dense = o.precond == 3;
     iim_geometry g0 = geos[0];
     G->nx = g0->nx; G->ny = g0->ny; G->NX = g0->NX; G->NY = g0->NY; G->wide = g0->wide_lines; G->cols_c = g0->cols_c;
+    G->tri = o.prec != IIM_FP64 && g0->col_solver == 1 && g0->nx >= 32 && g0->tri_e;
     for (iim_geometry g : geos) {
         G->max_na = std::max(G->max_na, g->na);
         G->max_ns = std::max(G->max_ns, g->na + g->ncirc);
@@ -960,6 +987,7 @@ static LsGroup* find_group(const std::vector<iim_geometry>& geos, const iim_opts
         bool same = true;
         for (iim_geometry g : geos)
             same = same && g->wide_lines == G->wide && g->cols_c == G->cols_c &&
+                   (o.prec != IIM_FP64 && g->col_solver == 1 && g->nx >= 32 && g->tri_e) == (G->tri != 0) &&
                    (g->ncirc > 0 && g->cap_ready ? 1 : 0) <= G->cap;
         if (same) return G;
     }

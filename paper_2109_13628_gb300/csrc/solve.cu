@@ -113,10 +113,33 @@ template <typename T, int C>
 static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
                             cudaStream_t s, int batch, long fstride);
 
+// Tridiagonal column pass (tri.cuh); blockIdx.y selects one of several fields fstride elements
+// apart.
+__global__ void __launch_bounds__(32)
+k_cols_tri(int NX, int NY, int nx, int in0, int in1, int out0, int out1, float* __restrict__ buf, TriTab t,
+           const int* __restrict__ stop, long fstride) {
+    if (stop && *stop) return;
+    cols_tri_body(NX, NY, nx, in0, in1, out0, out1, buf + (long)blockIdx.y * fstride, t);
+}
+
+// Launch: one warp per 32 padded columns, batch fields on grid y.
+static iim_status cols_tri(const Plan<float>& p, int in0, int in1, int out0, int out1, float* buf, const int* stop,
+                           cudaStream_t s, int batch, long fstride) {
+    IIM_CHECK(allow_smem(k_cols_tri, kTriSmem));
+    launch("tri_cols_f32", (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(float),
+           (double)batch * p.NX * 5.0 * p.NY, k_cols_tri, dim3(p.nx / 32, batch), 32, kTriSmem, s, p.NX, p.NY, p.nx,
+           in0, in1, out0, out1, buf, p.tri, stop, fstride);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
 // batch > 1: as many fields, fstride elements apart, in one launch
 template <typename T>
 static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s,
                        int batch = 1, long fstride = 0) {
+    if constexpr (sizeof(T) == 4) {
+        if (p.tri.e) return cols_tri(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
+    }
     const int C = tile_width<T>(p.cols_c);
     if (C == 8) return cols_tile<T, (sizeof(T) == 4 ? 8 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
     if (C == 2) return cols_tile<T, (sizeof(T) == 8 ? 2 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
@@ -180,8 +203,11 @@ Plan<double> make_plan<double>(iim_geometry g) {
 }
 template <>
 Plan<float> make_plan<float>(iim_geometry g) {
-    return Plan<float>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
-                       twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c, g->wide_lines};
+    Plan<float> p{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
+                  twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c, g->wide_lines};
+    if (g->col_solver == 1 && g->nx >= 32 && g->tri_e)
+        p.tri = TriTab{g->tri_e, g->tri_off, g->tri_len, g->tri_estar, (float)(g->h * g->h * (2.0 / g->nx))};
+    return p;
 }
 
 
@@ -1701,6 +1727,19 @@ extern "C" iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_lin
         g->wide_lines = wide;
         drop_solve_graph(g);
         // captured iteration graphs hold the previous kernels
+        for (void** gp : {&g->graph64, &g->graph32}) {
+            IterGraph* G = (IterGraph*)*gp;
+            if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+        }
+    }
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_geometry_set_column_solver(iim_geometry g, int mode) {
+    if (!g || (mode != 0 && mode != 1)) return IIM_ERR_INVALID_ARG;
+    if (g->col_solver != mode) {
+        g->col_solver = mode;
+        drop_solve_graph(g);   // the captured kernels change
         for (void** gp : {&g->graph64, &g->graph32}) {
             IterGraph* G = (IterGraph*)*gp;
             if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }

@@ -236,3 +236,29 @@ def test_multibody_2048_residual_circulation_and_mixed_vs_fp64():
     assert np.allclose(outs[iim.IIM_MIXED]["psibar"], outs[iim.IIM_FP64]["psibar"], rtol=0,
                        atol=1e-8 * np.abs(outs[iim.IIM_FP64]["psi"]).max())
     geo.close()
+
+
+@pytest.mark.parametrize("n", [64, 256, 512])
+def test_tridiagonal_and_transform_column_passes_agree_with_oracle(n):
+    """The FP32 column pass as the column DST pair (default) and as per-mode tridiagonal solves
+    compute the same discrete inverse: mixed-mode solves with either match the oracle to 1e-8,
+    with dense and with sparse (Schur operator) right-hand sides."""
+    P = inputs.bicubic_bodies(n, seed=n + 3, circulation=True)
+    w = inputs.vortex_field(P.grid, 17, count=12, sigma=0.2)
+    P.omega = np.where(P.phi >= 0, w, 0.0)[1:-1, 1:-1]
+    gam = op.gamma_from_regions(P)
+    ref, pb_ref = op.solve_unreduced(op.Setup(P), gamma=gam)
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    geo = gu.setup(P)
+    for mode in (1, 0, 1):
+        iim.iim_geometry_set_column_solver(geo, mode)
+        for precond in (0, 3):
+            if precond:
+                iim.iim_build_preconditioner(geo)
+            out = gu.solve_opts(P, geo, gamma=gam, opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-12,
+                                                                         precond=precond))
+            assert rel_linf(out["psi"], ref[1:-1, 1:-1], fl) < 1e-8, (mode, precond, out["stats"])
+            assert np.allclose(out["psibar"], pb_ref, atol=1e-8 * np.abs(ref).max())
+    with pytest.raises(iim.IIMError):
+        iim.iim_geometry_set_column_solver(geo, 2)
+    geo.close()
