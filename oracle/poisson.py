@@ -90,6 +90,28 @@ def poisson_box(f, h, ring=None):
     return dst1(dst1(U, axis=1), axis=0) * (2.0 / nx) * (2.0 / ny)
 
 
+def poisson_free(f, h):
+    """Free-space solve (Sec. 4.1, unbounded domain; Sec. 4.2, nabla_h^-2 with unbounded
+    boundary conditions): psi = h^2 sum_y G(x - y) f(y) with the lattice Green's function G of
+    the five-point Laplacian (oracle/lgf.py, gauge G(0, 0) = 0), for f on the interior nodes.
+    Returns psi at every node of the box, interior and ring: a node array (ny+1, nx+1).  The
+    convolution is a plain zero-padded linear convolution (scipy's FFT convolution)."""
+    from scipy.signal import fftconvolve
+
+    from . import lgf
+    ny1, nx1 = f.shape
+    nx, ny = nx1 + 1, ny1 + 1
+    src = np.zeros((ny + 1, nx + 1))
+    src[1:-1, 1:-1] = f
+    full = fftconvolve(src, lgf.lgf_full(nx, ny), mode="full")
+    return h * h * full[ny:2 * ny + 1, nx:2 * nx + 1]
+
+
+def ring_of(nodes):
+    """The box ring (layout of ring_to_nodes) of a node array."""
+    return np.concatenate([nodes[0, :], nodes[-1, :], nodes[1:-1, 0], nodes[1:-1, -1]])
+
+
 # ----------------------------------------------------------------------------- setup
 class Setup:
     """Geometry, ghost operators and index maps of one problem (Sec. 2.2, App. A)."""
@@ -324,18 +346,30 @@ def gmres_mgs(apply, b, tol, restart, max_iter, x0=None):
 
 
 def solve_schur(S: Setup, omega=None, ring=None, gamma=None, psibar=None,
-                tol=1e-13, restart=60, max_iter=2000, ops=None):
+                tol=1e-13, restart=60, max_iter=2000, ops=None, outer="dirichlet"):
     """The paper's algorithm (Sec. 4.2): GMRES on the augmented Schur system, then Eq.
-    psirecovery.  Returns (psi node array, psibar, gmres iterations, gmres rel. residual)."""
+    psirecovery.  Returns (psi node array, psibar, gmres iterations, gmres rel. residual).
+    outer = "dirichlet": the rectangular solve is the Dirichlet box (DST-I) with box data
+    `ring`; outer = "unbounded": it is the free-space solve (poisson_free), the box ring of the
+    result is part of the solution and `ring` is ignored."""
     P = S.prob
     omega = P.omega if omega is None else omega
-    ring = P.psi_box if ring is None else ring
+    free = outer == "unbounded"
+    ring = (np.zeros(2 * (S.nx + S.ny)) if free else P.psi_box) if ring is None else ring
     psibar = np.zeros(S.nb) if psibar is None else np.asarray(psibar, dtype=np.float64)
     gamma = np.zeros(S.nb) if gamma is None else np.asarray(gamma, dtype=np.float64)
     O = SchurOperators(S) if ops is None else ops
     h = S.h
     na, circ = O.na, S.circ
-    u0 = poisson_box(omega, h, ring)
+
+    def solve_rect(f, with_ring):
+        """Interior values of the rectangular solve (and the node array in free space)."""
+        if free:
+            nodes = poisson_free(f, h)
+            return nodes[1:-1, 1:-1], nodes
+        return poisson_box(f, h, ring if with_ring else None), None
+
+    u0, _ = solve_rect(omega, True)
     rhs_g = O.apply_A(u0) + O.B @ S.psi_b
     for k in range(S.nb):
         if k not in circ:
@@ -345,7 +379,7 @@ def solve_schur(S: Setup, omega=None, ring=None, gamma=None, psibar=None,
 
     def apply(x):
         g = x[:na]
-        y = g + O.apply_A(poisson_box(O.scatter(g), h))
+        y = g + O.apply_A(solve_rect(O.scatter(g), False)[0])
         for n, k in enumerate(circ):
             y = y - O.B1[:, k] * x[na + n]
         c = np.array([g[O.abody == k].sum() for k in circ])
@@ -353,8 +387,8 @@ def solve_schur(S: Setup, omega=None, ring=None, gamma=None, psibar=None,
 
     x, iters, rel = gmres_mgs(apply, bvec, tol, restart, max_iter)
     g = x[:na]
-    psi_in = poisson_box(omega - O.scatter(g), h, ring)
-    psi = ring_to_nodes(S.nx, S.ny, ring)
+    psi_in, nodes = solve_rect(omega - O.scatter(g), True)
+    psi = nodes.copy() if free else ring_to_nodes(S.nx, S.ny, ring)
     psi[1:-1, 1:-1] = np.where(S.solid[1:-1, 1:-1], 0.0, psi_in)
     pb = psibar.copy()
     for n, k in enumerate(circ):
@@ -379,12 +413,17 @@ def velocity(S: Setup, psi_nodes, psibar):
     return np.where(fl, ux, 0.0), np.where(fl, uy, 0.0)
 
 
-def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None):
+def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None, outer="dirichlet"):
     """Relative residual ||f - L u|| / ||f|| of the un-reduced system (circulation rows in the
-    units of omega).  Evaluated matrix-free; `psi_nodes` must carry the box data."""
+    units of omega).  Evaluated matrix-free; `psi_nodes` must carry the box data.  In free
+    space (outer = "unbounded") the box ring of psi_nodes is part of the solution, so the
+    known part f carries no box terms."""
     P = S.prob
     omega = P.omega if omega is None else omega
-    ring = P.psi_box if ring is None else ring
+    if outer == "unbounded":
+        ring = np.zeros(2 * (S.nx + S.ny))
+    else:
+        ring = P.psi_box if ring is None else ring
     gamma = np.zeros(S.nb) if gamma is None else np.asarray(gamma, dtype=np.float64)
     h = S.h
     e = extended_psi(S, psi_nodes, psibar)

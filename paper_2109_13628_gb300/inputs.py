@@ -192,6 +192,39 @@ def transport_body(n: int, nu: float) -> Problem:
                    gamma=np.zeros(1), exact=None, name=f"transport_body_{n}")
 
 
+# Sec. 4.3 (free-space velocity reconstruction): vortex and notched bodies of the paper's table;
+# the printed centres put the two bodies 0.014 apart with interlocking bounding boxes (no
+# rectangle R_k encloses one body without the other), so the bodies are moved apart here, with
+# their shapes, sizes and notches kept.
+FREE_SPACE_TWO_BODIES = dict(x0=(0.501, 0.501), gamma=1.0, nu_t=0.0025,
+                             bodies=[dict(xc=0.26, yc=0.72, r_a=0.167, r_b=0.057, theta_a=0.5, theta_b=1.8),
+                                     dict(xc=0.68, yc=0.34, r_a=0.157, r_b=0.057, theta_a=3.7, theta_b=2.0)])
+
+
+def lamb_oseen_two_bodies(n: int) -> Problem:
+    """Free-space reconstruction workload (Sec. 4.3, adapted as above): unit box, n x n cells,
+    a Lamb-Oseen vortex (Eq. lovorticity) and two notched disks in circulation mode; the body
+    data psi_b is the Lamb-Oseen streamfunction at the crossings (the velocity it implies is
+    the exact u_b); Gamma_k = h^2 sum over the nodes of R_k of the original (unmasked)
+    Lamb-Oseen vorticity, as in the paper (the vortex's circulation inside each body included).
+    The box ring is not data in free space (psi_box zeros)."""
+    c = FREE_SPACE_TWO_BODIES
+    g = Grid(0.0, 1.0, 0.0, 1.0, n, n)
+    X, Y = g.nodes()
+    bodies = [phi_notched_disk(X, Y, b["xc"], b["yc"], b["r_a"], b["r_b"], b["theta_a"], b["theta_b"])
+              for b in c["bodies"]]
+    phi = union(*bodies)
+    w, _, _ = lamb_oseen(X, Y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
+
+    def psi_b(x, y, body=None):
+        return psi_lamb_oseen(x, y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
+    regions = [region_around(g, b) for b in bodies]
+    gam = np.array([g.h * g.h * w[ly:ry + 1, lx:rx + 1].sum() for (lx, rx, ly, ry) in regions])
+    return Problem(grid=g, phi=phi, regions=regions, modes=[1, 1], omega=_mask_interior(g, phi, w),
+                   psi_box=np.zeros(4 * n), psi_b_fn=psi_b, psibar=np.zeros(2), gamma=gam, exact=None,
+                   name=f"lamb_oseen_two_bodies_{n}")
+
+
 ROTATED_CYLINDER = dict(R=0.5, omega=1.0, re=50.0, xc=0.013, yc=0.007, half=2.0, c_stab=0.5)
 
 

@@ -1,0 +1,111 @@
+"""Pins of the oracle's free-space (unbounded) rectangular solve and of the free-space IIM solve
+(Sec. 4.1 unbounded domains, Sec. 4.2 nabla_h^-2 with unbounded conditions, Sec. 4.3 test)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import lgf
+from oracle import poisson as op
+from paper_2109_13628_gb300 import inputs
+
+
+def test_lattice_green_function_closed_forms():
+    """G(0,0) = 0 (gauge); -L G = delta at the origin with the lattice symmetry gives
+    G(1,0) = -1/4; G(1,1) = -1/pi is the classical closed form of the potential kernel."""
+    T = lgf.lgf_table(4, 4)
+    assert T[0, 0] == 0.0
+    assert abs(T[0, 1] + 0.25) < 1e-14 and abs(T[1, 0] + 0.25) < 1e-14
+    assert abs(T[1, 1] + 1.0 / math.pi) < 1e-14
+    assert abs(lgf.lgf_quad(1, 1) + 1.0 / math.pi) < 1e-13
+
+
+def test_lattice_green_function_is_the_inverse_of_the_five_point_stencil():
+    """-(sum of the four neighbours - 4 centre) of G is 1 at the origin and 0 elsewhere."""
+    M = 40
+    T = lgf.lgf_table(M + 1, M + 1)
+    G = lambda m, n: T[abs(n), abs(m)]
+    for m in range(0, M):
+        for n in (0, 1, 3, 17, M - 1):
+            L = G(m + 1, n) + G(m - 1, n) + G(m, n + 1) + G(m, n - 1) - 4.0 * G(m, n)
+            assert abs(-L - (1.0 if m == n == 0 else 0.0)) < 1e-13, (m, n, L)
+
+
+def test_lattice_green_function_far_field_and_composite_rule():
+    """G = -(1/2 pi)(log r + euler_gamma + (3/2) log 2) + O(r^-2), and the composite rule
+    equals scipy's adaptive quadrature."""
+    T = lgf.lgf_table(64, 64)
+    for m, n in ((16, 0), (20, 11), (33, 33), (64, 7), (50, 50)):
+        r = math.hypot(m, n)
+        lead = -(math.log(r) + 0.5772156649015329 + 1.5 * math.log(2.0)) / (2 * math.pi)
+        assert abs(T[n, m] - lead) < 0.02 / r ** 2, (m, n, T[n, m] - lead)
+    for m, n in ((0, 1), (2, 3), (7, 0), (12, 5), (24, 19)):
+        assert abs(T[n, m] - lgf.lgf_quad(m, n)) < 1e-13
+
+
+def test_free_space_solve_satisfies_the_five_point_equation_everywhere():
+    """psi = poisson_free(f): -nabla_h^2 psi = f at every interior node, the box-adjacent ones
+    included (their ring neighbours are the solution's own ring values), and outside the box
+    too (f = 0 there): the convolution is evaluated at the nodes one layer out."""
+    rng = np.random.default_rng(3)
+    nx, ny, h = 32, 24, 0.1
+    f = rng.normal(size=(ny - 1, nx - 1))
+    psi = op.poisson_free(f, h)
+    assert np.abs(op.neg_laplacian_5pt(psi, h) - f).max() < 1e-11 * np.abs(f).max() * max(1, 1 / h ** 2) * h * h
+    # one more layer outside: the same convolution on a box grown by one node
+    big = np.zeros((ny + 1, nx + 1))
+    big[1:-1, 1:-1] = f
+    psi_big = op.poisson_free(big, h)
+    assert np.abs(psi_big[1:-1, 1:-1] - psi).max() < 1e-12 * np.abs(psi).max()
+    ring_eq = op.neg_laplacian_5pt(psi_big, h)
+    assert np.abs(ring_eq[[0, -1], :]).max() < 1e-10 and np.abs(ring_eq[:, [0, -1]]).max() < 1e-10
+
+
+def test_free_space_lamb_oseen_velocity_second_order():
+    """A Lamb-Oseen vortex in free space: velocity by centred differences of the free-space
+    psi converges to the exact velocity at second order."""
+    errs = []
+    for n in (32, 64, 128):
+        g = inputs.Grid(0.0, 1.0, 0.0, 1.0, n, n)
+        X, Y = g.nodes()
+        w, ux, uy = inputs.lamb_oseen(X, Y, 0.501, 0.501, 1.0, 0.0025)
+        psi = op.poisson_free(w[1:-1, 1:-1], g.h)
+        vx = (psi[2:, 1:-1] - psi[:-2, 1:-1]) / (2 * g.h)
+        vy = -(psi[1:-1, 2:] - psi[1:-1, :-2]) / (2 * g.h)
+        errs.append(max(np.abs(vx - ux[1:-1, 1:-1]).max(), np.abs(vy - uy[1:-1, 1:-1]).max()))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.8, (errs, rates)
+
+
+def _free_two_bodies(n):
+    P = inputs.lamb_oseen_two_bodies(n)
+    S = op.Setup(P)
+    gam = P.gamma
+    psi, pb, it, rel = op.solve_schur(S, gamma=gam, outer="unbounded", tol=1e-13)
+    return P, S, gam, psi, pb
+
+
+def test_free_space_iim_residual_and_circulation():
+    """The free-space IIM result satisfies the un-reduced equations (residual with the
+    solution's own ring) and the discrete circulation constraint of each body."""
+    P, S, gam, psi, pb = _free_two_bodies(64)
+    assert op.residual(S, psi, pb, gamma=gam, outer="unbounded") < 1e-11
+    for k, r in enumerate(P.regions):
+        assert abs(op.discrete_circulation(psi, r) - gam[k]) < 1e-11
+
+
+@pytest.mark.slow
+def test_free_space_iim_lamb_oseen_two_bodies_second_order():
+    """Sec. 4.3: a Lamb-Oseen vortex with two non-convex bodies in free space; the
+    reconstructed velocity converges to the exact one at second order in the max norm."""
+    c = inputs.FREE_SPACE_TWO_BODIES
+    errs = []
+    for n in (64, 128, 256):
+        P, S, gam, psi, pb = _free_two_bodies(n)
+        ux, uy = op.velocity(S, psi, pb)
+        X, Y = P.grid.nodes()
+        _, ex, ey = inputs.lamb_oseen(X, Y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
+        fl = (P.phi >= 0)[1:-1, 1:-1]
+        errs.append(max(np.abs(ux - ex[1:-1, 1:-1])[fl].max(), np.abs(uy - ey[1:-1, 1:-1])[fl].max()))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.7, (errs, rates)
