@@ -228,6 +228,28 @@ iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, cons
  * IIM_ERR_INVALID_ARG. */
 iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
 
+/* Exterior condition of the geometry's solves (Sec. 4.1: bounded and unbounded domains;
+ * Sec. 4.2: the rectangular solution operator nabla_h^-2 with those conditions).
+ *   outer 0 (default): Dirichlet box -- psi_box is the data on the box ring, gauge psibar_0 = 0.
+ *   outer 1: unbounded -- psi is the free-space solution on the infinite lattice: the solution
+ *     operator is the convolution psi(x) = h^2 sum_y G(x - y) f(y) with the lattice Green's
+ *     function G of the five-point Laplacian in the gauge G(0, 0) = 0 (the gauge the paper
+ *     leaves to "an arbitrary constant in the Green's function"), evaluated exactly (to
+ *     rounding) by James's method: one box solve of the source, the ring sum of G against the
+ *     box solve next to the box, and one box solve of the ring values.  psi_box is ignored: the
+ *     box ring of psi is part of the solution (iim_geometry_outer_ring); omega must vanish outside
+ *     the box.  psi is the perturbation field: for a free stream u_inf add u_inf x x (lattice-
+ *     harmonic, so give psi_b minus it at the control points).  guess mode 1 is refused.
+ * Changing it drops the geometry's preconditioner, circulation responses and solve graphs (they
+ * are rebuilt by the next solve).  The first switch to 1 for a grid size builds that size's G
+ * table (device, shared, kept until exit; synchronizes the device).
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA. */
+iim_status iim_geometry_set_outer(iim_geometry g, int outer);
+
+/* In free space (outer 1): psi on the box ring of the last solve (device, 2 (nx + ny) values in
+ * the ring layout).  Asynchronous.  Errors: IIM_ERR_INVALID_ARG (not in free space). */
+iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stream);
+
 /* How the column pass of the geometry's FP32 rectangular solves works: 0 (default) uses the
  * column DST pair with the eigenvalue division; 1 solves, for every x mode of the row transform,
  * the tridiagonal system that the 5-point operator becomes along the column (Thomas algorithm

@@ -112,6 +112,31 @@ def ring_of(nodes):
     return np.concatenate([nodes[0, :], nodes[-1, :], nodes[1:-1, 0], nodes[1:-1, -1]])
 
 
+def ring_residual(nodes):
+    """Free-space consistency of the box ring: for a field that is the free-space potential of
+    sources inside the box, the discrete Green's second identity on the interior nodes (the
+    five-point stencil summed by parts against G(x - .), which is harmonic there for x on the
+    ring) gives psi(x) = sum over the non-corner ring nodes z of G(x - z) psi(n(z)) -
+    G(x - n(z)) psi(z), n(z) the interior neighbour of z.  Returns psi(x) minus that sum on the
+    ring (ring layout): zero for free-space fields, exactly e(x) for a field e harmonic inside
+    the box."""
+    from . import lgf
+    ny, nx = nodes.shape[0] - 1, nodes.shape[1] - 1
+    G = lgf.lgf_table(nx + 1, ny + 1)
+    ring = [(i, 0) for i in range(nx + 1)] + [(i, ny) for i in range(nx + 1)] + \
+           [(0, j) for j in range(1, ny)] + [(nx, j) for j in range(1, ny)]
+    src = [((i, 0), (i, 1)) for i in range(1, nx)] + [((i, ny), (i, ny - 1)) for i in range(1, nx)] + \
+          [((0, j), (1, j)) for j in range(1, ny)] + [((nx, j), (nx - 1, j)) for j in range(1, ny)]
+    zi = np.array([z[0] for z, _ in src]); zj = np.array([z[1] for z, _ in src])
+    ai = np.array([a[0] for _, a in src]); aj = np.array([a[1] for _, a in src])
+    out = np.empty(len(ring))
+    for t, (xi, xj) in enumerate(ring):
+        s = (G[np.abs(xj - zj), np.abs(xi - zi)] * nodes[aj, ai]).sum() - \
+            (G[np.abs(xj - aj), np.abs(xi - ai)] * nodes[zj, zi]).sum()
+        out[t] = nodes[xj, xi] - s
+    return out
+
+
 # ----------------------------------------------------------------------------- setup
 class Setup:
     """Geometry, ghost operators and index maps of one problem (Sec. 2.2, App. A)."""
@@ -440,6 +465,10 @@ def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None, out
     f = np.where(fl, omega - neg_laplacian_5pt(ek, h), 0.0)
     rc = np.array([(gamma[k] - discrete_circulation(psi_nodes, P.regions[k])) / (h * h) for k in S.circ])
     fc = np.array([gamma[k] / (h * h) for k in S.circ])
+    if outer == "unbounded":
+        # the ring equations of the free-space system (ring_residual), in units of omega
+        rr = ring_residual(psi_nodes) / (h * h)
+        rc = np.concatenate([rc, rr])
     num = np.sqrt((r * r).sum() + (rc * rc).sum())
     den = np.sqrt((f * f).sum() + (fc * fc).sum())
     return num / den

@@ -70,6 +70,8 @@ SIGNATURES = [
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
     ("iim_geometry_set_lines", _i, [_vp, _i]),
     ("iim_geometry_set_column_solver", _i, [_vp, _i]),
+    ("iim_geometry_set_outer", _i, [_vp, _i]),
+    ("iim_geometry_outer_ring", _i, [_vp, _vp, _vp]),
     ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
     ("iim_net_num_params", ctypes.c_longlong, [_vp]),
     ("iim_net_get_params", _i, [_vp, _vp, ctypes.c_longlong]),
@@ -238,6 +240,21 @@ def iim_geometry_set_column_solver(g: "Geometry", mode: int):
     """Column pass of the FP32 rectangular solves: 1 tridiagonal solves per x mode (default),
     0 the column DST pair."""
     _check(load().iim_geometry_set_column_solver(g.handle, int(mode)), "iim_geometry_set_column_solver")
+
+
+def iim_geometry_set_outer(g: "Geometry", outer: int):
+    """Exterior condition: 0 Dirichlet box (default), 1 unbounded (free space)."""
+    _check(load().iim_geometry_set_outer(g.handle, int(outer)), "iim_geometry_set_outer")
+
+
+def iim_geometry_outer_ring(g: "Geometry", ring=None, stream=None):
+    """psi on the box ring of the last free-space solve (device tensor, ring layout)."""
+    n = 2 * (g.grid.nx + g.grid.ny)
+    if ring is None:
+        ring = torch.empty(n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+    _check(load().iim_geometry_outer_ring(g.handle, _ptr(ring, torch.float64, n, "ring"), _stream(stream)),
+           "iim_geometry_outer_ring")
+    return ring
 
 
 def _host_ptr(t, dtype=None, numel=None, name="tensor"):

@@ -140,6 +140,15 @@ struct iim_geometry_s {
     int *tri_off = nullptr, *tri_len = nullptr;
     float* tri_estar = nullptr;
     int col_solver = 0;
+    // free space (iim_geometry_set_outer): 0 = Dirichlet box, 1 = unbounded (freespace.cu); the
+    // lattice Green's function table (shared per grid size, not owned), psi on the box ring of
+    // the current solve, the ring sum of the last free-space application, and psi_1 next to the
+    // box (first / last interior row, then first / last interior column)
+    int outer = 0;
+    const double* lgf = nullptr;
+    double *fs_ring = nullptr, *fs_rho = nullptr, *fs_bnd = nullptr;
+    double* fs_rres = nullptr;   // ring rows of the last FP64 residual
+    double* cap_ring = nullptr;  // ring values of the unit-circulation responses (free space)
 
     // ---- solver workspace
     double* psi_ext = nullptr;   // NY*NX FP64: fluid values, ghosts at A-, 0 elsewhere
@@ -206,6 +215,16 @@ iim_status lockstep_enqueue(const std::vector<int>& idx, iim_geometry const* geo
 void lockstep_finish(void* handle, const std::vector<int>& idx, const iim_opts& o, bool host_driven,
                      std::vector<iim_status>& status, std::vector<iim_stats>& stats);
 void lockstep_forget(iim_geometry g);
+// free-space rectangular solve (freespace.cu)
+iim_status lgf_table(int nx, int ny, const double** out);
+template <typename T>
+iim_status launch_bnd_cols(int NX, int NY, int nx, const T* buf, double* vl, double* vr, const int* stop,
+                           cudaStream_t s);
+iim_status launch_ring_conv(int nx, int ny, const double* G, const double* bnd, const double* vl, const double* vr,
+                            double* rho, const int* stop, cudaStream_t s);
+iim_status launch_ring_add(int n, double a, const double* x, double* y, const int* stop, cudaStream_t s);
+iim_status launch_ring_residual(int nx, int ny, double h, const double* G, const double* psi, const double* ring,
+                                double* rres, double* res2, cudaStream_t s);
 // dense Schur-complement preconditioner (precond.cu)
 // [S | I] -> [I | S^-1] in place; scratch holds gj_scratch_floats(n) floats
 size_t gj_scratch_floats(int n);

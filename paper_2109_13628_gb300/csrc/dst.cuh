@@ -728,12 +728,13 @@ k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T*
                         g_tw);
 }
 
-enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2 };
+enum RowsInvMode { INV_STORE_T = 0, INV_STORE_F64 = 1, INV_ACCUM_FLUID = 2, INV_ACCUM_T = 3 };
 
 // Inverse row transforms of rows [row0, row0 + nrows) of a padded buffer.
 //   INV_STORE_T     outT (padded) = transform
 //   INV_STORE_F64   out64[r*old + ooff + i] = transform
 //   INV_ACCUM_FLUID out64 (padded) += transform at fluid nodes (class FLUID / PLUS) only
+//   INV_ACCUM_T     outT (padded) += transform
 // blockIdx.y selects one of several fields fstride elements apart (in and outT).
 template <typename T, int WARPS, int MODE, int FP>
 __device__ __forceinline__ void
@@ -763,6 +764,10 @@ rows_inv_body(int NX, int NY, int n, int logn, int row0, int nrows, const T* __r
         double* dst = out64 + (size_t)r * old + ooff;
 #pragma unroll 4
         for (int i = tid; i < NX; i += TN) dst[i] = (double)res[i + 1];
+    } else if (MODE == INV_ACCUM_T) {
+        T* dst = outT + (size_t)r * n + 1;
+#pragma unroll 4
+        for (int i = tid; i < NX; i += TN) dst[i] += res[i + 1];
     } else {
         const size_t base = (size_t)r * n;
 #pragma unroll 4

@@ -604,7 +604,7 @@ void free_geometry(iim_geometry g) {
                     g->gh_idx, g->gh_w, g->node_class, g->body_circ, g->d_regions, g->lam_x64, g->lam_y64,
                     g->lam_x32, g->lam_y32, g->tri_e, g->tri_off, g->tri_len, g->tri_estar, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
                     g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf,
-                    g->pc_aug, g->pc_S, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
+                    g->pc_aug, g->pc_S, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
     for (void* p : ptrs) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);

@@ -517,7 +517,7 @@ int lockstep_group_size() { return g_ls_group.load(); }
 // Problems that can join a lockstep group under these options.
 bool lockstep_eligible(iim_geometry g, const iim_opts& o) {
     const int ns = g->na + g->ncirc;
-    return g_ls_group.load() >= 2 && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 &&
+    return g_ls_group.load() >= 2 && g->host_solves > 0 && !g->solve_graph_failed && o.guess == 0 && !g->outer &&
            (o.precond == 1 || (o.precond == 3 && g->pc_S)) && ns > 0 && g->pc_ready &&
            g->V && g->krylov_m >= o.restart && (g->ncirc == 0 || g->cap_ready) &&
            sizeof(float) * 4 * (size_t)((ns + 3) & ~3) <= 200 * 1024;

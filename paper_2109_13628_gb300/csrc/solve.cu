@@ -744,7 +744,7 @@ struct Solver {
             IIM_LAUNCHED();
         }
         launch("residual_f64", 25.0 * (double)g->NX * g->NY, 8.0 * (double)g->NX * g->NY, k_residual<256>, kResBlocks,
-               256, 0, s, g->NX, g->NY, ih2, g->psi_ext, omega, g->node_class, ring, g->res, g->partial);
+               256, 0, s, g->NX, g->NY, ih2, g->psi_ext, omega, g->node_class, ring_now(), g->res, g->partial);
         IIM_LAUNCHED();
         double* small = g->small;
         const int* circ_ids_d = g->d_int + DI_CIRC;
@@ -758,6 +758,9 @@ struct Solver {
         launch("finish_residual", 0.0, 0.0, k_finish_residual<256>, 1, 256, 0, s, kResBlocks, g->partial, g->ncirc,
                circ_ids_d, gamma, ih2, small, small + SM_REG, g->bvec ? g->bvec + g->na : nullptr, small + SM_RES2);
         IIM_LAUNCHED();
+        if (g->outer)   // free space: the ring rows (freespace.cu), kept for the next recovery
+            IIM_CHECK(launch_ring_residual(g->nx, g->ny, g->h, g->lgf, g->psi_ext, g->fs_ring, g->fs_rres,
+                                           small + SM_RES2, s));
         return IIM_OK;
     }
 
@@ -774,11 +777,21 @@ struct Solver {
         T* tb = (T*)g->tbuf;
         T* pt = (T*)g->psiT;
         const long ld = ns;
-        if (g->na > 0) {
+        if (g->na > 0 && !g->outer) {
             IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, 0, 0, nullptr, 0.0, g->aff_row_ptr,
                                   g->aff_node, vj, 1.0, tb, stop, s));
             IIM_CHECK(cols<T>(p, g->ja0, g->ja1, g->jo0, g->jo1, tb, stop, s));
             IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, stop, s)));
+        } else if (g->na > 0) {
+            // free space: psi_1 with every row of the column pass kept for the boundary values,
+            // then the harmonic part with the ring data rho
+            IIM_CHECK(rows_fwd<T>(p, g->ja0, g->ja1 - g->ja0 + 1, nullptr, 0, 0, nullptr, 0.0, g->aff_row_ptr,
+                                  g->aff_node, vj, 1.0, tb, stop, s));
+            IIM_CHECK(cols<T>(p, g->ja0, g->ja1, 0, g->NY - 1, tb, stop, s));
+            IIM_CHECK(free_ring<T>(p, stop));
+            IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, stop, s)));
+            IIM_CHECK(free_harmonic<T>(p, g->jo0, g->jo1, stop));
+            IIM_CHECK((rows_inv<T, INV_ACCUM_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, stop, s)));
         }
         const int nga = (g->na + 3) / 4;   // gather blocks: 4 warps, one affected point each
         launch("gather", 0.0, 0.0, k_gather<T, 128>, nga + g->ncirc, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx,
@@ -786,6 +799,34 @@ struct Solver {
         IIM_LAUNCHED();
         return IIM_OK;
     }
+
+    // ---- free space (freespace.cu): with tbuf holding the column-processed transform of the
+    // first box solve psi_1 on every row, its values next to the box (two dot products per row
+    // for the first and last interior columns, the inverse transform of the first and last
+    // interior rows) and the ring sum rho = sum_y G(x - y) psi_1(neighbour of y) into fs_rho
+    template <typename T>
+    iim_status free_ring(const Plan<T>& p, const int* stop) {
+        const int NX = g->NX, NY = g->NY;
+        double* bnd = g->fs_bnd;
+        IIM_CHECK(launch_bnd_cols<T>(NX, NY, g->nx, (const T*)g->tbuf, bnd + 2 * NX, bnd + 2 * NX + NY, stop, s));
+        IIM_CHECK((rows_inv<T, INV_STORE_F64>(p, 0, 1, (const T*)g->tbuf, nullptr, bnd, 0, 0, nullptr, stop, s)));
+        IIM_CHECK((rows_inv<T, INV_STORE_F64>(p, NY - 1, 1, (const T*)g->tbuf, nullptr, bnd, 0, NX, nullptr, stop, s)));
+        return launch_ring_conv(g->nx, g->ny, g->lgf, bnd, bnd + 2 * NX, bnd + 2 * NX + NY, g->fs_rho, stop, s);
+    }
+
+    // ---- free space: the box solve of a zero source with box data fs_rho (the harmonic part),
+    // column pass written back on rows [out0, out1] of tbuf
+    template <typename T>
+    iim_status free_harmonic(const Plan<T>& p, int out0, int out1, const int* stop) {
+        const double ih2 = 1.0 / (g->h * g->h);
+        IIM_CHECK(rows_fwd<T>(p, 0, g->NY, nullptr, 0, 0, g->fs_rho, ih2, nullptr, nullptr, kNoVec, 0.0, (T*)g->tbuf,
+                              stop, s));
+        return cols<T>(p, 0, g->NY - 1, out0, out1, (T*)g->tbuf, stop, s);
+    }
+
+    // ring values the residual and the velocity use: the box data, or in free space the ring of
+    // the current solution
+    const double* ring_now() const { return g->outer ? g->fs_ring : ring; }
 
     // ---- dense Schur-complement preconditioner: columns S e_j from FP32 operator applications,
     // then [S | I] -> [I | S^-1] by blocked Gauss-Jordan with partial pivoting (FP32)
@@ -801,8 +842,9 @@ struct Solver {
         }
         IIM_TRY(cudaEventRecord(g->ev0, s));
         // gamma columns j < |A|, K at a time: unit row transforms, column pass, inverse rows of
-        // the gathered band, gather straight into the matrix (one launch each per batch)
-        {
+        // the gathered band, gather straight into the matrix (one launch each per batch); in free
+        // space every column takes one operator application (below)
+        if (!g->outer) {
             const long fstride = (long)g->nx * g->NY;
             const size_t fbytes = sizeof(float) * (size_t)fstride;
             const int K = (int)std::max<size_t>(1, std::min<size_t>(32, (size_t(256) << 20) / (2 * fbytes)));
@@ -837,10 +879,10 @@ struct Solver {
             if (bs != IIM_OK) return bs;
             IIM_TRY(se);
         }
-        // psibar columns: one operator application each
+        // psibar columns (and in free space all columns): one operator application each
         launch("set_tmpj", 0.0, 0.0, k_set_int, 1, 1, 0, s, di() + DI_TMPJ, 0);
         const int eb = (n + 255) / 256;
-        for (int j = g->na; j < n; ++j) {
+        for (int j = g->outer ? 0 : g->na; j < n; ++j) {
             launch("pc_unit", 0.0, 0.0, k_unit_vector, eb, 256, 0, s, n, j, g->V);
             IIM_CHECK(apply_at<float>(DI_TMPJ, nullptr));
             launch("pc_column", 0.0, 0.0, k_store_column, eb, 256, 0, s, n, j, (const double*)(g->V + ld), g->pc_aug);
@@ -974,8 +1016,13 @@ struct Solver {
         T* pt = (T*)g->psiT;
         if (g->na == 0) return IIM_OK;
         IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, g->nx, 1, nullptr, 0.0, nullptr, nullptr, kNoVec, 0.0, tb, nullptr, s));
-        IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->jo0, g->jo1, tb, nullptr, s));
+        IIM_CHECK(cols<T>(p, 0, g->NY - 1, g->outer ? 0 : g->jo0, g->outer ? g->NY - 1 : g->jo1, tb, nullptr, s));
+        if (g->outer) IIM_CHECK(free_ring<T>(p, nullptr));
         IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
+        if (g->outer) {
+            IIM_CHECK(free_harmonic<T>(p, g->jo0, g->jo1, nullptr));
+            IIM_CHECK((rows_inv<T, INV_ACCUM_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
+        }
         const int nga = (g->na + 3) / 4;   // gather blocks: 4 warps, one affected point each
         launch("gather", 0.0, 0.0, k_gather<T, 128>, nga, 128, 0, s, g->na, nga, g->gop_ptr, g->gop_idx, g->gop_w, pt,
                g->cp_body, g->body_circ, g->aff_body, kNoVec, 0, g->bvec, nullptr, 0L, nullptr);
@@ -992,7 +1039,18 @@ struct Solver {
         IIM_CHECK(rows_fwd<T>(p, 0, g->NY, g->res, g->nx, 1, nullptr, 0.0, g->aff_row_ptr, g->aff_node, xg, -1.0, tb,
                               nullptr, s));
         IIM_CHECK(cols<T>(p, 0, g->NY - 1, 0, g->NY - 1, tb, nullptr, s));
+        if (g->outer) IIM_CHECK(free_ring<T>(p, nullptr));
         IIM_CHECK((rows_inv<T, INV_ACCUM_FLUID>(p, 0, g->NY, tb, nullptr, g->psi_ext, 0, 0, g->node_class, nullptr, s)));
+        if (g->outer) {
+            // the harmonic part carries rho minus the ring rows of the last residual: the field
+            // harmonic inside the box that removes the ring error (the interior rows do not see
+            // it); the ring moves by the same values
+            const int nr = 2 * (g->nx + g->ny);
+            IIM_CHECK(launch_ring_add(nr, -1.0, g->fs_rres, g->fs_rho, nullptr, s));
+            IIM_CHECK(free_harmonic<T>(p, 0, g->NY - 1, nullptr));
+            IIM_CHECK((rows_inv<T, INV_ACCUM_FLUID>(p, 0, g->NY, tb, nullptr, g->psi_ext, 0, 0, g->node_class, nullptr, s)));
+            IIM_CHECK(launch_ring_add(nr, 1.0, g->fs_rho, g->fs_ring, nullptr, s));
+        }
         if (g->ncirc > 0) {
             launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, g->ncirc, di() + DI_CIRC, x + g->na, psibar);
             IIM_LAUNCHED();
@@ -1190,6 +1248,7 @@ struct Solver {
         piece(top_seg, [&]() -> iim_status {
             launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, nullptr,
                    g->node_class, g->psi_ext);
+            if (g->outer) IIM_TRY(cudaMemsetAsync(g->fs_ring, 0, sizeof(double) * 2 * (g->nx + g->ny), s));
             if (g->nb > 0)
                 launch("init_psibar", 0.0, 0.0, k_init_psibar, 1, 64, 0, s, g->nb, g->body_circ, psibar, 0, psibar);
             IIM_CHECK(residual_launch());
@@ -1267,6 +1326,11 @@ struct Solver {
                        g->small + SM_CAPC, g->small + SM_CAPP);
                 launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((npad + 255) / 256), 256, 0, s, npad, nc,
                        (const double*)g->cap_psi, (const double*)(g->small + SM_CAPC), g->psi_ext);
+                if (g->outer) {   // the responses' ring values move the free-space ring
+                    const long nr = 2L * (g->nx + g->ny);
+                    launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((nr + 255) / 256), 256, 0, s, nr, nc,
+                           (const double*)g->cap_ring, (const double*)(g->small + SM_CAPC), g->fs_ring);
+                }
                 launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, nc, (const int*)(g->d_int + DI_CIRC),
                        (const double*)(g->small + SM_CAPP), psibar);
                 IIM_CHECK(residual_launch());
@@ -1274,7 +1338,7 @@ struct Solver {
             }
             const long n = (long)g->NX * g->NY;
             launch("velocity_f64", 0.0, 0.0, k_velocity, (unsigned)((n + 255) / 256), 256, 0, s, g->NX, g->NY,
-                   0.5 / g->h, g->psi_ext, g->node_class, ring, psi_out, ux_out, uy_out);
+                   0.5 / g->h, g->psi_ext, g->node_class, ring_now(), psi_out, ux_out, uy_out);
             IIM_LAUNCHED();
             return IIM_OK;
         });
@@ -1409,7 +1473,14 @@ static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaSt
         }
         st = poisson_solve(g, w0, pb0, nullptr, gam, pbar, out, nullptr, nullptr, nullptr, &o, nullptr, s, false);
         if (st != IIM_OK) break;
-        if (cudaMemcpyAsync(g->cap_psi + (size_t)l * npad, g->psi_ext, sizeof(double) * npad, cudaMemcpyDeviceToDevice,
+        const size_t nring = 2 * (size_t)(g->nx + g->ny);
+        if (g->outer && !g->cap_ring && cudaMalloc(&g->cap_ring, sizeof(double) * (size_t)nc * nring) != cudaSuccess) {
+            st = IIM_ERR_CUDA;
+            break;
+        }
+        if ((g->outer && cudaMemcpyAsync(g->cap_ring + (size_t)l * nring, g->fs_ring, sizeof(double) * nring,
+                                         cudaMemcpyDeviceToDevice, s) != cudaSuccess) ||
+            cudaMemcpyAsync(g->cap_psi + (size_t)l * npad, g->psi_ext, sizeof(double) * npad, cudaMemcpyDeviceToDevice,
                             s) != cudaSuccess ||
             cudaMemcpyAsync(hp.data(), pbar, sizeof(double) * nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaMemcpyAsync(circ.data(), g->small + SM_CIRC, sizeof(double) * nc, cudaMemcpyDeviceToHost, s) !=
@@ -1544,6 +1615,8 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     if (opts.restart < 1 || opts.restart > 64 || !(opts.rtol > 0.0) || opts.max_iter < 1 || opts.max_refine < 1)
         return IIM_ERR_INVALID_ARG;
     if ((opts.guess == 1 || opts.guess == 2) && !psi_guess) return IIM_ERR_INVALID_ARG;
+    if (g->outer && opts.guess == 1) return IIM_ERR_INVALID_ARG;   // a free-space iterate has no given ring
+    if (g->outer) psi_box = nullptr;                                  // the ring is part of the solution
     if (opts.guess < 0 || opts.guess > 2 || opts.precond < 0 || opts.precond > 3) return IIM_ERR_INVALID_ARG;
     IIM_CHECK(ensure_twiddles());
     IIM_CHECK(ensure_krylov(g, opts.restart));
@@ -1620,6 +1693,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     int fallback = 0;
     launch("init_psi", 0.0, 0.0, k_init_psi, (unsigned)((npad + 255) / 256), 256, 0, s, g->NX, g->NY, nullptr,
            g->node_class, g->psi_ext);
+    if (g->outer) IIM_TRY(cudaMemsetAsync(g->fs_ring, 0, sizeof(double) * 2 * (g->nx + g->ny), s));
     if (g->nb > 0) launch("init_psibar", 0.0, 0.0, k_init_psibar, 1, 64, 0, s, g->nb, g->body_circ, psibar, 0, psibar);
     IIM_LAUNCHED();
     IIM_CHECK(S.residual(&res2, &cerr));
@@ -1691,6 +1765,11 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
         IIM_TRY(cudaMemcpyAsync(g->small + SM_CAPP, dpb.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, s));
         launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((npad + 255) / 256), 256, 0, s, npad, nc,
                (const double*)g->cap_psi, (const double*)(g->small + SM_CAPC), g->psi_ext);
+        if (g->outer) {   // the responses' ring values move the free-space ring
+            const long nr = 2L * (g->nx + g->ny);
+            launch("cap_update", 0.0, 0.0, k_cap_update, (unsigned)((nr + 255) / 256), 256, 0, s, nr, nc,
+                   (const double*)g->cap_ring, (const double*)(g->small + SM_CAPC), g->fs_ring);
+        }
         launch("add_psibar", 0.0, 0.0, k_add_psibar, 1, 64, 0, s, nc, (const int*)(g->d_int + DI_CIRC),
                (const double*)(g->small + SM_CAPP), psibar);
         IIM_LAUNCHED();
@@ -1699,7 +1778,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
     }
     const long n = (long)g->NX * g->NY;
     launch("velocity_f64", (double)n * (9.0 + 8.0 + (ux_out ? 8.0 : 0.0) + (uy_out ? 8.0 : 0.0)), 0.0, k_velocity,
-           (unsigned)((n + 255) / 256), 256, 0, s, g->NX, g->NY, 0.5 / g->h, g->psi_ext, g->node_class, psi_box, psi_out,
+           (unsigned)((n + 255) / 256), 256, 0, s, g->NX, g->NY, 0.5 / g->h, g->psi_ext, g->node_class, S.ring_now(), psi_out,
            ux_out, uy_out);
     IIM_LAUNCHED();
     IIM_TRY(cudaEventRecord(g->ev1, s));
@@ -1732,6 +1811,52 @@ extern "C" iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_lin
             if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
         }
     }
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_geometry_set_outer(iim_geometry g, int outer) {
+    if (!g || (outer != 0 && outer != 1)) return IIM_ERR_INVALID_ARG;
+    if (g->outer == outer) return IIM_OK;
+    int cur = 0;
+    IIM_TRY(cudaGetDevice(&cur));
+    IIM_TRY(cudaSetDevice(g->device));
+    iim_status st = IIM_OK;
+    if (outer == 1) {
+        const size_t nring = 2 * (size_t)(g->nx + g->ny), nbnd = 2 * (size_t)(g->NX + g->NY);
+        if (!g->lgf) st = lgf_table(g->nx, g->ny, &g->lgf);
+        if (st == IIM_OK && !g->fs_ring) {
+            if (cudaMalloc(&g->fs_ring, sizeof(double) * nring) != cudaSuccess ||
+                cudaMalloc(&g->fs_rho, sizeof(double) * nring) != cudaSuccess ||
+                cudaMalloc(&g->fs_bnd, sizeof(double) * nbnd) != cudaSuccess ||
+                cudaMalloc(&g->fs_rres, sizeof(double) * nring) != cudaSuccess ||
+                cudaMemset(g->fs_rres, 0, sizeof(double) * nring) != cudaSuccess ||
+                cudaMemset(g->fs_ring, 0, sizeof(double) * nring) != cudaSuccess) {
+                record_cuda_error(cudaGetLastError(), "free-space buffers", __FILE__, __LINE__);
+                st = IIM_ERR_CUDA;
+            }
+        }
+    }
+    if (st == IIM_OK) {
+        g->outer = outer;
+        // everything built from the rectangular operator is rebuilt on the next solve
+        g->pc_ready = 0;
+        g->cap_ready = 0;
+        g->host_solves = 0;
+        drop_solve_graph(g);
+        lockstep_forget(g);
+        for (void** gp : {&g->graph64, &g->graph32}) {
+            IterGraph* G = (IterGraph*)*gp;
+            if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
+        }
+    }
+    cudaSetDevice(cur);
+    return st;
+}
+
+extern "C" iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stream) {
+    if (!g || !ring || !g->outer || !g->fs_ring) return IIM_ERR_INVALID_ARG;
+    IIM_TRY(cudaMemcpyAsync(ring, g->fs_ring, sizeof(double) * 2 * (g->nx + g->ny), cudaMemcpyDeviceToDevice,
+                            (cudaStream_t)stream));
     return IIM_OK;
 }
 

@@ -1,0 +1,133 @@
+"""Free-space (unbounded) exterior condition on the GPU (Sec. 4.1, Sec. 4.2's solution operator
+with unbounded conditions, Sec. 4.3's free-space test), against the oracle's direct lattice
+Green's function convolution (oracle/lgf.py, oracle.poisson.poisson_free / solve_schur with
+outer="unbounded").  The library evaluates the same operator by James's method (box solves and
+a ring sum), so agreement checks that reformulation too.
+
+Tolerances as everywhere: relative L-infinity 1e-10 in FP64 mode, 1e-8 in mixed mode."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2109_13628_gb300 as iim
+from oracle import poisson as op
+from paper_2109_13628_gb300 import inputs
+from tests import gpu_util as gu
+
+pytestmark = pytest.mark.gpu
+
+TOL = {iim.IIM_FP64: 1e-10, iim.IIM_MIXED: 1e-8}
+
+
+def rel(a, b, m=None):
+    if m is None:
+        return np.abs(a - b).max() / np.abs(b).max()
+    return np.abs(a - b)[m].max() / np.abs(b)[m].max()
+
+
+@pytest.mark.parametrize("nx,ny", [(64, 64), (128, 64), (256, 256)])
+@pytest.mark.parametrize("prec", [iim.IIM_FP64, iim.IIM_MIXED])
+def test_free_space_solve_without_bodies_matches_oracle(nx, ny, prec):
+    """No bodies: the solve is the free-space operator itself; interior psi and the box ring
+    equal the oracle's convolution."""
+    h = 1.0 / 64
+    g = inputs.Grid(0.0, nx * h, 0.0, ny * h, nx, ny)
+    rng = np.random.default_rng(nx + 7 * ny)
+    f = rng.normal(size=(ny - 1, nx - 1))
+    ref = op.poisson_free(f, h)
+    P = inputs.Problem(grid=g, phi=np.ones((ny + 1, nx + 1)), regions=[], modes=[], omega=f,
+                       psi_box=np.zeros(2 * (nx + ny)), psi_b_fn=lambda x, y, b: np.zeros_like(x),
+                       psibar=np.zeros(0), gamma=None, exact=None)
+    geo = gu.setup(P)
+    iim.iim_geometry_set_outer(geo, 1)
+    out = gu.solve(P, geo, prec=prec, rtol=1e-12)
+    assert rel(out["psi"], ref[1:-1, 1:-1]) < TOL[prec], (out["stats"], rel(out["psi"], ref[1:-1, 1:-1]))
+    ring = iim.iim_geometry_outer_ring(geo).cpu().numpy()
+    assert np.abs(ring - op.ring_of(ref)).max() < TOL[prec] * np.abs(ref).max()
+    geo.close()
+
+
+@pytest.fixture(scope="module")
+def two_bodies_64():
+    P = inputs.lamb_oseen_two_bodies(64)
+    S = op.Setup(P)
+    psi, pb, it, relr = op.solve_schur(S, gamma=P.gamma, outer="unbounded", tol=1e-14)
+    ux, uy = op.velocity(S, psi, pb)
+    return P, psi, pb, ux, uy
+
+
+@pytest.mark.parametrize("prec,precond", [(iim.IIM_FP64, 0), (iim.IIM_MIXED, 0), (iim.IIM_MIXED, 3),
+                                          (iim.IIM_FP64, 1)])
+def test_free_space_iim_two_bodies_matches_oracle(two_bodies_64, prec, precond):
+    """Sec. 4.3 case (two notched bodies, Lamb-Oseen vortex, circulation mode) in free space:
+    psi, psibar, the box ring and the velocity equal the oracle's Schur solve; the graph-driven
+    second solve equals the first bit for bit."""
+    P, ref, pb_ref, ux_ref, uy_ref = two_bodies_64
+    geo = gu.setup(P)
+    iim.iim_geometry_set_outer(geo, 1)
+    if precond:
+        iim.iim_build_preconditioner(geo)
+    opts = iim.default_opts(prec=prec, rtol=1e-12, precond=precond, max_iter=3000)
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    outs = []
+    for rep in range(2):
+        out = gu.solve_opts(P, geo, gamma=P.gamma, opts=opts, velocity=True)
+        assert rel(out["psi"], ref[1:-1, 1:-1], fl) < TOL[prec], (rep, out["stats"])
+        assert np.abs(out["psibar"] - pb_ref).max() < TOL[prec] * np.abs(ref).max()
+        assert rel(out["ux"], ux_ref, fl) < TOL[prec] and rel(out["uy"], uy_ref, fl) < TOL[prec]
+        ring = iim.iim_geometry_outer_ring(geo).cpu().numpy()
+        assert np.abs(ring - op.ring_of(ref)).max() < TOL[prec] * np.abs(ref).max()
+        assert out["stats"]["circ_err_max"] < 1e-12
+        outs.append(out)
+    assert np.array_equal(outs[0]["psi"], outs[1]["psi"]) or precond == 0
+    geo.close()
+
+
+def test_free_space_iim_second_order_on_the_gpu():
+    """Sec. 4.3 on the GPU up to 512^2: the reconstructed velocity converges to the exact
+    Lamb-Oseen velocity at second order (mixed precision, dense inner operator)."""
+    c = inputs.FREE_SPACE_TWO_BODIES
+    errs, errs2 = [], []
+    for n in (64, 128, 256, 512):
+        P = inputs.lamb_oseen_two_bodies(n)
+        geo = gu.setup(P)
+        iim.iim_geometry_set_outer(geo, 1)
+        iim.iim_build_preconditioner(geo)
+        out = gu.solve_opts(P, geo, gamma=P.gamma, velocity=True,
+                            opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11, precond=3))
+        X, Y = P.grid.nodes()
+        _, ex, ey = inputs.lamb_oseen(X, Y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
+        fl = (P.phi >= 0)[1:-1, 1:-1]
+        e = np.hypot(out["ux"] - ex[1:-1, 1:-1], out["uy"] - ey[1:-1, 1:-1])[fl]
+        errs.append(e.max())
+        errs2.append(math.sqrt((e * e).sum()) * P.grid.h)
+        geo.close()
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(3)]
+    rates2 = [math.log2(errs2[k] / errs2[k + 1]) for k in range(3)]
+    # max norm: second order over 64..256 (the cut-cell scatter of the maximum moves it at 512)
+    assert min(rates[:2]) > 1.8 and rates[2] > 1.5, (errs, rates)
+    assert min(rates2) > 1.85, (errs2, rates2)
+
+
+def test_outer_switch_back_and_errors():
+    """Switching back to the Dirichlet box gives the Dirichlet result again; free-space-only
+    calls and guess mode 1 are refused in the wrong mode."""
+    P = inputs.bicubic_bodies(64, seed=4, circulation=True)
+    gam = op.gamma_from_regions(P)
+    geo = gu.setup(P)
+    a = gu.solve(P, geo, gamma=gam, rtol=1e-12)
+    with pytest.raises(iim.IIMError):
+        iim.iim_geometry_outer_ring(geo)
+    iim.iim_geometry_set_outer(geo, 1)
+    free = gu.solve(P, geo, gamma=gam, rtol=1e-12)
+    assert not np.allclose(free["psi"], a["psi"])
+    with pytest.raises(iim.IIMError):
+        gu.solve(P, geo, gamma=gam, rtol=1e-12, guess=np.zeros_like(P.omega))
+    iim.iim_geometry_set_outer(geo, 0)
+    b = gu.solve(P, geo, gamma=gam, rtol=1e-12)
+    assert np.abs(a["psi"] - b["psi"]).max() < 1e-12 * np.abs(a["psi"]).max()
+    with pytest.raises(iim.IIMError):
+        iim.iim_geometry_set_outer(geo, 2)
+    geo.close()

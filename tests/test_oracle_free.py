@@ -109,3 +109,18 @@ def test_free_space_iim_lamb_oseen_two_bodies_second_order():
         errs.append(max(np.abs(ux - ex[1:-1, 1:-1])[fl].max(), np.abs(uy - ey[1:-1, 1:-1])[fl].max()))
     rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
     assert min(rates) > 1.7, (errs, rates)
+
+
+def test_ring_residual_identity():
+    """The ring equations of the free-space system: zero for the free-space potential of
+    interior sources, and exactly e on the ring for a field e harmonic inside the box (the box
+    solve of a zero source with ring data e) -- what makes a ring error visible to the FP64
+    residual."""
+    rng = np.random.default_rng(1)
+    nx, ny, h = 24, 16, 0.1
+    psi = op.poisson_free(rng.normal(size=(ny - 1, nx - 1)), h)
+    assert np.abs(op.ring_residual(psi)).max() < 1e-13 * np.abs(psi).max()
+    e = rng.normal(size=2 * (nx + ny))
+    H = op.ring_to_nodes(nx, ny, e)
+    H[1:-1, 1:-1] = op.poisson_box(np.zeros((ny - 1, nx - 1)), h, e)
+    assert np.abs(op.ring_residual(psi + H) - e).max() < 1e-12
