@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--no-c3", action="store_true", help="skip the 2048^2 multi-body leg")
     ap.add_argument("--tiles", type=int, default=0, help="column-pass tile width (0: tuned on the batch)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT box-solve cross-check")
+    ap.add_argument("--no-free", action="store_true", help="skip the free-space (unbounded) leg")
     return ap.parse_args()
 
 
@@ -439,6 +440,54 @@ def calibrate_inner(solve_at, candidates, reps=2):
         if ok and (best is None or ms < best[1]):
             best = (inner, ms)
     return (best[0] if best else candidates[-1]), rows
+
+
+def free_space_c43(iim, inputs, dev, n=1024, steps=3):
+    """Free-space velocity reconstruction (Sec. 4.3's case: Lamb-Oseen vortex, two notched bodies
+    in circulation mode, unbounded exterior) at n^2: mixed solve with the dense inner operator
+    and the plain FP64 iteration, and the velocity error against the exact Lamb-Oseen field."""
+    import numpy as np
+    import torch
+    c = inputs.FREE_SPACE_TWO_BODIES
+    P = inputs.lamb_oseen_two_bodies(n)
+    g = P.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    geo = iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions, P.modes)
+    t0 = time.perf_counter()
+    iim.iim_geometry_set_outer(geo, 1)
+    t_lgf = time.perf_counter() - t0
+    cp = iim.iim_geometry_control_points(geo)
+    pb = T(P.psi_b_fn(cp["x"].cpu().numpy(), cp["y"].cpu().numpy(), None))
+    om, gam = T(P.omega.ravel()), T(P.gamma)
+    psi = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
+    ux, uy = torch.empty_like(psi), torch.empty_like(psi)
+    pbar = torch.zeros(2, dtype=torch.float64, device=dev)
+    t0 = time.perf_counter()
+    pc_ms = iim.iim_build_preconditioner(geo)
+    t_pc = time.perf_counter() - t0
+    X, Y = g.nodes()
+    _, ex, ey = inputs.lamb_oseen(X, Y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
+    fl = (P.phi >= 0)[1:-1, 1:-1]
+    out = {"config": f"Sec. 4.3 case in free space (unbounded exterior), {n}^2 cells, |A| = {geo.n_affected}",
+           "lgf_table_and_buffers_s": t_lgf, "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms}
+    for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed_dense_op", iim.IIM_MIXED, 3)):
+        opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc, max_iter=4000)
+        iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, ux, uy, opts=opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            st = iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, ux, uy, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        e = np.hypot(ux.cpu().numpy().reshape(P.omega.shape) - ex[1:-1, 1:-1],
+                     uy.cpu().numpy().reshape(P.omega.shape) - ey[1:-1, 1:-1])[fl]
+        out[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "krylov_iters": st["iters"],
+                     "refinements": st["refinements"], "rel_res": st["rel_res"], "circ_err_max": st["circ_err_max"],
+                     "velocity_err_max": float(e.max()), "velocity_err_l2": float(np.sqrt((e * e).sum()) * g.h)}
+    out["speedup_mixed_dense_op_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed_dense_op"]["ms_per_solve"]
+    geo.close()
+    return out
 
 
 def cufft_dst1(x, dim):
@@ -876,6 +925,7 @@ def main():
     rk3 = None if args.no_rk3 else rk3_c2(iim, inputs, dev)
     c3 = None if args.no_c3 else c3_multibody(iim, inputs, dev)
     cufft = None if args.no_cufft else cufft_crosscheck(iim, dev)
+    free = None if args.no_free else free_space_c43(iim, inputs, dev)
     c5 = None
     if not args.no_learned:
         c5 = learned_c5(iim, dev, opts_for)
@@ -935,6 +985,7 @@ def main():
         "rk3_c2": rk3,
         "multibody_c3": c3,
         "cufft_crosscheck": cufft,
+        "free_space_c43": free,
         "cpu_baseline": cpu,
     }
     if rank == 0:
