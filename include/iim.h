@@ -233,8 +233,8 @@ iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
  *   outer 0 (default): Dirichlet box -- psi_box is the data on the box ring, gauge psibar_0 = 0.
  *   outer 1: unbounded -- psi is the free-space solution on the infinite lattice: the solution
  *     operator is the convolution psi(x) = h^2 sum_y G(x - y) f(y) with the lattice Green's
- *     function G of the five-point Laplacian in the gauge G(0, 0) = 0 (the gauge the paper
- *     leaves to "an arbitrary constant in the Green's function"), evaluated exactly (to
+ *     function G of the five-point Laplacian in the gauge G(0, 0) = 0 (the paper leaves the
+ *     gauge to the free constant of the Green's function), evaluated exactly (to
  *     rounding) by James's method: one box solve of the source, the ring sum of G against the
  *     box solve next to the box, and one box solve of the ring values.  psi_box is ignored: the
  *     box ring of psi is part of the solution (iim_geometry_outer_ring); omega must vanish outside
