@@ -303,6 +303,28 @@ iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* 
 iim_status iim_box_poisson_noalloc(const iim_grid* grid, const double* f, const double* psi_box, double* u,
                                    int prec, iim_stream stream);
 
+/* Control-volume force and moment on a stationary body (App. C: the momentum formulation of
+ * Noca, Eq. Fm with its tensor gamma, and the moment formulation of Eqs. Mm1 and Mm2), density 1.
+ * The control volume is the node box `box` (global node indices lx..rx, ly..ry; 2 <= lx < rx <=
+ * nx - 2, likewise in y) minus the body inside it; the box edges and their neighbours must be
+ * plain fluid (else IIM_ERR_BAD_REGION).  Surface integrals use the trapezoidal rule on the box's
+ * node lines and centred differences.
+ *   psi, ux, uy  interior arrays of a solve (psi 0 in the solid, as iim_poisson_solve writes it)
+ *   omega        interior array of the vorticity
+ *   psi_wall     psi on the body's wall (psi_b + psibar_k; constant on a stationary no-slip wall)
+ *   nu           viscosity;  xbar  host, the moment centre
+ *   out          host, 9 values: A_x, A_y, B_x, B_y, C_x, C_y, P, Q, R with
+ *                A = int_V u, B = oint x cross (n cross u), C = oint n . gamma,
+ *                P = int_V x cross u, Q = oint |x|^2/2 (n cross u), R = oint lambda(n),
+ *                so that F = -dA/dt - dB/dt + C and M = -dP/dt + dQ/dt + R (x from xbar); the
+ *                time derivatives come from a series of calls (the volume integrals are
+ *                evaluated through psi: A = (oint psi n_y, -oint psi n_x),
+ *                P = -oint psi (x.n) + 2 int_box psi~, psi~ = psi_wall in the body).
+ * Synchronizes `stream`.  Errors: IIM_ERR_INVALID_ARG, IIM_ERR_BAD_REGION, IIM_ERR_CUDA. */
+iim_status iim_cv_terms(iim_geometry g, const double* psi, const double* ux, const double* uy, const double* omega,
+                        double psi_wall, const iim_region* box, double nu, const double xbar[2], double* out,
+                        iim_stream stream);
+
 /* Conservative vorticity transport right-hand side with the IIM boundary treatment (Sec. 3:
  * Eqs. upwind, 2dshuconserve, Sec. 3.2) and the Kelvin ODE (Sec. 5.1, Eq. discreteKelvinChoice)
  * for a given velocity; omega_b from the velocity by the local vorticity boundary condition of

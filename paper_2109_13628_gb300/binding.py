@@ -7,6 +7,8 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
+
 import torch
 
 from . import build as _build
@@ -72,6 +74,7 @@ SIGNATURES = [
     ("iim_geometry_set_column_solver", _i, [_vp, _i]),
     ("iim_geometry_set_outer", _i, [_vp, _i]),
     ("iim_geometry_outer_ring", _i, [_vp, _vp, _vp]),
+    ("iim_cv_terms", _i, [_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(iim_region), _d, ctypes.POINTER(_d), _vp, _vp]),
     ("iim_net_create", _i, [_i, _i, _i, _ip, ctypes.c_ulonglong, ctypes.POINTER(_vp)]),
     ("iim_net_num_params", ctypes.c_longlong, [_vp]),
     ("iim_net_get_params", _i, [_vp, _vp, ctypes.c_longlong]),
@@ -255,6 +258,20 @@ def iim_geometry_outer_ring(g: "Geometry", ring=None, stream=None):
     _check(load().iim_geometry_outer_ring(g.handle, _ptr(ring, torch.float64, n, "ring"), _stream(stream)),
            "iim_geometry_outer_ring")
     return ring
+
+
+def iim_cv_terms(g: "Geometry", psi, ux, uy, omega, psi_wall, box, nu, xbar, stream=None):
+    """Control-volume force / moment quantities (A_x, A_y, B_x, B_y, C_x, C_y, P, Q, R) on the node
+    box `box` = (lx, rx, ly, ry) around one stationary body (see iim.h)."""
+    nxy = (g.grid.nx - 1) * (g.grid.ny - 1)
+    out = (_d * 9)()
+    xb = (_d * 2)(*xbar)
+    reg = iim_region(*[int(v) for v in box])
+    _check(load().iim_cv_terms(g.handle, _ptr(psi, torch.float64, nxy, "psi"), _ptr(ux, torch.float64, nxy, "ux"),
+                               _ptr(uy, torch.float64, nxy, "uy"), _ptr(omega, torch.float64, nxy, "omega"),
+                               float(psi_wall), ctypes.byref(reg), float(nu), xb, out, _stream(stream)),
+           "iim_cv_terms")
+    return np.array(out[:])
 
 
 def _host_ptr(t, dtype=None, numel=None, name="tensor"):
