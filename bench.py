@@ -15,6 +15,7 @@ host cores on the same workload, metric and unit.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -40,10 +41,16 @@ NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722200, "l2_bytes_per_launc
                                          "flushed by ncu before each launch"}}
 
 
+L2_BYTES = 126 * 1024 * 1024
+# kernel names of the three passes of iim_time_box_passes, per column pass (0 DSTs, 1 scans)
+PASS_NAMES = {0: ("dst_rows_fwd_f32", "dst_cols_f32", "dst_rows_inv_f32"),
+              1: ("dst_rows_fwd_f32", "tri_cols_f32", "dst_rows_inv_f32")}
+
+
 def kernel_source_hash():
     """Hash of the files holding the transform kernels and their launch configuration."""
     h = hashlib.sha256()
-    for f in ("dst.cuh", "iim_ops.cuh", "solve.cu", "lockstep.cu"):
+    for f in ("dst.cuh", "tri.cuh", "iim_ops.cuh", "solve.cu", "lockstep.cu"):
         with open(os.path.join(ROOT, "paper_2109_13628_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -74,6 +81,8 @@ def parse():
     ap.add_argument("--tiles", type=int, default=0, help="column-pass tile width (0: tuned on the batch)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT box-solve cross-check")
     ap.add_argument("--no-free", action="store_true", help="skip the free-space (unbounded) leg")
+    ap.add_argument("--col-solver", type=int, default=-1,
+                    help="column pass of the chosen form: 1 tridiagonal scans, 0 column DSTs, -1 tuned on the batch")
     return ap.parse_args()
 
 
@@ -470,8 +479,12 @@ def free_space_c43(iim, inputs, dev, n=1024, steps=3):
     fl = (P.phi >= 0)[1:-1, 1:-1]
     out = {"config": f"Sec. 4.3 case in free space (unbounded exterior), {n}^2 cells, |A| = {geo.n_affected}",
            "lgf_table_and_buffers_s": t_lgf, "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms}
-    for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed_dense_op", iim.IIM_MIXED, 3)):
-        opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc, max_iter=4000)
+    # column pass per leg: FP64 on the tridiagonal scans (its fastest); mixed on both passes (in
+    # free space their FP32 rounding changes the number of refinements)
+    for name, prec, pc, col in (("fp64", iim.IIM_FP64, 0, 1), ("mixed_dense_op", iim.IIM_MIXED, 3, 0),
+                                ("mixed_dense_op_tri", iim.IIM_MIXED, 3, 1)):
+        iim.iim_geometry_set_column_solver(geo, col)
+        opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc, max_iter=4000, max_refine=30)
         iim.iim_poisson_solve(geo, om, pb, None, gam, pbar, psi, ux, uy, opts=opts)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -482,10 +495,12 @@ def free_space_c43(iim, inputs, dev, n=1024, steps=3):
         torch.cuda.synchronize()
         e = np.hypot(ux.cpu().numpy().reshape(P.omega.shape) - ex[1:-1, 1:-1],
                      uy.cpu().numpy().reshape(P.omega.shape) - ey[1:-1, 1:-1])[fl]
-        out[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "krylov_iters": st["iters"],
+        out[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "column_pass": ["column DSTs", "tridiagonal scans"][col],
+                     "krylov_iters": st["iters"],
                      "refinements": st["refinements"], "rel_res": st["rel_res"], "circ_err_max": st["circ_err_max"],
                      "velocity_err_max": float(e.max()), "velocity_err_l2": float(np.sqrt((e * e).sum()) * g.h)}
-    out["speedup_mixed_dense_op_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed_dense_op"]["ms_per_solve"]
+    out["speedup_mixed_dense_op_vs_fp64"] = out["fp64"]["ms_per_solve"] / min(
+        out["mixed_dense_op"]["ms_per_solve"], out["mixed_dense_op_tri"]["ms_per_solve"])
     geo.close()
     return out
 
@@ -670,6 +685,9 @@ def main():
     t_setup = time.perf_counter()
     geos = [iim.iim_setup_geometry(grid, T(P.phi), P.regions, P.modes) for _ in range(B)]
     t_setup = (time.perf_counter() - t_setup) / B
+    col_mode, col_tuned = (args.col_solver if args.col_solver >= 0 else 1), None
+    for gg in geos:
+        iim.iim_geometry_set_column_solver(gg, col_mode)
     cp = iim.iim_geometry_control_points(geos[0])
     psi_b_h = P.psi_b_fn(cp["x"].cpu().numpy(), cp["y"].cpu().numpy(), None)
     omega, psi_b, ring = T(P.omega.ravel()), T(psi_b_h), T(P.psi_box)
@@ -756,6 +774,8 @@ def main():
     if B > 1:
         # the per-problem form's tile width and streams, then the lockstep group size
         prev = iim.iim_set_lockstep(0)
+        if args.col_solver < 0:
+            col_mode, col_tuned = autotune.tune_column_solver(geos, lambda: solve_batch(B), rebuild_precond=bool(precond))
         if not args.tiles:
             tile_w, tiles_tuned = autotune.tune_tiles_batch(geos, lambda: solve_batch(B))
         n_streams, tuned = autotune.tune_streams(solve_batch, tuple(c for c in (1, 2, 4, 8, 12, 16) if c <= B))
@@ -776,6 +796,8 @@ def main():
     single = args.steps / (sum(ms1) * 1e-3)
     # ---- plain FP64 iteration (the comparator: unpreconditioned, one problem at a time), at its
     # loosest Krylov tolerance that still ends at the same FP64 residual target (no over-solve)
+    # (FP64 legs on their fastest column pass, the tridiagonal scans)
+    iim.iim_geometry_set_column_solver(geo, 1)
     inner64, calib64 = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 0), PLAIN_INNER)
     k64 = max(3, args.steps // 5)
     ms64, stats64 = timed(lambda: solve(iim.IIM_FP64, inner64, 0), k64, 2)
@@ -790,6 +812,7 @@ def main():
                    "inner_rtol": inner64p, "krylov_iters": statistics.mean(s["iters"] for s in statsp),
                    "refinements": statistics.mean(s["refinements"] for s in statsp),
                    "final_rel_res": max(s["rel_res"] for s in statsp), "calibration": calib64p}
+    iim.iim_geometry_set_column_solver(geo, col_mode)
     # ---- lockstep off: one whole-solve graph per problem on the tuned streams (same B solves)
     per_problem = None
     if B > 1:
@@ -823,23 +846,39 @@ def main():
     peaks, src = measured_peaks()
     mem = [r for r in kern if r["bytes"] > 0]
     dom = mem[0] if mem else None
+    # ---- the transform passes of this grid timed alone (iim_time_box_passes: each pass launched
+    # back to back inside a CUDA graph, CUDA events around the graph): one field (L2-resident),
+    # the B fields of a step in one launch, and enough fields that the working set exceeds L2
+    big = max(B, int(math.ceil(3 * L2_BYTES / (4.0 * NXY))))
+    passes = {}
+    for label, nb in (("single", 1), (f"batch_{B}", B), (f"batch_{big}_beyond_l2", big)):
+        r = iim.iim_time_box_passes(geo, iim.IIM_MIXED, nb, 10)
+        passes[label] = {k: {"us_per_launch": u, "alg_bytes_per_launch": b, "gbs": b / u / 1e3,
+                             "frac_of_hbm": b / u / 1e3 / peaks["hbm_gbs"]}
+                         for k, u, b in zip(PASS_NAMES[col_mode], r["us"], r["bytes"])}
     roof = None
     if dom:
         per_launch_s = dom["ms"] * 1e-3 / dom["launches"]
-        achieved = dom["bytes"] / dom["launches"] / per_launch_s / 1e9
+        ev_achieved = dom["bytes"] / dom["launches"] / per_launch_s / 1e9
         tr = NCU_TRAFFIC.get(dom["name"])
         valid = bool(tr) and tr.get("source_hash") == kernel_source_hash() and tr.get("tile_width") == tile_w
         traffic = tr["bytes_per_launch"] if valid else None
         l2_traffic = tr.get("l2_bytes_per_launch") if valid else None
+        alone = passes[f"batch_{big}_beyond_l2"].get(dom["name"])
+        achieved = alone["gbs"] if alone else ev_achieved
         roof = {"bound": "hbm", "kernel": dom["name"], "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "l2_traffic": l2_traffic, "peak_source": src,
-                "alg_bytes_per_launch": dom["bytes"] / dom["launches"], "avg_launch_us": per_launch_s * 1e6,
+                "alg_bytes_per_launch": alone["alg_bytes_per_launch"] if alone else dom["bytes"] / dom["launches"],
+                "avg_launch_us": alone["us_per_launch"] if alone else per_launch_s * 1e6,
                 "share_of_kernel_time": dom["ms"] / tot_k if tot_k else None,
-                "timing": (f"batched step (lockstep groups of {group}, one launch per step for a group): the same "
-                           "kernels run host-driven under the per-kernel profiler, CUDA events around each launch on "
-                           "its stream; bytes = the algorithmic bytes of all problems of the launch" if group > 1 else
-                           "timed form = one whole-solve graph per problem: the same solve's kernels one problem at "
-                           "a time under the per-kernel profiler, CUDA events around each launch on its stream")}
+                "event_profile": {"achieved": ev_achieved, "avg_launch_us": per_launch_s * 1e6,
+                                  "alg_bytes_per_launch": dom["bytes"] / dom["launches"]},
+                "timing": ((f"the dominant kernel by share of the timed form's per-kernel profile, timed alone on "
+                            f"this grid: {big} fields per launch (working set beyond L2), launches back to back in a "
+                            "CUDA graph, CUDA events around the graph launch on its stream" if alone else
+                            "per-kernel profile of the timed form (CUDA events around each launch on its stream)") +
+                           "; event_profile: the same kernel in the timed form's per-kernel profile, host-driven "
+                           "launches (includes host gaps between launches)")}
     # ---- end to end through the C ABI with host buffers (B problems per step)
     e2e = None
     if not args.no_e2e:
@@ -898,6 +937,7 @@ def main():
                                                  n_streams=nst)
 
         prev_group = iim.iim_set_lockstep(0)
+        c4_col, c4_col_tuned = autotune.tune_column_solver(cgeos, lambda: c4_run(8), rebuild_precond=bool(precond))
         c4_streams, c4_tuned = autotune.tune_streams(c4_run, (4, 8, 16, 24))
         iim.iim_set_lockstep(prev_group)
         c4_group, c4_group_tuned = autotune.tune_lockstep(lambda: c4_run(c4_streams), (1, 4, 8, 24), reps=1)
@@ -907,6 +947,7 @@ def main():
               "unknown_solves_per_s": unknowns * len(cms) / (sum(cms) * 1e-3), "ms_per_batch": sum(cms) / len(cms),
               "streams": c4_streams, "lockstep_group": c4_group, "lockstep_tuning_ms": c4_group_tuned,
               "tiles_by_size": {f"{k[0]}x{k[1]}": v for k, v in tiles.items()},
+              "column_pass": ["column DSTs", "tridiagonal scans"][c4_col], "column_pass_tuning_ms": c4_col_tuned,
               "precond_setup_s": c4_pc, "max_rel_res": max(s["rel_res"] for o in couts for s in o),
               "krylov_iters_mean": statistics.mean(s["iters"] for o in couts for s in o)}
         # the same batch with FP64 transforms throughout (same preconditioner and streams)
@@ -914,6 +955,8 @@ def main():
             return iim.iim_poisson_solve_batched(cgeos, om, pbv, None, gm, pbar, cout,
                                                  opts=opts_for(iim.IIM_FP64, pc=precond), n_streams=c4_streams)
 
+        for gg in cgeos:   # FP64 on its fastest column pass, the tridiagonal scans
+            iim.iim_geometry_set_column_solver(gg, 1)
         c4_run64()
         fms, fouts = timed(lambda: c4_run64()[1], 2, 0)
         c4["fp64"] = {"solves_per_s": len(kept) * len(fms) / (sum(fms) * 1e-3), "ms_per_batch": sum(fms) / len(fms),
@@ -965,10 +1008,13 @@ def main():
                    "refinements": statistics.mean(s["refinements"] for s in stats),
                    "final_rel_res_max": max(s["rel_res"] for s in stats), "setup_s": t_setup,
                    "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms, "streams_tuning_ms": tuned,
+                   "column_pass": "tridiagonal scans" if col_mode == 1 else "column DSTs",
+                   "column_pass_tuning_ms": col_tuned,
                    "tile_width": tile_w, "tile_tuning_ms": tiles_tuned, "lockstep_group": group,
                    "lockstep_tuning_ms": group_tuned,
                    "n_control": geo.n_control, "n_affected": geo.n_affected},
         "roofline": roof,
+        "transform_passes": passes,
         "kernels": [{"name": r["name"], "launches_per_step": r["launches"] / kprof, "ms_per_step": r["ms"] / kprof,
                      "share": r["ms"] / tot_k if tot_k else None} for r in kern[:12]],
         "kernels_single_problem": [{"name": r["name"], "launches_per_solve": r["launches"] / kprof,

@@ -250,14 +250,13 @@ iim_status iim_geometry_set_outer(iim_geometry g, int outer);
  * the ring layout).  Asynchronous.  Errors: IIM_ERR_INVALID_ARG (not in free space). */
 iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stream);
 
-/* How the column pass of the geometry's FP32 rectangular solves works: 0 (default) uses the
- * column DST pair with the eigenvalue division; 1 solves, for every x mode of the row transform,
- * the tridiagonal system that the 5-point operator becomes along the column (Thomas algorithm
- * with tabulated elimination factors; O(ny) work per column, one thread per column).  Both
- * compute the same discrete inverse (the FFT / tridiagonal form of the rectangular solve of
- * Sec. 4.2) to FP32 rounding; the tridiagonal form's rounding is larger and its sequential
- * recurrence slower on the GPU, so it is an alternative, not the default.  FP64 transforms
- * always use the DST pair; grids with nx < 32 too.  Errors: IIM_ERR_INVALID_ARG. */
+/* How the column pass of the geometry's rectangular solves (FP32 and FP64) works.  After the
+ * row transforms, every x mode turns the 5-point operator along a column into a tridiagonal
+ * system (the FFT / tridiagonal form of the Sec. 4.2 rectangular solve).  1 (default) solves
+ * these systems directly: the two Thomas recurrences as segmented scans, with the elimination
+ * factors tabulated through their complements 1 - e_j; O(ny) work per column.  0 uses the
+ * column DST pair with the eigenvalue division.  Both compute the same discrete inverse to
+ * rounding.  Errors: IIM_ERR_INVALID_ARG (mode not 0 or 1). */
 iim_status iim_geometry_set_column_solver(iim_geometry g, int mode);
 
 /* Threads per transformed line for 1024-point lines: 32 (default: one warp, fewest
@@ -284,6 +283,19 @@ iim_status iim_build_preconditioner(iim_geometry g, float* setup_ms, iim_stream 
  * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA.  Asynchronous on `stream`. */
 iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* psi_box,
                            double* u, int prec, double* work, iim_stream stream);
+
+/* Pass timing of the rectangular solve (no counterpart in the paper: a measurement hook for
+ * benchmarks, not part of any solve).  Runs, in precision `prec` (IIM_FP64 or IIM_MIXED = FP32
+ * transforms) and with the geometry's current column pass and tile width, the three passes of
+ * the Sec. 4.2 rectangular solve on `batch` synthetic fields of g's grid: forward row transforms
+ * of a dense FP64 field (one launch per field), the column pass and the inverse row transforms
+ * (one launch over all fields); each pass is launched `reps` times back to back inside a CUDA
+ * graph of its own, timed with CUDA events around one launch of that graph.  Outputs (host): us[3] = average device time per
+ * launch in microseconds, bytes[3] = algorithmic bytes one launch moves (inputs read once,
+ * outputs written once).  The call allocates and frees its own device scratch (3 fields), uses
+ * a stream of its own and returns after the measurement.  Errors: IIM_ERR_INVALID_ARG (null
+ * pointers, batch or reps < 1, bad prec), IIM_ERR_CUDA. */
+iim_status iim_time_box_passes(iim_geometry g, int prec, int batch, int reps, double* us, double* bytes);
 
 /* Allocation-free variant of iim_box_poisson.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- code running while a CUDA graph is

@@ -1,5 +1,5 @@
-"""Autotuner of the batched solver: the column-pass tile width per grid-size bucket, the number
-of concurrent worker streams and the lockstep group size, each chosen by timing real solves of
+"""Autotuner of the batched solver: the column pass and its tile width per grid-size bucket, the
+number of concurrent worker streams and the lockstep group size, each chosen by timing real solves of
 the caller's own problems on the device (CUDA events), keeping the fastest."""
 from __future__ import annotations
 
@@ -55,6 +55,30 @@ def tune_tiles_batch(geoms, run_batch, widths=(4, 8), reps=2):
     best = min(times, key=times.get)
     for g in geoms:
         B.iim_geometry_set_tiles(g, best)
+    return best, times
+
+
+def tune_column_solver(geoms, run_batch, modes=(1, 0), reps=2, rebuild_precond=False):
+    """One column pass for all geometries (iim_geometry_set_column_solver: 1 tridiagonal scans,
+    0 column DSTs), chosen by timing the whole batch `run_batch()`: the passes differ in speed and
+    in FP32 rounding, and the rounding can change how many refinements a solve takes.  With
+    `rebuild_precond` each candidate also rebuilds the dense Schur preconditioner with its own
+    column pass (the preconditioner's FP32 rounding matters too).  Applies the choice and returns
+    (mode, {mode: ms})."""
+    times = {}
+
+    def apply(m):
+        for g in geoms:
+            B.iim_geometry_set_column_solver(g, m)
+            if rebuild_precond:
+                B.iim_build_preconditioner(g)
+
+    for m in modes:
+        apply(m)
+        run_batch()
+        times[m] = _time(run_batch, reps)
+    best = min(times, key=times.get)
+    apply(best)
     return best, times
 
 

@@ -72,6 +72,7 @@ SIGNATURES = [
     ("iim_geometry_set_tiles", _i, [_vp, _i]),
     ("iim_geometry_set_lines", _i, [_vp, _i]),
     ("iim_geometry_set_column_solver", _i, [_vp, _i]),
+    ("iim_time_box_passes", _i, [_vp, _i, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
     ("iim_geometry_set_outer", _i, [_vp, _i]),
     ("iim_geometry_outer_ring", _i, [_vp, _vp, _vp]),
     ("iim_cv_terms", _i, [_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(iim_region), _d, ctypes.POINTER(_d), _vp, _vp]),
@@ -243,6 +244,14 @@ def iim_geometry_set_column_solver(g: "Geometry", mode: int):
     """Column pass of the FP32 rectangular solves: 1 tridiagonal solves per x mode (default),
     0 the column DST pair."""
     _check(load().iim_geometry_set_column_solver(g.handle, int(mode)), "iim_geometry_set_column_solver")
+
+
+def iim_time_box_passes(g: "Geometry", prec: int, batch: int = 1, reps: int = 20):
+    """Device time per launch (us) and algorithmic bytes per launch of the three passes of the
+    rectangular solve (forward rows, columns, inverse rows) on `batch` fields (see iim.h)."""
+    us, by = (_d * 3)(), (_d * 3)()
+    _check(load().iim_time_box_passes(g.handle, int(prec), int(batch), int(reps), us, by), "iim_time_box_passes")
+    return {"us": list(us), "bytes": list(by)}
 
 
 def iim_geometry_set_outer(g: "Geometry", outer: int):

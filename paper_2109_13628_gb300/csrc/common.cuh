@@ -134,12 +134,16 @@ struct iim_geometry_s {
     // eigenvalues of the 1D three-point operators, x modes (NX) and y modes (NY)
     double *lam_x64 = nullptr, *lam_y64 = nullptr;
     float *lam_x32 = nullptr, *lam_y32 = nullptr;
-    // factor table of the tridiagonal column pass (FP32 transforms; tri.cuh): factors, per-column
-    // offsets, lengths and limits; col_solver 1 = tridiagonal column pass, 0 = column transforms
-    float* tri_e = nullptr;
-    int *tri_off = nullptr, *tri_len = nullptr;
-    float* tri_estar = nullptr;
-    int col_solver = 0;
+    // factors of the tridiagonal column pass (tri.cuh), FP32 and FP64: complements of the
+    // Thomas factors (FP64 table, row-major over rows, and its row offsets), per-column table
+    // limits and limits 1 - e*; col_solver 1 = tridiagonal column pass, 0 = column transforms
+    float* sc32_delta = nullptr;
+    double* sc64_delta = nullptr;
+    int *sc32_rowoff = nullptr, *sc32_lim = nullptr, *sc64_rowoff = nullptr, *sc64_lim = nullptr;
+    float* sc32_dstar = nullptr;
+    double* sc64_dstar = nullptr;
+    float4* sc32_par = nullptr;   // FP32: per-column parameters of the closed form (tri.cuh)
+    int col_solver = 1;
     // free space (iim_geometry_set_outer): 0 = Dirichlet box, 1 = unbounded (freespace.cu); the
     // lattice Green's function table (shared per grid size, not owned), psi on the box ring of
     // the current solve, the ring sum of the last free-space application, and psi_1 next to the

@@ -396,6 +396,66 @@ static iim_status dalloc(T** p, size_t n) {
     return IIM_OK;
 }
 
+// Factors of the tridiagonal column pass (tri.cuh) in one precision.  For x mode p = c + 1:
+// eps = 4 sin^2(pi p / (2 nx)), theta = acosh(1 + eps / 2), and the Thomas factors in closed form
+// e_j = sinh((j + 1) theta) / sinh((j + 2) theta), so with e* = exp(-theta), q = exp(-2 theta)
+//   delta_j = 1 - e_j = delta* + e* q^(j+1) (1 - q) / (1 - q^(j+2)),   delta* = -expm1(-theta),
+// every term accurate to a few units in the last place in FP64 (no recurrence, no
+// cancellation).  Column c uses delta* from row lim[c] on, lim[c] the first row whose
+// correction term is within tol of delta* (relative), made non-increasing in c.  FP64: the rows
+// before lim as a table, row-major over rows (the tabulated columns of a row are a prefix);
+// FP32: per column (delta*, log2 q, q, e* (1 - q)) for the kernel's own evaluation of the form.
+static double scan_corr(double theta, int j) {
+    return std::exp(-theta) * std::exp(-2.0 * (j + 1) * theta) * std::expm1(-2.0 * theta) /
+           std::expm1(-2.0 * (j + 2) * theta);
+}
+
+template <typename T>
+static iim_status scan_tables(int nx, int NX, int NY, double tol, T** delta, int** rowoff, float4** par, int** lim,
+                              T** dstar) {
+    std::vector<int> L(NX);
+    std::vector<double> th(NX);
+    std::vector<T> ds(NX);
+    std::vector<float4> pr(NX);
+    for (int c = 0; c < NX; ++c) {
+        const double sn = std::sin(M_PI * (c + 1) / (2.0 * nx));
+        const double eps = 4.0 * sn * sn;
+        const double theta = std::log1p(0.5 * eps + std::sqrt(eps + 0.25 * eps * eps));
+        const double dstar_c = -std::expm1(-theta);
+        th[c] = theta;
+        ds[c] = (T)dstar_c;
+        pr[c] = make_float4((float)dstar_c, (float)(-2.0 * theta / M_LN2), (float)std::exp(-2.0 * theta),
+                            (float)(-std::exp(-theta) * std::expm1(-2.0 * theta)));
+        int j = 0;
+        while (j < NY && scan_corr(theta, j) > tol * dstar_c) ++j;
+        L[c] = j;
+    }
+    for (int c = NX - 2; c >= 0; --c) L[c] = std::max(L[c], L[c + 1]);
+    IIM_CHECK(dalloc(lim, NX));
+    IIM_CHECK(dalloc(dstar, NX));
+    IIM_TRY(cudaMemcpy(*lim, L.data(), NX * sizeof(int), cudaMemcpyHostToDevice));
+    IIM_TRY(cudaMemcpy(*dstar, ds.data(), NX * sizeof(T), cudaMemcpyHostToDevice));
+    if (sizeof(T) == 4) {
+        IIM_CHECK(dalloc(par, NX));
+        IIM_TRY(cudaMemcpy(*par, pr.data(), NX * sizeof(float4), cudaMemcpyHostToDevice));
+        return IIM_OK;
+    }
+    std::vector<int> off(NY + 1, 0);
+    std::vector<T> tab;
+    int C = NX;
+    for (int j = 0; j < NY; ++j) {
+        while (C > 0 && L[C - 1] <= j) --C;
+        off[j] = (int)tab.size();
+        for (int c = 0; c < C; ++c) tab.push_back((T)(-std::expm1(-th[c]) + scan_corr(th[c], j)));
+    }
+    off[NY] = (int)tab.size();
+    IIM_CHECK(dalloc(delta, tab.size()));
+    IIM_CHECK(dalloc(rowoff, NY + 1));
+    if (!tab.empty()) IIM_TRY(cudaMemcpy(*delta, tab.data(), tab.size() * sizeof(T), cudaMemcpyHostToDevice));
+    IIM_TRY(cudaMemcpy(*rowoff, off.data(), (NY + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    return IIM_OK;
+}
+
 void free_geometry(iim_geometry g);
 
 }  // namespace iim
@@ -545,31 +605,11 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
         SETUP_CUDA(cudaMemcpy(g->lam_y64, ly.data(), NY * sizeof(double), cudaMemcpyHostToDevice));
         SETUP_CUDA(cudaMemcpy(g->lam_x32, fx.data(), NX * sizeof(float), cudaMemcpyHostToDevice));
         SETUP_CUDA(cudaMemcpy(g->lam_y32, fy.data(), NY * sizeof(float), cudaMemcpyHostToDevice));
-        // Thomas factors of the per-mode tridiagonal column systems (tri.cuh): for x mode c + 1,
-        // b = 2 + h^2 lam_x = 4 - 2 cos(pi (c + 1) / nx), e_0 = 1/b, e_j = 1/(b - e_{j-1}), kept
-        // (FP64 recurrence, stored in FP32) until they reach e* = (b - sqrt(b^2 - 4)) / 2 to within
-        // 2.5e-8 relative; later rows use e*
-        std::vector<float> te, tes(NX);
-        std::vector<int> toff(NX), tlen(NX);
-        for (int c = 0; c < NX; ++c) {
-            const double b = 4.0 - 2.0 * std::cos(M_PI * (c + 1) / nx);
-            const double es = 0.5 * (b - std::sqrt(b * b - 4.0));
-            toff[c] = (int)te.size();
-            double e = 1.0 / b;
-            for (int j = 0; j < NY; ++j) {
-                if (j > 0) e = 1.0 / (b - e);
-                if (std::fabs(e - es) <= 2.5e-8 * es) break;
-                te.push_back((float)e);
-            }
-            tlen[c] = (int)te.size() - toff[c];
-            tes[c] = (float)es;
-        }
-        SETUP_TRY(dalloc(&g->tri_e, te.size()));
-        SETUP_TRY(dalloc(&g->tri_off, NX)); SETUP_TRY(dalloc(&g->tri_len, NX)); SETUP_TRY(dalloc(&g->tri_estar, NX));
-        if (!te.empty()) SETUP_CUDA(cudaMemcpy(g->tri_e, te.data(), te.size() * sizeof(float), cudaMemcpyHostToDevice));
-        SETUP_CUDA(cudaMemcpy(g->tri_off, toff.data(), NX * sizeof(int), cudaMemcpyHostToDevice));
-        SETUP_CUDA(cudaMemcpy(g->tri_len, tlen.data(), NX * sizeof(int), cudaMemcpyHostToDevice));
-        SETUP_CUDA(cudaMemcpy(g->tri_estar, tes.data(), NX * sizeof(float), cudaMemcpyHostToDevice));
+        SETUP_TRY(scan_tables<float>(nx, NX, NY, 0x1p-26, &g->sc32_delta, &g->sc32_rowoff, &g->sc32_par,
+                                     &g->sc32_lim, &g->sc32_dstar));
+        float4* unused_par = nullptr;
+        SETUP_TRY(scan_tables<double>(nx, NX, NY, 0x1p-53, &g->sc64_delta, &g->sc64_rowoff, &unused_par,
+                                      &g->sc64_lim, &g->sc64_dstar));
     }
     // solver workspace
     SETUP_TRY(dalloc(&g->psi_ext, npad));
@@ -581,6 +621,12 @@ extern "C" iim_status iim_setup_geometry(const iim_grid* grid, const double* phi
     SETUP_TRY(dalloc(&g->partial, 4096 * 72));
     SETUP_TRY(dalloc(&g->small, 4096));
     SETUP_TRY(dalloc(&g->d_int, 256));   // [32, 96): circulation body ids
+    // scalars, counters and flags start at zero (no solve path may read stale memory)
+    SETUP_CUDA(cudaMemsetAsync(g->partial, 0, 4096 * 72 * sizeof(double), s));
+    SETUP_CUDA(cudaMemsetAsync(g->small, 0, 4096 * sizeof(double), s));
+    SETUP_CUDA(cudaMemsetAsync(g->d_int, 0, 256 * sizeof(int), s));
+    SETUP_CUDA(cudaMemsetAsync(g->tbuf, 0, npad * sizeof(double), s));
+    SETUP_CUDA(cudaMemsetAsync(g->res, 0, npad * sizeof(double), s));
     SETUP_CUDA(cudaMallocHost(&g->h_pinned, 64 * sizeof(double)));
     SETUP_CUDA(cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking));
     SETUP_CUDA(cudaEventCreate(&g->ev0));
@@ -602,7 +648,8 @@ void free_geometry(iim_geometry g) {
     void* ptrs[] = {g->cp_x, g->cp_y, g->cp_t, g->cp_body, g->cp_axis, g->cp_ei, g->cp_ej, g->aff_node, g->aff_body,
                     g->aff_row_ptr, g->aff_solid, g->gop_ptr, g->gop_idx, g->gop_w, g->minus_node, g->gh_ptr,
                     g->gh_idx, g->gh_w, g->node_class, g->body_circ, g->d_regions, g->lam_x64, g->lam_y64,
-                    g->lam_x32, g->lam_y32, g->tri_e, g->tri_off, g->tri_len, g->tri_estar, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
+                    g->lam_x32, g->lam_y32, g->sc32_delta, g->sc64_delta, g->sc32_rowoff, g->sc32_lim, g->sc64_rowoff, g->sc64_lim,
+                    g->sc32_dstar, g->sc64_dstar, g->sc32_par, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
                     g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf,
                     g->pc_aug, g->pc_S, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
     for (void* p : ptrs) cudaFree(p);

@@ -25,7 +25,7 @@ struct Plan {
     T norm;
     int cols_c = 4;   // columns per block of the column pass (tile width)
     int wide = 0;     // 64 threads per 1024-point line instead of one warp
-    TriTab tri{};     // FP32 only: factor table of the tridiagonal column pass (e == nullptr: transforms)
+    ScanTab<T> scan{};   // factors of the tridiagonal column pass (lim == nullptr: column transforms)
 };
 
 // Algorithmic flops of one DST-I of n - 1 points through an n/2-point complex FFT
@@ -54,6 +54,21 @@ template <typename T>
 inline int tile_width(int requested) {
     if (sizeof(T) == 4) return requested >= 8 ? 8 : 4;
     return requested <= 2 ? 2 : 4;
+}
+
+// Streaming multiprocessors of the current device (queried once per device).
+inline int sm_count() {
+    static std::mutex m;
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(m);
+    if (dev >= 0 && dev < 64 && cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+        cached[dev] = v;
+    }
+    return dev >= 0 && dev < 64 ? cached[dev] : 1;
 }
 
 // Raises a kernel's dynamic shared memory limit once per (device, kernel, size).  A failed

@@ -55,7 +55,8 @@ struct LsProb {
     void* psiT;
     const float* pc_inv;   // right half of [S | S^-1], leading dimension 2 ns
     const float* pc_S;     // S itself (ns x ns), the inner operator of iim_opts.precond == 3
-    TriTab tri;            // factor table of the tridiagonal column pass (FP32)
+    ScanTab<float> s32;    // factors of the tridiagonal column pass (used when the group's tri is set)
+    ScanTab<double> s64;
     int* di;
     const double *cap_psi, *cap_dev;
     const double *omega, *psi_b, *ring, *gamma;
@@ -118,13 +119,20 @@ kb_cols(const LsProb* __restrict__ P, int mode, int gate, T norm, const cpx<T>* 
                         (const T*)p.lam_x, (const T*)p.lam_y, norm, tw);
 }
 
-__global__ void __launch_bounds__(32) kb_cols_tri(const LsProb* __restrict__ P, int mode, int gate) {
+template <typename T>
+__device__ __forceinline__ const ScanTab<T>& ls_scan(const LsProb& p) {
+    if constexpr (sizeof(T) == 4) return p.s32;
+    else return p.s64;
+}
+
+template <typename T, int CW, int NT>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 2 : 4) kb_cols_scan(const LsProb* __restrict__ P, int mode, int gate) {
     const LsProb& p = P[blockIdx.z];
     if (ls_off(p, gate) || (mode != M_RECOVER && p.na == 0)) return;
     int in0 = 0, in1 = p.NY - 1, out0 = p.jo0, out1 = p.jo1;
     if (mode == M_APPLY_PCZ || mode == M_APPLY_VTMP) { in0 = p.ja0; in1 = p.ja1; }
     if (mode == M_RECOVER) { out0 = 0; out1 = p.NY - 1; }
-    cols_tri_body(p.NX, p.NY, p.nx, in0, in1, out0, out1, (float*)p.tbuf, p.tri);
+    cols_scan_body<T, CW, NT>(p.NX, p.NY, p.nx, in0, in1, out0, out1, (T*)p.tbuf, ls_scan<T>(p));
 }
 
 template <typename T, int WARPS, int MODE, int FP>
@@ -541,8 +549,11 @@ static void fill_prob(LsProb& q, iim_geometry g, int prec, const double* omega, 
     q.xsol = g->xsol; q.bvec = g->bvec; q.pc_z = g->pc_z; q.tbuf = g->tbuf; q.psiT = g->psiT;
     q.pc_inv = g->pc_aug + (q.ns);
     q.pc_S = g->pc_S;
-    if (prec != IIM_FP64 && g->col_solver == 1 && g->nx >= 32 && g->tri_e)
-        q.tri = TriTab{g->tri_e, g->tri_off, g->tri_len, g->tri_estar, (float)(g->h * g->h * (2.0 / g->nx))};
+    if (g->col_solver == 1) {
+        q.s32 = ScanTab<float>{g->sc32_delta, g->sc32_rowoff, g->sc32_par, g->sc32_lim, g->sc32_dstar,
+                               (float)(g->h * g->h * (2.0 / g->nx))};
+        q.s64 = ScanTab<double>{g->sc64_delta, g->sc64_rowoff, nullptr, g->sc64_lim, g->sc64_dstar, g->h * g->h * (2.0 / g->nx)};
+    }
     q.di = g->d_int;
     q.cap_psi = g->cap_psi; q.cap_dev = g->cap_dev;
     q.omega = omega; q.psi_b = psi_b; q.ring = ring; q.gamma = gamma; q.psibar = psibar; q.psi_out = psi_out;
@@ -619,17 +630,27 @@ struct LsEmit {
 
     template <typename T>
     iim_status cols(int mode, int gate) {
-        if (sizeof(T) == 4 && G->tri) {
+        if (G->tri) {
             double bytes = 0.0;
             for (iim_geometry g : G->geos) {
                 int in = g->NY, out = g->jo1 - g->jo0 + 1;
                 if (mode == M_APPLY_PCZ || mode == M_APPLY_VTMP) in = g->ja1 - g->ja0 + 1;
                 if (mode == M_RECOVER) out = g->NY;
-                bytes += (double)(in + out) * g->NX * sizeof(float);
+                bytes += (double)(in + out) * g->NX * sizeof(T);
             }
-            IIM_CHECK(allow_smem(kb_cols_tri, kTriSmem));
-            launch("ls_tri_cols_f32", bytes, 0.0, kb_cols_tri, dim3(G->nx / 32, 1, G->n()), 32, kTriSmem, s,
-                   (const LsProb*)G->d_probs, mode, gate);
+            constexpr int CW = 32 / sizeof(T);
+            auto go = [&](auto kern, int NT, size_t sm) -> iim_status {
+                IIM_CHECK(allow_smem(kern, sm));
+                launch(sizeof(T) == 8 ? "ls_tri_cols_f64" : "ls_tri_cols_f32", bytes, 0.0, kern,
+                       dim3(G->nx / CW, 1, G->n()), NT, sm, s, (const LsProb*)G->d_probs, mode, gate);
+                return IIM_OK;
+            };
+            bool wide = false;
+            if constexpr (sizeof(T) == 4) {   // FP64 keeps 256 threads (bound by FP64 arithmetic)
+                wide = scan_threads(G->NY, (long)(G->nx / CW) * G->n(), sm_count()) == 1024;
+                if (wide) IIM_CHECK(go(kb_cols_scan<T, CW, 1024>, 1024, scan_smem<T, CW, 1024>(G->NY)));
+            }
+            if (!wide) IIM_CHECK(go(kb_cols_scan<T, CW, 256>, 256, scan_smem<T, CW, 256>(G->NY)));
             IIM_LAUNCHED();
             return IIM_OK;
         }
@@ -941,7 +962,7 @@ static iim_status make_group(const std::vector<iim_geometry>& geos, const iim_op
     G->rtol = o.rtol; G->inner = inner; G->dense = o.precond == 3;
     iim_geometry g0 = geos[0];
     G->nx = g0->nx; G->ny = g0->ny; G->NX = g0->NX; G->NY = g0->NY; G->wide = g0->wide_lines; G->cols_c = g0->cols_c;
-    G->tri = o.prec != IIM_FP64 && g0->col_solver == 1 && g0->nx >= 32 && g0->tri_e;
+    G->tri = g0->col_solver == 1;
     for (iim_geometry g : geos) {
         G->max_na = std::max(G->max_na, g->na);
         G->max_ns = std::max(G->max_ns, g->na + g->ncirc);
@@ -987,7 +1008,7 @@ static LsGroup* find_group(const std::vector<iim_geometry>& geos, const iim_opts
         bool same = true;
         for (iim_geometry g : geos)
             same = same && g->wide_lines == G->wide && g->cols_c == G->cols_c &&
-                   (o.prec != IIM_FP64 && g->col_solver == 1 && g->nx >= 32 && g->tri_e) == (G->tri != 0) &&
+                   (g->col_solver == 1) == (G->tri != 0) &&
                    (g->ncirc > 0 && g->cap_ready ? 1 : 0) <= G->cap;
         if (same) return G;
     }

@@ -115,31 +115,46 @@ static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int ou
 
 // Tridiagonal column pass (tri.cuh); blockIdx.y selects one of several fields fstride elements
 // apart.
-__global__ void __launch_bounds__(32)
-k_cols_tri(int NX, int NY, int nx, int in0, int in1, int out0, int out1, float* __restrict__ buf, TriTab t,
-           const int* __restrict__ stop, long fstride) {
+template <typename T, int CW, int NT>
+__global__ void __launch_bounds__(NT, NT == 1024 ? 2 : 4)
+k_cols_scan(int NX, int NY, int ld, int in0, int in1, int out0, int out1, T* __restrict__ buf, ScanTab<T> t,
+            const int* __restrict__ stop, long fstride) {
     if (stop && *stop) return;
-    cols_tri_body(NX, NY, nx, in0, in1, out0, out1, buf + (long)blockIdx.y * fstride, t);
+    cols_scan_body<T, CW, NT>(NX, NY, ld, in0, in1, out0, out1, buf + (long)blockIdx.y * fstride, t);
 }
 
-// Launch: one warp per 32 padded columns, batch fields on grid y.
-static iim_status cols_tri(const Plan<float>& p, int in0, int in1, int out0, int out1, float* buf, const int* stop,
-                           cudaStream_t s, int batch, long fstride) {
-    IIM_CHECK(allow_smem(k_cols_tri, kTriSmem));
-    launch("tri_cols_f32", (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(float),
-           (double)batch * p.NX * 5.0 * p.NY, k_cols_tri, dim3(p.nx / 32, batch), 32, kTriSmem, s, p.NX, p.NY, p.nx,
-           in0, in1, out0, out1, buf, p.tri, stop, fstride);
+// Launch: one block per 32-byte tile of padded columns (8 FP32 or 4 FP64 columns), batch
+// fields on grid y.
+template <typename T, int NT>
+static iim_status cols_scan_nt(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
+                               cudaStream_t s, int batch, long fstride) {
+    constexpr int CW = 32 / sizeof(T);
+    const size_t sm = scan_smem<T, CW, NT>(p.NY);
+    IIM_CHECK(allow_smem(k_cols_scan<T, CW, NT>, sm));
+    launch(sizeof(T) == 8 ? "tri_cols_f64" : "tri_cols_f32",
+           (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T), (double)batch * p.NX * 14.0 * p.NY,
+           k_cols_scan<T, CW, NT>, dim3(p.nx / CW, batch), NT, sm, s, p.NX, p.NY, p.nx, in0, in1, out0, out1, buf,
+           p.scan, stop, fstride);
     IIM_LAUNCHED();
     return IIM_OK;
+}
+
+template <typename T>
+static iim_status cols_scan(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop,
+                            cudaStream_t s, int batch, long fstride) {
+    constexpr int CW = 32 / sizeof(T);
+    if constexpr (sizeof(T) == 4) {   // FP64 keeps 256 threads (it is bound by FP64 arithmetic)
+        if (scan_threads(p.NY, (long)(p.nx / CW) * batch, sm_count()) == 1024)
+            return cols_scan_nt<T, 1024>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
+    }
+    return cols_scan_nt<T, 256>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
 }
 
 // batch > 1: as many fields, fstride elements apart, in one launch
 template <typename T>
 static iim_status cols(const Plan<T>& p, int in0, int in1, int out0, int out1, T* buf, const int* stop, cudaStream_t s,
                        int batch = 1, long fstride = 0) {
-    if constexpr (sizeof(T) == 4) {
-        if (p.tri.e) return cols_tri(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
-    }
+    if (p.scan.lim) return cols_scan(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
     const int C = tile_width<T>(p.cols_c);
     if (C == 8) return cols_tile<T, (sizeof(T) == 4 ? 8 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
     if (C == 2) return cols_tile<T, (sizeof(T) == 8 ? 2 : 4)>(p, in0, in1, out0, out1, buf, stop, s, batch, fstride);
@@ -198,15 +213,19 @@ template <typename T>
 static Plan<T> make_plan(iim_geometry g);
 template <>
 Plan<double> make_plan<double>(iim_geometry g) {
-    return Plan<double>{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x64, g->lam_y64,
-                        twiddles64(), (2.0 / g->nx) * (2.0 / g->ny), g->cols_c, g->wide_lines};
+    Plan<double> p{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x64, g->lam_y64,
+                   twiddles64(), (2.0 / g->nx) * (2.0 / g->ny), g->cols_c, g->wide_lines};
+    if (g->col_solver == 1)
+        p.scan = ScanTab<double>{g->sc64_delta, g->sc64_rowoff, nullptr, g->sc64_lim, g->sc64_dstar, g->h * g->h * (2.0 / g->nx)};
+    return p;
 }
 template <>
 Plan<float> make_plan<float>(iim_geometry g) {
     Plan<float> p{g->NX, g->NY, g->nx, g->ny, ilog2(g->nx), ilog2(g->ny), g->lam_x32, g->lam_y32,
                   twiddles32(), (float)((2.0 / g->nx) * (2.0 / g->ny)), g->cols_c, g->wide_lines};
-    if (g->col_solver == 1 && g->nx >= 32 && g->tri_e)
-        p.tri = TriTab{g->tri_e, g->tri_off, g->tri_len, g->tri_estar, (float)(g->h * g->h * (2.0 / g->nx))};
+    if (g->col_solver == 1)
+        p.scan = ScanTab<float>{g->sc32_delta, g->sc32_rowoff, g->sc32_par, g->sc32_lim, g->sc32_dstar,
+                                (float)(g->h * g->h * (2.0 / g->nx))};
     return p;
 }
 
@@ -1402,6 +1421,13 @@ static iim_status ensure_krylov(iim_geometry g, int m) {
     IIM_TRY(cudaMalloc(&g->H, sizeof(double) * (size_t)L.total()));
     IIM_TRY(cudaMalloc(&g->xsol, sizeof(double) * (size_t)std::max(ns, 1)));
     IIM_TRY(cudaMalloc(&g->bvec, sizeof(double) * (size_t)std::max(ns, 1)));
+    // zero-filled: the solve graph's control kernels read the scalar slots of H also in solves
+    // that never run a Krylov iteration (no affected points), and must not see stale memory
+    IIM_TRY(cudaMemset(g->x0g, 0, sizeof(double) * (size_t)std::max(ns, 1)));
+    IIM_TRY(cudaMemset(g->V, 0, sizeof(double) * (size_t)(m + 1) * std::max(ns, 1)));
+    IIM_TRY(cudaMemset(g->H, 0, sizeof(double) * (size_t)L.total()));
+    IIM_TRY(cudaMemset(g->xsol, 0, sizeof(double) * (size_t)std::max(ns, 1)));
+    IIM_TRY(cudaMemset(g->bvec, 0, sizeof(double) * (size_t)std::max(ns, 1)));
     g->krylov_m = m;
     // the captured iteration graphs refer to the old buffers
     for (void** gp : {&g->graph64, &g->graph32}) {
@@ -1940,6 +1966,107 @@ extern "C" iim_status iim_box_poisson(const iim_grid* grid, const double* f, con
     // pageable-memory copies are staged before cudaMemcpyAsync returns, so the host vectors
     // may go out of scope here
     return IIM_OK;
+}
+
+// ------------------------------------------------------------------------- pass timing
+// Times the three passes of the geometry's rectangular solve in the precision `prec`: the
+// forward row transforms of a dense FP64 field (one launch per field), the column pass and the
+// inverse row transforms (one launch over all `batch` fields).  Each pass is captured `reps`
+// times back to back into a CUDA graph of its own; CUDA events on the stream around a launch of
+// that graph give its device time with no host gap between the kernels.  Inputs are a fixed
+// smooth field.
+template <typename T>
+static iim_status time_passes(iim_geometry g, int batch, int reps, double* us, double* bytes, cudaStream_t cs) {
+    const Plan<T> p = make_plan<T>(g);
+    const long fs = (long)p.nx * p.NY;
+    T *buf = nullptr, *out = nullptr;
+    double* dense = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    iim_status st = IIM_OK;
+#define TP_TRY(call)                                                          \
+    do {                                                                      \
+        const cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess && st == IIM_OK) {                              \
+            record_cuda_error(e_, "iim_time_box_passes", __FILE__, __LINE__); \
+            st = IIM_ERR_CUDA;                                                \
+        }                                                                     \
+    } while (0)
+    TP_TRY(cudaMalloc((void**)&buf, sizeof(T) * fs * batch));
+    TP_TRY(cudaMalloc((void**)&out, sizeof(T) * fs * batch));
+    TP_TRY(cudaMalloc((void**)&dense, sizeof(double) * fs));
+    TP_TRY(cudaEventCreate(&ev0));
+    TP_TRY(cudaEventCreate(&ev1));
+    if (st == IIM_OK) {
+        std::vector<double> h(fs);
+        for (int j = 0; j < p.NY; ++j)
+            for (int i = 0; i < p.nx; ++i)
+                h[(size_t)j * p.nx + i] = i == 0 ? 0.0 : std::sin(0.37 * i) * std::cos(0.11 * j) + 1e-3 * ((i * 7 + j * 13) % 17);
+        TP_TRY(cudaMemcpy(dense, h.data(), sizeof(double) * fs, cudaMemcpyHostToDevice));
+        TP_TRY(cudaMemset(buf, 0, sizeof(T) * fs * batch));
+    }
+    auto pass = [&](int k) -> iim_status {
+        if (k == 0) {
+            for (int b = 0; b < batch; ++b)
+                IIM_CHECK(rows_fwd<T>(p, 0, p.NY, dense, p.nx, 1, nullptr, 0.0, nullptr, nullptr, kNoVec, 0.0,
+                                      buf + b * fs, nullptr, cs));
+            return IIM_OK;
+        }
+        if (k == 1) return cols<T>(p, 0, p.NY - 1, 0, p.NY - 1, buf, nullptr, cs, batch, fs);
+        return rows_inv<T, INV_STORE_T>(p, 0, p.NY, buf, out, nullptr, 0, 0, nullptr, nullptr, cs, batch, fs);
+    };
+    const int launches[3] = {reps * batch, reps, reps};
+    for (int k = 0; k < 3 && st == IIM_OK; ++k) {
+        // one uncaptured pass first: kernel attributes are set outside the capture
+        iim_status ls = pass(k);
+        TP_TRY(cudaStreamSynchronize(cs));
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        if (ls == IIM_OK && st == IIM_OK) {
+            TP_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            for (int r = 0; r < reps && ls == IIM_OK; ++r) ls = pass(k);
+            TP_TRY(cudaStreamEndCapture(cs, &graph));
+        }
+        if (ls == IIM_OK && st == IIM_OK) TP_TRY(cudaGraphInstantiate(&exec, graph, 0));
+        if (ls == IIM_OK && st == IIM_OK) {
+            TP_TRY(cudaGraphLaunch(exec, cs));   // warm-up
+            TP_TRY(cudaEventRecord(ev0, cs));
+            TP_TRY(cudaGraphLaunch(exec, cs));
+            TP_TRY(cudaEventRecord(ev1, cs));
+            TP_TRY(cudaEventSynchronize(ev1));
+            float ms = 0.f;
+            TP_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+            us[k] = 1e3 * ms / launches[k];
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (ls != IIM_OK && st == IIM_OK) st = ls;
+    }
+#undef TP_TRY
+    if (st == IIM_OK) {
+        const double e = (double)p.NY * p.NX;
+        bytes[0] = e * (8.0 + sizeof(T));
+        bytes[1] = 2.0 * e * sizeof(T) * batch;
+        bytes[2] = 2.0 * e * sizeof(T) * batch;
+    }
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    cudaFree(buf);
+    cudaFree(out);
+    cudaFree(dense);
+    return st;
+}
+
+extern "C" iim_status iim_time_box_passes(iim_geometry g, int prec, int batch, int reps, double* us, double* bytes) {
+    if (!g || !us || !bytes || batch < 1 || reps < 1 || (prec != IIM_FP64 && prec != IIM_MIXED))
+        return IIM_ERR_INVALID_ARG;
+    cudaSetDevice(g->device);
+    IIM_CHECK(ensure_twiddles());
+    cudaStream_t cs = nullptr;
+    IIM_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    const iim_status st = prec == IIM_FP64 ? time_passes<double>(g, batch, reps, us, bytes, cs)
+                                           : time_passes<float>(g, batch, reps, us, bytes, cs);
+    cudaStreamDestroy(cs);
+    return st;
 }
 
 // ------------------------------------------------------------------------- allocation-free box solve

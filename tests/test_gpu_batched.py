@@ -185,7 +185,7 @@ def test_lockstep_groups_equal_single_solves(prec, precond):
             assert run[4][k]["rel_res"] == s1["rel_res"] and run[4][k]["rel_res"] < 1e-11
     assert lock[5] < per_problem[5]
     names = {r["name"] for r in prof}
-    assert ("ls_cols_f64" if prec == iim.IIM_FP64 else "ls_cols_f32") in names
+    assert ("ls_tri_cols_f64" if prec == iim.IIM_FP64 else "ls_tri_cols_f32") in names   # default column pass
     assert ("ls_dense_schur_matvec" in names) == (precond == 3)
     assert "ls_gmres_arnoldi" in names and "ls_residual_f64" in names
     for g in geos:

@@ -87,7 +87,9 @@ def test_free_space_iim_two_bodies_matches_oracle(two_bodies_64, prec, precond):
 
 def test_free_space_iim_second_order_on_the_gpu():
     """Sec. 4.3 on the GPU up to 512^2: the reconstructed velocity converges to the exact
-    Lamb-Oseen velocity at second order (mixed precision, dense inner operator)."""
+    Lamb-Oseen velocity at second order (mixed precision, dense inner operator).  In free
+    space a mixed-precision correction contracts the FP64 residual by only 0.03-0.3 (the ring
+    rows weigh FP32 rounding next to the box heavily), so 512^2 takes 8-12 refinements."""
     c = inputs.FREE_SPACE_TWO_BODIES
     errs, errs2 = [], []
     for n in (64, 128, 256, 512):
@@ -96,7 +98,7 @@ def test_free_space_iim_second_order_on_the_gpu():
         iim.iim_geometry_set_outer(geo, 1)
         iim.iim_build_preconditioner(geo)
         out = gu.solve_opts(P, geo, gamma=P.gamma, velocity=True,
-                            opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11, precond=3))
+                            opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-11, precond=3, max_refine=24))
         X, Y = P.grid.nodes()
         _, ex, ey = inputs.lamb_oseen(X, Y, c["x0"][0], c["x0"][1], c["gamma"], c["nu_t"])
         fl = (P.phi >= 0)[1:-1, 1:-1]
