@@ -90,21 +90,48 @@ def poisson_box(f, h, ring=None):
     return dst1(dst1(U, axis=1), axis=0) * (2.0 / nx) * (2.0 / ny)
 
 
-def poisson_free(f, h):
+def poisson_free(f, h, sym=False, plane=None):
     """Free-space solve (Sec. 4.1, unbounded domain; Sec. 4.2, nabla_h^-2 with unbounded
     boundary conditions): psi = h^2 sum_y G(x - y) f(y) with the lattice Green's function G of
     the five-point Laplacian (oracle/lgf.py, gauge G(0, 0) = 0), for f on the interior nodes.
     Returns psi at every node of the box, interior and ring: a node array (ny+1, nx+1).  The
-    convolution is a plain zero-padded linear convolution (scipy's FFT convolution)."""
+    convolution is a plain zero-padded linear convolution (scipy's FFT convolution).
+
+    sym: the outflow variant of Sec. 5.2 -- the vorticity mirrored evenly across the vertical
+    plane through the right box edge (node column nx): the sources are f on the interior nodes,
+    their images at y* = (2 nx - i, j), and `plane` (ny - 1 values, rows 1..ny-1; zero if None)
+    on the plane column itself, which is its own image:
+        psi(x) = h^2 { sum_y [G(x - y) + G(x - y*)] f(y) + sum_j G(x - (nx, j)) plane_j }.
+    psi is then even about the plane (d psi / dx = 0 there, so u_y = 0 and d u_x / dx = 0)."""
     from scipy.signal import fftconvolve
 
     from . import lgf
     ny1, nx1 = f.shape
     nx, ny = nx1 + 1, ny1 + 1
-    src = np.zeros((ny + 1, nx + 1))
-    src[1:-1, 1:-1] = f
-    full = fftconvolve(src, lgf.lgf_full(nx, ny), mode="full")
-    return h * h * full[ny:2 * ny + 1, nx:2 * nx + 1]
+    if not sym:
+        src = np.zeros((ny + 1, nx + 1))
+        src[1:-1, 1:-1] = f
+        full = fftconvolve(src, lgf.lgf_full(nx, ny), mode="full")
+        return h * h * full[ny:2 * ny + 1, nx:2 * nx + 1]
+    W = 2 * nx                      # source columns 0..2nx: the box, the plane and the image
+    src = np.zeros((ny + 1, W + 1))
+    src[1:-1, 1:nx] = f
+    src[1:-1, W - nx + 1:W] = f[:, ::-1]    # column 2nx - i holds f(i)
+    if plane is not None:
+        src[1:-1, nx] = plane
+    full = fftconvolve(src, lgf.lgf_full(W, ny), mode="full")
+    return h * h * full[ny:2 * ny + 1, W:W + nx + 1]
+
+
+def plane_potential(nx, ny, h, plane):
+    """h^2 sum_j G(x - (nx, j)) plane_j on the box ring (ring layout): the field of the sources
+    on the outflow plane, harmonic inside the box."""
+    from . import lgf
+    G = lgf.lgf_table(nx + 1, ny + 1)
+    ring = [(i, 0) for i in range(nx + 1)] + [(i, ny) for i in range(nx + 1)] + \
+           [(0, j) for j in range(1, ny)] + [(nx, j) for j in range(1, ny)]
+    js = np.arange(1, ny)
+    return np.array([h * h * (G[np.abs(xj - js), abs(xi - nx)] * plane).sum() for xi, xj in ring])
 
 
 def ring_of(nodes):
@@ -112,28 +139,44 @@ def ring_of(nodes):
     return np.concatenate([nodes[0, :], nodes[-1, :], nodes[1:-1, 0], nodes[1:-1, -1]])
 
 
-def ring_residual(nodes):
+def ring_residual(nodes, sym=False, plane=None, h=None):
     """Free-space consistency of the box ring: for a field that is the free-space potential of
     sources inside the box, the discrete Green's second identity on the interior nodes (the
     five-point stencil summed by parts against G(x - .), which is harmonic there for x on the
     ring) gives psi(x) = sum over the non-corner ring nodes z of G(x - z) psi(n(z)) -
     G(x - n(z)) psi(z), n(z) the interior neighbour of z.  Returns psi(x) minus that sum on the
     ring (ring layout): zero for free-space fields, exactly e(x) for a field e harmonic inside
-    the box."""
+    the box.
+
+    sym (the outflow variant, see poisson_free): the kernel is K(x, y) = G(x - y) + G(x* - y),
+    x* = (2 nx - i, j) the image of the ring node x across the right box edge.  The mirrored
+    part of the field is harmonic inside the box and G(x* - .) is harmonic there too, so the
+    same identity holds with K: psi(x) = psi_f(x) + psi_f(x*) = sum K(x, z) psi(n(z)) -
+    K(x, n(z)) psi(z).  Sources on the plane column (`plane`, with the grid spacing h) make a
+    field harmonic inside the box, which the identity leaves on the ring: it is subtracted
+    (plane_potential)."""
     from . import lgf
     ny, nx = nodes.shape[0] - 1, nodes.shape[1] - 1
-    G = lgf.lgf_table(nx + 1, ny + 1)
+    G = lgf.lgf_table(2 * nx + 1 if sym else nx + 1, ny + 1)
     ring = [(i, 0) for i in range(nx + 1)] + [(i, ny) for i in range(nx + 1)] + \
            [(0, j) for j in range(1, ny)] + [(nx, j) for j in range(1, ny)]
     src = [((i, 0), (i, 1)) for i in range(1, nx)] + [((i, ny), (i, ny - 1)) for i in range(1, nx)] + \
           [((0, j), (1, j)) for j in range(1, ny)] + [((nx, j), (nx - 1, j)) for j in range(1, ny)]
     zi = np.array([z[0] for z, _ in src]); zj = np.array([z[1] for z, _ in src])
     ai = np.array([a[0] for _, a in src]); aj = np.array([a[1] for _, a in src])
+
+    def K(xi, xj, yi, yj):
+        k = G[np.abs(xj - yj), np.abs(xi - yi)]
+        if sym:
+            k = k + G[np.abs(xj - yj), np.abs(2 * nx - xi - yi)]
+        return k
+
     out = np.empty(len(ring))
     for t, (xi, xj) in enumerate(ring):
-        s = (G[np.abs(xj - zj), np.abs(xi - zi)] * nodes[aj, ai]).sum() - \
-            (G[np.abs(xj - aj), np.abs(xi - ai)] * nodes[zj, zi]).sum()
+        s = (K(xi, xj, zi, zj) * nodes[aj, ai]).sum() - (K(xi, xj, ai, aj) * nodes[zj, zi]).sum()
         out[t] = nodes[xj, xi] - s
+    if sym and plane is not None:
+        out = out - plane_potential(nx, ny, h, plane)
     return out
 
 
@@ -371,15 +414,18 @@ def gmres_mgs(apply, b, tol, restart, max_iter, x0=None):
 
 
 def solve_schur(S: Setup, omega=None, ring=None, gamma=None, psibar=None,
-                tol=1e-13, restart=60, max_iter=2000, ops=None, outer="dirichlet"):
+                tol=1e-13, restart=60, max_iter=2000, ops=None, outer="dirichlet", plane=None):
     """The paper's algorithm (Sec. 4.2): GMRES on the augmented Schur system, then Eq.
     psirecovery.  Returns (psi node array, psibar, gmres iterations, gmres rel. residual).
     outer = "dirichlet": the rectangular solve is the Dirichlet box (DST-I) with box data
     `ring`; outer = "unbounded": it is the free-space solve (poisson_free), the box ring of the
-    result is part of the solution and `ring` is ignored."""
+    result is part of the solution and `ring` is ignored; outer = "symmetric": the same with
+    the outflow plane through the right box edge (poisson_free(..., sym=True), Sec. 5.2) and
+    `plane` the vorticity on the plane column."""
     P = S.prob
     omega = P.omega if omega is None else omega
-    free = outer == "unbounded"
+    free = outer in ("unbounded", "symmetric")
+    sym = outer == "symmetric"
     ring = (np.zeros(2 * (S.nx + S.ny)) if free else P.psi_box) if ring is None else ring
     psibar = np.zeros(S.nb) if psibar is None else np.asarray(psibar, dtype=np.float64)
     gamma = np.zeros(S.nb) if gamma is None else np.asarray(gamma, dtype=np.float64)
@@ -388,9 +434,10 @@ def solve_schur(S: Setup, omega=None, ring=None, gamma=None, psibar=None,
     na, circ = O.na, S.circ
 
     def solve_rect(f, with_ring):
-        """Interior values of the rectangular solve (and the node array in free space)."""
+        """Interior values of the rectangular solve (and the node array in free space); the
+        plane sources are data, so they enter with the data (with_ring) only."""
         if free:
-            nodes = poisson_free(f, h)
+            nodes = poisson_free(f, h, sym=sym, plane=plane if with_ring else None)
             return nodes[1:-1, 1:-1], nodes
         return poisson_box(f, h, ring if with_ring else None), None
 
@@ -438,14 +485,14 @@ def velocity(S: Setup, psi_nodes, psibar):
     return np.where(fl, ux, 0.0), np.where(fl, uy, 0.0)
 
 
-def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None, outer="dirichlet"):
+def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None, outer="dirichlet", plane=None):
     """Relative residual ||f - L u|| / ||f|| of the un-reduced system (circulation rows in the
     units of omega).  Evaluated matrix-free; `psi_nodes` must carry the box data.  In free
-    space (outer = "unbounded") the box ring of psi_nodes is part of the solution, so the
-    known part f carries no box terms."""
+    space (outer = "unbounded" or "symmetric") the box ring of psi_nodes is part of the solution,
+    so the known part f carries no box terms."""
     P = S.prob
     omega = P.omega if omega is None else omega
-    if outer == "unbounded":
+    if outer in ("unbounded", "symmetric"):
         ring = np.zeros(2 * (S.nx + S.ny))
     else:
         ring = P.psi_box if ring is None else ring
@@ -465,10 +512,12 @@ def residual(S: Setup, psi_nodes, psibar, omega=None, ring=None, gamma=None, out
     f = np.where(fl, omega - neg_laplacian_5pt(ek, h), 0.0)
     rc = np.array([(gamma[k] - discrete_circulation(psi_nodes, P.regions[k])) / (h * h) for k in S.circ])
     fc = np.array([gamma[k] / (h * h) for k in S.circ])
-    if outer == "unbounded":
+    if outer in ("unbounded", "symmetric"):
         # the ring equations of the free-space system (ring_residual), in units of omega
-        rr = ring_residual(psi_nodes) / (h * h)
+        rr = ring_residual(psi_nodes, sym=outer == "symmetric", plane=plane, h=h) / (h * h)
         rc = np.concatenate([rc, rr])
+        if outer == "symmetric" and plane is not None:
+            fc = np.concatenate([fc, plane_potential(S.nx, S.ny, h, plane) / (h * h)])
     num = np.sqrt((r * r).sum() + (rc * rc).sum())
     den = np.sqrt((f * f).sum() + (fc * fc).sum())
     return num / den

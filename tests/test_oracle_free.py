@@ -124,3 +124,96 @@ def test_ring_residual_identity():
     H = op.ring_to_nodes(nx, ny, e)
     H[1:-1, 1:-1] = op.poisson_box(np.zeros((ny - 1, nx - 1)), h, e)
     assert np.abs(op.ring_residual(psi + H) - e).max() < 1e-12
+
+
+# ----------------------------------------------------------------------------- outflow plane
+def test_symmetric_solve_matches_brute_force_on_a_tiny_box():
+    """poisson_free(sym=True) equals the double sum h^2 {sum_y [G(x - y) + G(x - y*)] f(y) +
+    sum_j G(x - (nx, j)) plane_j} over every box node x, with G from scipy's adaptive quadrature
+    (no table, no FFT)."""
+    rng = np.random.default_rng(5)
+    nx, ny, h = 6, 5, 0.3
+    f = rng.normal(size=(ny - 1, nx - 1))
+    plane = rng.normal(size=ny - 1)
+    psi = op.poisson_free(f, h, sym=True, plane=plane)
+    ref = np.zeros((ny + 1, nx + 1))
+    for xj in range(ny + 1):
+        for xi in range(nx + 1):
+            acc = 0.0
+            for yj in range(1, ny):
+                for yi in range(1, nx):
+                    acc += (lgf.lgf_quad(xi - yi, xj - yj) + lgf.lgf_quad(xi - (2 * nx - yi), xj - yj)) * f[yj - 1, yi - 1]
+                acc += lgf.lgf_quad(xi - nx, xj - yj) * plane[yj - 1]
+            ref[xj, xi] = h * h * acc
+    assert np.abs(psi - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_symmetric_solve_five_point_equation_and_even_plane():
+    """The outflow variant: -nabla_h^2 psi = f at every interior node, and on the plane column
+    (the right box edge) the five-point equation holds with the mirrored neighbour
+    psi(nx + 1, j) = psi(nx - 1, j) and the plane's own source: psi is the even continuation
+    there (d psi / dx = 0 on the plane).  The free-space solve without the image does not
+    satisfy it."""
+    rng = np.random.default_rng(7)
+    nx, ny, h = 32, 24, 0.1
+    f = rng.normal(size=(ny - 1, nx - 1))
+    plane = rng.normal(size=ny - 1)
+    for sym in (True, False):
+        psi = op.poisson_free(f, h, sym=sym, plane=plane if sym else None)
+        assert np.abs(op.neg_laplacian_5pt(psi, h) - f).max() < 1e-9
+        eq = -(2 * psi[1:-1, nx - 1] + psi[2:, nx] + psi[:-2, nx] - 4 * psi[1:-1, nx]) / (h * h)
+        if sym:
+            assert np.abs(eq - plane).max() < 1e-9 * np.abs(f).max()
+        else:
+            assert np.abs(eq - plane).max() > 1e-3 * np.abs(f).max()
+
+
+def test_symmetric_ring_residual_identity():
+    """The ring equations with the symmetric kernel: zero for the outflow-variant field (its
+    plane sources given), exactly e for a field e harmonic inside the box added to it; the
+    free-space kernel does not give zero for the symmetric field."""
+    rng = np.random.default_rng(2)
+    nx, ny, h = 24, 16, 0.1
+    plane = rng.normal(size=ny - 1)
+    psi = op.poisson_free(rng.normal(size=(ny - 1, nx - 1)), h, sym=True, plane=plane)
+    assert np.abs(op.ring_residual(psi, sym=True, plane=plane, h=h)).max() < 1e-12 * np.abs(psi).max()
+    assert np.abs(op.ring_residual(psi)).max() > 1e-3 * np.abs(psi).max()
+    e = rng.normal(size=2 * (nx + ny))
+    H = op.ring_to_nodes(nx, ny, e)
+    H[1:-1, 1:-1] = op.poisson_box(np.zeros((ny - 1, nx - 1)), h, e)
+    assert np.abs(op.ring_residual(psi + H, sym=True, plane=plane, h=h) - e).max() < 1e-12
+
+
+def test_symmetric_lamb_oseen_with_image_second_order():
+    """A Lamb-Oseen vortex near the outflow plane x = 1 (the right edge of [0, 1]^2): the
+    vorticity is the vortex plus its mirror image (even about the plane), given on the interior
+    nodes and on the plane column; the outflow-variant velocity converges at second order to the
+    exact velocity of the pair."""
+    errs = []
+    x0, y0, gam, nut = 0.8, 0.501, 1.0, 0.0025
+    for n in (32, 64, 128):
+        g = inputs.Grid(0.0, 1.0, 0.0, 1.0, n, n)
+        X, Y = g.nodes()
+        w1, ux1, uy1 = inputs.lamb_oseen(X, Y, x0, y0, gam, nut)
+        w2, ux2, uy2 = inputs.lamb_oseen(X, Y, 2.0 - x0, y0, gam, nut)
+        w = w1 + w2
+        psi = op.poisson_free(w[1:-1, 1:-1], g.h, sym=True, plane=w[1:-1, -1])
+        vx = (psi[2:, 1:-1] - psi[:-2, 1:-1]) / (2 * g.h)
+        vy = -(psi[1:-1, 2:] - psi[1:-1, :-2]) / (2 * g.h)
+        errs.append(max(np.abs(vx - (ux1 + ux2)[1:-1, 1:-1]).max(), np.abs(vy - (uy1 + uy2)[1:-1, 1:-1]).max()))
+    rates = [math.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert min(rates) > 1.8, (errs, rates)
+
+
+def test_symmetric_iim_residual_and_circulation():
+    """The IIM solve with the outflow plane (plane sources given): the result satisfies the
+    un-reduced equations with the symmetric ring rows and the circulation constraint of each
+    body; it is not the free-space solution."""
+    P = inputs.lamb_oseen_two_bodies(64)
+    S = op.Setup(P)
+    plane = np.linspace(0.1, -0.2, P.grid.ny - 1)
+    psi, pb, it, rel = op.solve_schur(S, gamma=P.gamma, outer="symmetric", tol=1e-13, plane=plane)
+    assert op.residual(S, psi, pb, gamma=P.gamma, outer="symmetric", plane=plane) < 1e-11
+    assert op.residual(S, psi, pb, gamma=P.gamma, outer="unbounded") > 1e-6
+    for k, r in enumerate(P.regions):
+        assert abs(op.discrete_circulation(psi, r) - P.gamma[k]) < 1e-11
