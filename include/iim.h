@@ -229,7 +229,8 @@ iim_status iim_poisson_solve_batched_host(int n, iim_geometry const* geoms, cons
 iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
 
 /* Exterior condition of the geometry's solves (Sec. 4.1: bounded and unbounded domains;
- * Sec. 4.2: the rectangular solution operator nabla_h^-2 with those conditions).
+ * Sec. 4.2: the rectangular solution operator nabla_h^-2 with those conditions; Sec. 5.2:
+ * outflow boundaries).
  *   outer 0 (default): Dirichlet box -- psi_box is the data on the box ring, gauge psibar_0 = 0.
  *   outer 1: unbounded -- psi is the free-space solution on the infinite lattice: the solution
  *     operator is the convolution psi(x) = h^2 sum_y G(x - y) f(y) with the lattice Green's
@@ -240,11 +241,24 @@ iim_status iim_geometry_set_tiles(iim_geometry g, int cols_per_block);
  *     box ring of psi is part of the solution (iim_geometry_outer_ring); omega must vanish outside
  *     the box.  psi is the perturbation field: for a free stream u_inf add u_inf x x (lattice-
  *     harmonic, so give psi_b minus it at the control points).  guess mode 1 is refused.
+ *   outer 2: unbounded with an outflow plane through the right box edge (node column nx): the
+ *     vorticity is mirrored evenly across that plane (Sec. 5.2), so psi is the free-space field
+ *     of omega, of its images (2 nx - i, j) and of the vorticity on the plane column itself
+ *     (iim_geometry_set_plane_vorticity; zero until set), which is its own image:
+ *     psi(x) = h^2 { sum_y [G(x - y) + G(x - y*)] omega(y) + sum_j G(x - (nx, j)) w_j }; psi is
+ *     even about the plane (u_y = 0 and d u_x / dx = 0 there).  The same method with the ring
+ *     kernel G(x - y) + G(x* - y); the G table covers 2 nx columns.
  * Changing it drops the geometry's preconditioner, circulation responses and solve graphs (they
- * are rebuilt by the next solve).  The first switch to 1 for a grid size builds that size's G
- * table (device, shared, kept until exit; synchronizes the device).
- * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA. */
+ * are rebuilt by the next solve).  The first switch to 1 or 2 for a grid size builds that
+ * size's G table (device, shared, kept until exit; synchronizes the device).
+ * Errors: IIM_ERR_INVALID_ARG (outer not 0, 1 or 2), IIM_ERR_CUDA. */
 iim_status iim_geometry_set_outer(iim_geometry g, int outer);
+
+/* With the outflow plane (outer 2): the vorticity on the plane column, w (NY = ny - 1 values,
+ * rows j = 1..ny-1, host or device memory), copied into the geometry (stream-ordered) and used
+ * by every later solve until set again; the circulation responses leave it out.  Errors:
+ * IIM_ERR_INVALID_ARG (null pointer, or the geometry is not in mode 2), IIM_ERR_CUDA. */
+iim_status iim_geometry_set_plane_vorticity(iim_geometry g, const double* w, iim_stream stream);
 
 /* In free space (outer 1): psi on the box ring of the last solve (device, 2 (nx + ny) values in
  * the ring layout).  Asynchronous.  Errors: IIM_ERR_INVALID_ARG (not in free space). */

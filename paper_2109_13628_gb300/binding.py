@@ -73,6 +73,7 @@ SIGNATURES = [
     ("iim_geometry_set_lines", _i, [_vp, _i]),
     ("iim_geometry_set_column_solver", _i, [_vp, _i]),
     ("iim_time_box_passes", _i, [_vp, _i, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)]),
+    ("iim_geometry_set_plane_vorticity", _i, [_vp, _vp, _vp]),
     ("iim_geometry_set_outer", _i, [_vp, _i]),
     ("iim_geometry_outer_ring", _i, [_vp, _vp, _vp]),
     ("iim_cv_terms", _i, [_vp, _vp, _vp, _vp, _vp, _d, ctypes.POINTER(iim_region), _d, ctypes.POINTER(_d), _vp, _vp]),
@@ -254,8 +255,16 @@ def iim_time_box_passes(g: "Geometry", prec: int, batch: int = 1, reps: int = 20
     return {"us": list(us), "bytes": list(by)}
 
 
+def iim_geometry_set_plane_vorticity(g: "Geometry", w, stream=None):
+    """With the outflow plane (outer 2): the vorticity on the plane column (ny - 1 values, a CUDA
+    tensor of FP64; see iim.h)."""
+    _check(load().iim_geometry_set_plane_vorticity(g.handle, _ptr(w, torch.float64, g.grid.ny - 1, "w"),
+                                                   _stream(stream)), "iim_geometry_set_plane_vorticity")
+
+
 def iim_geometry_set_outer(g: "Geometry", outer: int):
-    """Exterior condition: 0 Dirichlet box (default), 1 unbounded (free space)."""
+    """Exterior condition: 0 Dirichlet box (default), 1 unbounded (free space), 2 unbounded with
+    the outflow plane through the right box edge."""
     _check(load().iim_geometry_set_outer(g.handle, int(outer)), "iim_geometry_set_outer")
 
 

@@ -144,12 +144,18 @@ struct iim_geometry_s {
     double* sc64_dstar = nullptr;
     float4* sc32_par = nullptr;   // FP32: per-column parameters of the closed form (tri.cuh)
     int col_solver = 1;
-    // free space (iim_geometry_set_outer): 0 = Dirichlet box, 1 = unbounded (freespace.cu); the
-    // lattice Green's function table (shared per grid size, not owned), psi on the box ring of
-    // the current solve, the ring sum of the last free-space application, and psi_1 next to the
-    // box (first / last interior row, then first / last interior column)
+    // free space (iim_geometry_set_outer): 0 = Dirichlet box, 1 = unbounded, 2 = unbounded with
+    // the outflow plane through the right box edge (freespace.cu); the lattice Green's function
+    // table (shared per size, not owned; columns 0..nx, or 0..2nx with the plane, row stride
+    // lgf_ld), psi on the box ring of the current solve, the ring sum of the last free-space
+    // application, and psi_1 next to the box (first / last interior row, then first / last
+    // interior column); the vorticity on the plane column (NY values) and a switch that leaves it
+    // out (the unit-circulation responses)
     int outer = 0;
     const double* lgf = nullptr;
+    int lgf_ld = 0;
+    double* fs_plane = nullptr;
+    int plane_off = 0;
     double *fs_ring = nullptr, *fs_rho = nullptr, *fs_bnd = nullptr;
     double* fs_rres = nullptr;   // ring rows of the last FP64 residual
     double* cap_ring = nullptr;  // ring values of the unit-circulation responses (free space)
@@ -224,11 +230,11 @@ iim_status lgf_table(int nx, int ny, const double** out);
 template <typename T>
 iim_status launch_bnd_cols(int NX, int NY, int nx, const T* buf, double* vl, double* vr, const int* stop,
                            cudaStream_t s);
-iim_status launch_ring_conv(int nx, int ny, const double* G, const double* bnd, const double* vl, const double* vr,
-                            double* rho, const int* stop, cudaStream_t s);
+iim_status launch_ring_conv(int nx, int ny, const double* G, int ld, int sym, const double* bnd, const double* vl,
+                            const double* vr, double* rho, const int* stop, cudaStream_t s);
 iim_status launch_ring_add(int n, double a, const double* x, double* y, const int* stop, cudaStream_t s);
-iim_status launch_ring_residual(int nx, int ny, double h, const double* G, const double* psi, const double* ring,
-                                double* rres, double* res2, cudaStream_t s);
+iim_status launch_ring_residual(int nx, int ny, double h, const double* G, int ld, int sym, const double* plane,
+                                const double* psi, const double* ring, double* rres, double* res2, cudaStream_t s);
 // dense Schur-complement preconditioner (precond.cu)
 // [S | I] -> [I | S^-1] in place; scratch holds gj_scratch_floats(n) floats
 size_t gj_scratch_floats(int n);

@@ -18,6 +18,14 @@
 // This file holds the lattice Green's function table, the extraction of psi_1 next to the box
 // and the ring sum; solve.cu strings them together with the box solves.
 //
+// Outflow plane (Sec. 5.2): the vorticity mirrored evenly across the vertical plane through
+// the right box edge (node column nx).  The mirrored interior sources are a field harmonic
+// inside the box whose values on the ring are those of the free-space field at the mirror
+// points, so the ring kernel becomes K(x, y) = G(x - y) + G(x* - y), x* = (2 nx - i, j) (table
+// columns up to 2 nx); sources on the plane column are their own images and are data: their
+// potential h^2 sum_j G(x - (nx, j)) w_j enters the ring equations, and through them the
+// correction of each refinement.
+//
 // The table G(m, n), 0 <= m <= nx, 0 <= n <= ny, depends on the lattice only (not on h), so it
 // is built once per (device, nx, ny) and shared by every geometry of that size:
 //   max(m, n) < 64: -G(m, n) = (1 / 2 pi) int_0^pi (1 - cos(m t) e^(-n a)) / sinh(a) dt,
@@ -117,8 +125,8 @@ __global__ void k_lgf_table(int M, int N, GaussRule R, double* __restrict__ G) {
 static std::mutex g_lgf_mutex;
 static std::map<std::tuple<int, int, int>, double*> g_lgf_tables;
 
-// The table for an (nx x ny)-cell box on the current device (built on first use, kept until the
-// process exits).  Synchronizes the device on first use.
+// The table G(m, n), 0 <= m <= nx, 0 <= n <= ny (row stride nx + 1), on the current device
+// (built on first use, kept until the process exits).  Synchronizes the device on first use.
 iim_status lgf_table(int nx, int ny, const double** out) {
     int dev = 0;
     IIM_TRY(cudaGetDevice(&dev));
@@ -172,13 +180,14 @@ __global__ void k_bnd_cols(int NX, int NY, int nx, const T* __restrict__ buf, do
     }
 }
 
-// rho(x) = sum over the non-corner ring nodes y of G(x - y) psi_1(neighbour of y), for every
+// rho(x) = sum over the non-corner ring nodes y of K(x, y) psi_1(neighbour of y), for every
 // ring node x (ring layout: bottom j = 0, i = 0..nx; top j = ny; left i = 0, j = 1..ny-1; right
-// i = nx).  bnd: psi_1 on the first interior row (NX values) then on the last (NX values);
-// vl, vr: psi_1 on the first and last interior columns (NY values each).  One block per x.
+// i = nx), K(x, y) = G(x - y) (+ G(x* - y) with the outflow plane, sym); G has row stride ld.
+// bnd: psi_1 on the first interior row (NX values) then on the last (NX values); vl, vr: psi_1
+// on the first and last interior columns (NY values each).  One block per x.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_ring_conv(int nx, int ny, const double* __restrict__ G, const double* __restrict__ bnd,
+k_ring_conv(int nx, int ny, const double* __restrict__ G, int ld, int sym, const double* __restrict__ bnd,
             const double* __restrict__ vl, const double* __restrict__ vr, double* __restrict__ rho,
             const int* __restrict__ stop) {
     if (stop && *stop) return;
@@ -188,7 +197,7 @@ k_ring_conv(int nx, int ny, const double* __restrict__ G, const double* __restri
     else if (t <= 2 * nx + 1) { xi = t - (nx + 1); xj = ny; }
     else if (t < 2 * (nx + 1) + (ny - 1)) { xi = 0; xj = t - 2 * (nx + 1) + 1; }
     else { xi = nx; xj = t - 2 * (nx + 1) - (ny - 1) + 1; }
-    const int NX = nx - 1, NY = ny - 1, ld = nx + 1;
+    const int NX = nx - 1, NY = ny - 1;
     const int nsrc = 2 * NX + 2 * NY;
     double acc = 0.0;
     for (int s = threadIdx.x; s < nsrc; s += BLOCK) {
@@ -198,7 +207,10 @@ k_ring_conv(int nx, int ny, const double* __restrict__ G, const double* __restri
         else if (s < 2 * NX) { si = s - NX + 1; sj = ny; v = bnd[s]; }
         else if (s < 2 * NX + NY) { si = 0; sj = s - 2 * NX + 1; v = vl[sj - 1]; }
         else { si = nx; sj = s - 2 * NX - NY + 1; v = vr[sj - 1]; }
-        acc += G[(size_t)abs(xj - sj) * ld + abs(xi - si)] * v;
+        const size_t row = (size_t)abs(xj - sj) * ld;
+        double k = G[row + abs(xi - si)];
+        if (sym) k += G[row + abs(2 * nx - xi - si)];
+        acc += k * v;
     }
     acc = block_sum<BLOCK>(acc);
     if (threadIdx.x == 0) rho[t] = acc;
@@ -218,19 +230,30 @@ __global__ void k_ring_add(int n, double a, const double* __restrict__ x, double
 //   psi(x) = sum over the non-corner ring nodes z of G(x - z) psi(n(z)) - G(x - n(z)) psi(z),
 // n(z) the interior neighbour of z; a field harmonic inside the box leaves exactly its ring
 // values in  rres(x) = psi(x) - that sum,  so a ring error that the interior rows cannot see
-// shows here.  psi: padded interior field; ring: psi on the ring.  One block per ring node.
+// shows here.  With the outflow plane (sym) the kernel is K(x, y) = G(x - y) + G(x* - y) (the
+// mirrored part is harmonic inside the box, and so is G(x* - .)), and the potential of the
+// plane sources, h^2 sum_j G(x - (nx, j)) plane_j (harmonic inside), is the data of the row and
+// is subtracted (plane null: no plane sources).  psi: padded interior field; ring: psi on the
+// ring.  One block per ring node.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-k_ring_residual(int nx, int ny, const double* __restrict__ G, const double* __restrict__ psi,
-                const double* __restrict__ ring, double* __restrict__ rres) {
+k_ring_residual(int nx, int ny, double h2, const double* __restrict__ G, int ld, int sym,
+                const double* __restrict__ plane, const double* __restrict__ psi, const double* __restrict__ ring,
+                double* __restrict__ rres) {
     const int t = blockIdx.x;
     int xi, xj;
     if (t <= nx) { xi = t; xj = 0; }
     else if (t <= 2 * nx + 1) { xi = t - (nx + 1); xj = ny; }
     else if (t < 2 * (nx + 1) + (ny - 1)) { xi = 0; xj = t - 2 * (nx + 1) + 1; }
     else { xi = nx; xj = t - 2 * (nx + 1) - (ny - 1) + 1; }
-    const int NX = nx - 1, NY = ny - 1, ld = nx + 1;
+    const int NX = nx - 1, NY = ny - 1;
     const int nsrc = 2 * NX + 2 * NY;
+    auto K = [&](int yi, int yj) {
+        const size_t row = (size_t)abs(xj - yj) * ld;
+        double k = G[row + abs(xi - yi)];
+        if (sym) k += G[row + abs(2 * nx - xi - yi)];
+        return k;
+    };
     double acc = 0.0;
     for (int s = threadIdx.x; s < nsrc; s += BLOCK) {
         int zi, zj, ai, aj, zr;   // ring node, its interior neighbour, its ring index
@@ -239,7 +262,11 @@ k_ring_residual(int nx, int ny, const double* __restrict__ G, const double* __re
         else if (s < 2 * NX + NY) { zi = 0; zj = s - 2 * NX + 1; ai = 1; aj = zj; zr = 2 * (nx + 1) + zj - 1; }
         else { zi = nx; zj = s - 2 * NX - NY + 1; ai = nx - 1; aj = zj; zr = 2 * (nx + 1) + NY + zj - 1; }
         const double pa = psi[(size_t)(aj - 1) * nx + ai];
-        acc += G[(size_t)abs(xj - zj) * ld + abs(xi - zi)] * pa - G[(size_t)abs(xj - aj) * ld + abs(xi - ai)] * ring[zr];
+        acc += K(zi, zj) * pa - K(ai, aj) * ring[zr];
+    }
+    if (sym && plane) {
+        for (int j = 1 + threadIdx.x; j <= NY; j += BLOCK)
+            acc += h2 * G[(size_t)abs(xj - j) * ld + abs(xi - nx)] * plane[j - 1];
     }
     acc = block_sum<BLOCK>(acc);
     if (threadIdx.x == 0) rres[t] = ring[t] - acc;
@@ -266,11 +293,11 @@ iim_status launch_bnd_cols(int NX, int NY, int nx, const T* buf, double* vl, dou
 template iim_status launch_bnd_cols<float>(int, int, int, const float*, double*, double*, const int*, cudaStream_t);
 template iim_status launch_bnd_cols<double>(int, int, int, const double*, double*, double*, const int*, cudaStream_t);
 
-iim_status launch_ring_conv(int nx, int ny, const double* G, const double* bnd, const double* vl, const double* vr,
-                            double* rho, const int* stop, cudaStream_t s) {
+iim_status launch_ring_conv(int nx, int ny, const double* G, int ld, int sym, const double* bnd, const double* vl,
+                            const double* vr, double* rho, const int* stop, cudaStream_t s) {
     const double nsrc = 2.0 * (nx - 1) + 2.0 * (ny - 1);
-    launch("free_ring_conv", 0.0, 2.0 * nsrc * 2.0 * (nx + ny), k_ring_conv<256>, 2 * (nx + ny), 256, 0, s, nx, ny, G,
-           bnd, vl, vr, rho, stop);
+    launch("free_ring_conv", 0.0, (sym ? 4.0 : 2.0) * nsrc * 2.0 * (nx + ny), k_ring_conv<256>, 2 * (nx + ny), 256, 0, s,
+           nx, ny, G, ld, sym, bnd, vl, vr, rho, stop);
     IIM_LAUNCHED();
     return IIM_OK;
 }
@@ -281,10 +308,11 @@ iim_status launch_ring_add(int n, double a, const double* x, double* y, const in
     return IIM_OK;
 }
 
-iim_status launch_ring_residual(int nx, int ny, double h, const double* G, const double* psi, const double* ring,
-                                double* rres, double* res2, cudaStream_t s) {
+iim_status launch_ring_residual(int nx, int ny, double h, const double* G, int ld, int sym, const double* plane,
+                                const double* psi, const double* ring, double* rres, double* res2, cudaStream_t s) {
     const int n = 2 * (nx + ny);
-    launch("free_ring_residual", 0.0, 0.0, k_ring_residual<256>, n, 256, 0, s, nx, ny, G, psi, ring, rres);
+    launch("free_ring_residual", 0.0, 0.0, k_ring_residual<256>, n, 256, 0, s, nx, ny, h * h, G, ld, sym, plane, psi,
+           ring, rres);
     launch("free_ring_res_norm", 0.0, 0.0, k_ring_res_norm<256>, 1, 256, 0, s, n, (const double*)rres,
            1.0 / (h * h * h * h), res2);
     IIM_LAUNCHED();

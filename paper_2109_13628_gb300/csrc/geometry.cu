@@ -651,7 +651,7 @@ void free_geometry(iim_geometry g) {
                     g->lam_x32, g->lam_y32, g->sc32_delta, g->sc64_delta, g->sc32_rowoff, g->sc32_lim, g->sc64_rowoff, g->sc64_lim,
                     g->sc32_dstar, g->sc64_dstar, g->sc32_par, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
                     g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf,
-                    g->pc_aug, g->pc_S, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
+                    g->pc_aug, g->pc_S, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->fs_plane, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
     for (void* p : ptrs) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);

@@ -778,8 +778,9 @@ struct Solver {
                circ_ids_d, gamma, ih2, small, small + SM_REG, g->bvec ? g->bvec + g->na : nullptr, small + SM_RES2);
         IIM_LAUNCHED();
         if (g->outer)   // free space: the ring rows (freespace.cu), kept for the next recovery
-            IIM_CHECK(launch_ring_residual(g->nx, g->ny, g->h, g->lgf, g->psi_ext, g->fs_ring, g->fs_rres,
-                                           small + SM_RES2, s));
+            IIM_CHECK(launch_ring_residual(g->nx, g->ny, g->h, g->lgf, g->lgf_ld, g->outer == 2,
+                                           g->outer == 2 && !g->plane_off ? g->fs_plane : nullptr, g->psi_ext,
+                                           g->fs_ring, g->fs_rres, small + SM_RES2, s));
         return IIM_OK;
     }
 
@@ -830,7 +831,8 @@ struct Solver {
         IIM_CHECK(launch_bnd_cols<T>(NX, NY, g->nx, (const T*)g->tbuf, bnd + 2 * NX, bnd + 2 * NX + NY, stop, s));
         IIM_CHECK((rows_inv<T, INV_STORE_F64>(p, 0, 1, (const T*)g->tbuf, nullptr, bnd, 0, 0, nullptr, stop, s)));
         IIM_CHECK((rows_inv<T, INV_STORE_F64>(p, NY - 1, 1, (const T*)g->tbuf, nullptr, bnd, 0, NX, nullptr, stop, s)));
-        return launch_ring_conv(g->nx, g->ny, g->lgf, bnd, bnd + 2 * NX, bnd + 2 * NX + NY, g->fs_rho, stop, s);
+        return launch_ring_conv(g->nx, g->ny, g->lgf, g->lgf_ld, g->outer == 2, bnd, bnd + 2 * NX, bnd + 2 * NX + NY,
+                                g->fs_rho, stop, s);
     }
 
     // ---- free space: the box solve of a zero source with box data fs_rho (the harmonic part),
@@ -1039,6 +1041,9 @@ struct Solver {
         if (g->outer) IIM_CHECK(free_ring<T>(p, nullptr));
         IIM_CHECK((rows_inv<T, INV_STORE_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
         if (g->outer) {
+            // the harmonic part of the correction carries rho minus the ring rows of the residual,
+            // as in the recovery below, so that the right-hand side sees the ring data and error
+            IIM_CHECK(launch_ring_add(2 * (g->nx + g->ny), -1.0, g->fs_rres, g->fs_rho, nullptr, s));
             IIM_CHECK(free_harmonic<T>(p, g->jo0, g->jo1, nullptr));
             IIM_CHECK((rows_inv<T, INV_ACCUM_T>(p, g->jo0, g->jo1 - g->jo0 + 1, tb, pt, nullptr, 0, 0, nullptr, nullptr, s)));
         }
@@ -1490,6 +1495,7 @@ static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaSt
     iim_opts o = opts;
     o.rtol = std::min(opts.rtol, 1e-11);
     o.guess = 0;
+    g->plane_off = 1;   // the responses carry no data: no plane sources (host-driven solves)
     for (int l = 0; l < nc && st == IIM_OK; ++l) {
         std::fill(hg.begin(), hg.end(), 0.0);
         hg[g->circ_ids[l]] = 1.0;
@@ -1520,6 +1526,7 @@ static iim_status build_capacitance(iim_geometry g, const iim_opts& opts, cudaSt
             pbv[(size_t)l * nc + k] = hp[g->circ_ids[k]];
         }
     }
+    g->plane_off = 0;
     cudaFree(w0); cudaFree(out); cudaFree(pb0); cudaFree(gam); cudaFree(pbar);
     if (st != IIM_OK) return st;
     // invert C (close to the identity) by Gauss-Jordan with partial pivoting
@@ -1841,15 +1848,24 @@ extern "C" iim_status iim_geometry_set_lines(iim_geometry g, int threads_per_lin
 }
 
 extern "C" iim_status iim_geometry_set_outer(iim_geometry g, int outer) {
-    if (!g || (outer != 0 && outer != 1)) return IIM_ERR_INVALID_ARG;
+    if (!g || outer < 0 || outer > 2) return IIM_ERR_INVALID_ARG;
     if (g->outer == outer) return IIM_OK;
     int cur = 0;
     IIM_TRY(cudaGetDevice(&cur));
     IIM_TRY(cudaSetDevice(g->device));
     iim_status st = IIM_OK;
-    if (outer == 1) {
+    if (outer >= 1) {
         const size_t nring = 2 * (size_t)(g->nx + g->ny), nbnd = 2 * (size_t)(g->NX + g->NY);
-        if (!g->lgf) st = lgf_table(g->nx, g->ny, &g->lgf);
+        const int M = outer == 2 ? 2 * g->nx : g->nx;   // table columns: with the plane, the images too
+        st = lgf_table(M, g->ny, &g->lgf);
+        if (st == IIM_OK) g->lgf_ld = M + 1;
+        if (st == IIM_OK && !g->fs_plane) {
+            if (cudaMalloc(&g->fs_plane, sizeof(double) * (size_t)g->NY) != cudaSuccess ||
+                cudaMemset(g->fs_plane, 0, sizeof(double) * (size_t)g->NY) != cudaSuccess) {
+                record_cuda_error(cudaGetLastError(), "free-space buffers", __FILE__, __LINE__);
+                st = IIM_ERR_CUDA;
+            }
+        }
         if (st == IIM_OK && !g->fs_ring) {
             if (cudaMalloc(&g->fs_ring, sizeof(double) * nring) != cudaSuccess ||
                 cudaMalloc(&g->fs_rho, sizeof(double) * nring) != cudaSuccess ||
@@ -1877,6 +1893,12 @@ extern "C" iim_status iim_geometry_set_outer(iim_geometry g, int outer) {
     }
     cudaSetDevice(cur);
     return st;
+}
+
+extern "C" iim_status iim_geometry_set_plane_vorticity(iim_geometry g, const double* w, iim_stream stream) {
+    if (!g || !w || g->outer != 2 || !g->fs_plane) return IIM_ERR_INVALID_ARG;
+    IIM_TRY(cudaMemcpyAsync(g->fs_plane, w, sizeof(double) * (size_t)g->NY, cudaMemcpyDefault, (cudaStream_t)stream));
+    return IIM_OK;
 }
 
 extern "C" iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stream) {
