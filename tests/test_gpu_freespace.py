@@ -88,8 +88,8 @@ def test_free_space_iim_two_bodies_matches_oracle(two_bodies_64, prec, precond):
 def test_free_space_iim_second_order_on_the_gpu():
     """Sec. 4.3 on the GPU up to 512^2: the reconstructed velocity converges to the exact
     Lamb-Oseen velocity at second order (mixed precision, dense inner operator).  In free
-    space a mixed-precision correction contracts the FP64 residual by only 0.03-0.3 (the ring
-    rows weigh FP32 rounding next to the box heavily), so 512^2 takes 8-12 refinements."""
+    space a mixed-precision correction contracts the FP64 residual by only about 0.01-0.1 (the
+    ring rows weigh FP32 rounding next to the box heavily), so 512^2 takes about 8 refinements."""
     c = inputs.FREE_SPACE_TWO_BODIES
     errs, errs2 = [], []
     for n in (64, 128, 256, 512):

@@ -94,11 +94,14 @@ def test_krylov_seed_from_exact_solution():
         assert (psi1 - psi).abs().max().item() <= 1e-8 * psi.abs().max().item()
 
 
-def test_learned_guess_gain_on_unseen_problems():
+def test_learned_guess_on_unseen_problems():
     """Trained on the method's own solves (64^2, grid symmetries as augmentation), evaluated on
-    unseen problems: Krylov iterations of the first correction (the one the seed starts) with
-    the learned guess vs from zero.  The seed is scaled to minimise its residual, so it never
-    starts above ||b||."""
+    unseen problems.  What the trained net gives, asserted as measured: its seed lowers the
+    first correction's starting residual (0.73 of ||b|| on average in the last GPU run, against
+    1 from zero; the seed is scaled to minimise that residual, so it never starts above ||b||),
+    and the solve still meets the FP64 target.  It does not save Krylov iterations (17.3 per
+    first correction against 17.7 from zero and 16.8 from the body-free box solve in that run):
+    the iterations are printed, not asserted."""
     dev = torch.device("cuda", 0)
     data = learned.make_dataset(96, 64, 1000, dev)
     net = learned.Net(seed=5)
@@ -125,5 +128,5 @@ def test_learned_guess_gain_on_unseen_problems():
         k += 1
     print(f"first-correction iterations: zero guess {np.mean(it0):.1f}, body-free box solve {np.mean(itb):.1f}, "
           f"learned guess {np.mean(it1):.1f}; learned seed residual / ||b|| {np.mean(seeds):.3f}")
-    assert np.mean(it1) <= np.mean(it0) + 1.0
+    assert np.mean(seeds) < 0.9
     net.close()
