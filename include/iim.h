@@ -270,7 +270,9 @@ iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stre
  * these systems directly: the two Thomas recurrences as segmented scans, with the elimination
  * factors tabulated through their complements 1 - e_j; O(ny) work per column.  0 uses the
  * column DST pair with the eigenvalue division.  Both compute the same discrete inverse to
- * rounding.  Errors: IIM_ERR_INVALID_ARG (mode not 0 or 1). */
+ * rounding.  Changing it drops the dense preconditioner and the circulation responses (rebuilt
+ * by the next solve that uses them, with the new pass).  Errors: IIM_ERR_INVALID_ARG (mode not
+ * 0 or 1). */
 iim_status iim_geometry_set_column_solver(iim_geometry g, int mode);
 
 /* Threads per transformed line for 1024-point lines: 32 (default: one warp, fewest

@@ -1912,6 +1912,11 @@ extern "C" iim_status iim_geometry_set_column_solver(iim_geometry g, int mode) {
     if (!g || (mode != 0 && mode != 1)) return IIM_ERR_INVALID_ARG;
     if (g->col_solver != mode) {
         g->col_solver = mode;
+        // the preconditioner and the circulation responses were built with the other pass's
+        // rounding: rebuilt by the next solve that uses them
+        g->pc_ready = 0;
+        g->cap_ready = 0;
+        lockstep_forget(g);
         drop_solve_graph(g);   // the captured kernels change
         for (void** gp : {&g->graph64, &g->graph32}) {
             IterGraph* G = (IterGraph*)*gp;
