@@ -707,10 +707,10 @@ def main():
         return iim.default_opts(prec=prec, rtol=RTOL, restart=args.restart, precond=use_pc,
                                 inner_rtol=args.inner_rtol if inner is None else inner)
 
-    def solve(prec, inner=None, pc=None):
+    def solve(prec, inner=None, pc=None, on=None):
         # the plain FP64 comparator is the unpreconditioned paper iteration
-        return iim.iim_poisson_solve(geo, omega, psi_b, ring, None, psibars[0], psis[0], uxs[0], uys[0],
-                                     opts=opts_for(prec, inner, pc))
+        return iim.iim_poisson_solve(geo if on is None else on, omega, psi_b, ring, None, psibars[0], psis[0], uxs[0],
+                                     uys[0], opts=opts_for(prec, inner, pc))
 
     def solve_batch(n_streams):
         return iim.iim_poisson_solve_batched(geos, [omega] * B, [psi_b] * B, [ring] * B, None, psibars, psis, uxs, uys,
@@ -796,23 +796,25 @@ def main():
     single = args.steps / (sum(ms1) * 1e-3)
     # ---- plain FP64 iteration (the comparator: unpreconditioned, one problem at a time), at its
     # loosest Krylov tolerance that still ends at the same FP64 residual target (no over-solve)
-    # (FP64 legs on their fastest column pass, the tridiagonal scans)
-    iim.iim_geometry_set_column_solver(geo, 1)
-    inner64, calib64 = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 0), PLAIN_INNER)
+    # (FP64 legs on a geometry of their own with their fastest column pass, the tridiagonal scans)
+    geo64 = iim.iim_setup_geometry(grid, T(P.phi), P.regions, P.modes)
+    iim.iim_geometry_set_column_solver(geo64, 1)
+    inner64, calib64 = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 0, geo64), PLAIN_INNER)
     k64 = max(3, args.steps // 5)
-    ms64, stats64 = timed(lambda: solve(iim.IIM_FP64, inner64, 0), k64, 2)
+    ms64, stats64 = timed(lambda: solve(iim.IIM_FP64, inner64, 0, geo64), k64, 2)
     plain = k64 / (sum(ms64) * 1e-3)
     # ---- FP64 transforms with the same dense preconditioner (isolates the mixed-precision gain)
     inner64p, calib64p = (None, None)
     fp64_pc = None
     if precond:
-        inner64p, calib64p = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 1), PLAIN_INNER)
-        msp, statsp = timed(lambda: solve(iim.IIM_FP64, inner64p, 1), k64, 2)
+        iim.iim_build_preconditioner(geo64)
+        inner64p, calib64p = calibrate_inner(lambda inner: solve(iim.IIM_FP64, inner, 1, geo64), PLAIN_INNER)
+        msp, statsp = timed(lambda: solve(iim.IIM_FP64, inner64p, 1, geo64), k64, 2)
         fp64_pc = {"value": k64 / (sum(msp) * 1e-3), "unit": UNIT, "ms_per_solve": sum(msp) / k64,
                    "inner_rtol": inner64p, "krylov_iters": statistics.mean(s["iters"] for s in statsp),
                    "refinements": statistics.mean(s["refinements"] for s in statsp),
                    "final_rel_res": max(s["rel_res"] for s in statsp), "calibration": calib64p}
-    iim.iim_geometry_set_column_solver(geo, col_mode)
+    geo64.close()
     # ---- lockstep off: one whole-solve graph per problem on the tuned streams (same B solves)
     per_problem = None
     if B > 1:
@@ -993,7 +995,7 @@ def main():
                              "right-hand side and recovery)" if precond == 3 else "")),
                    "parallelism": f"replicas x{ws}"},
         "single_problem": {"value": single, "unit": UNIT, "ms_per_solve": sum(ms1) / len(ms1)},
-        "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": sum(ms64) / k64,
+        "plain_fp64": {"value": plain, "unit": UNIT, "ms_per_step": sum(ms64) / k64, "column_pass": "tridiagonal scans",
                        "krylov_iters": statistics.mean(s["iters"] for s in stats64),
                        "refinements": statistics.mean(s["refinements"] for s in stats64),
                        "final_rel_res": max(s["rel_res"] for s in stats64), "inner_rtol": inner64,
