@@ -35,10 +35,19 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
             "fixed-psibar body, solve to un-reduced FP64 relative residual 1e-10")
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
-NCU_TRAFFIC = {"dst_cols_f32": {"bytes_per_launch": 2722200, "l2_bytes_per_launch": 11776011, "launches": 32,
-                                 "tile_width": 8, "source_hash": "9c414c1750de1e6b",
-                                 "note": "mean over the 32 column-pass launches of two profiled solves, caches "
-                                         "flushed by ncu before each launch"}}
+NCU_TRAFFIC = {
+    # python -m paper_2109_13628_gb300.passes --n 1024 --col 0 --batch 40 under ncu --set full
+    # (-k regex:k_cols -c 1): 40 fields in one launch, DRAM 167.7 MB read + 111.5 MB written, L2
+    # (requests from the SMs) 15.70 M read + 5.24 M write sectors; scaled by the fields to the
+    # roofline's launch of 95 fields
+    "dst_cols_f32": {"bytes_per_launch": 279203840 / 40 * 95, "l2_bytes_per_launch": 20934584 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "9efd3db833065476",
+                     "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
+    # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 111.9 MB, L2 11.03 M + 5.24 M
+    "tri_cols_f32": {"bytes_per_launch": 279616768 / 40 * 95, "l2_bytes_per_launch": 16271334 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "9efd3db833065476",
+                     "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
+}
 
 
 L2_BYTES = 126 * 1024 * 1024
