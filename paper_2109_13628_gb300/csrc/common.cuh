@@ -59,6 +59,11 @@ constexpr int kTwN = 1 << kTwLog;
 iim_status ensure_twiddles();                 // for the current device
 const cpx<double>* twiddles64();              // device address, current device
 const cpx<float>* twiddles32();
+// Twiddle region of the DST kernels for lines of n points on FFT path fp (dst.cuh, tw_region
+// entries: the full half table, then the path's stage tables), in global memory of the current
+// device, built by ensure_twiddles for every n = 16..4096.
+template <typename T>
+const cpx<T>* twiddle_region(int n, int fp);
 
 // ------------------------------------------------------------------------- node classes
 enum : uint8_t { CLS_FLUID = 0, CLS_PLUS = 1, CLS_MINUS = 2, CLS_SOLID = 3 };

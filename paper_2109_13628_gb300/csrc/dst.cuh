@@ -557,6 +557,27 @@ struct VecArg {
     }
 };
 
+// Twiddles of a block: the register paths (n = 512, 1024) read the region table straight from
+// global memory (L1-cached; fewer shared-memory bytes per block, more blocks per SM); the
+// Stockham path (other n) copies it into the first tw_region(n) entries of shared memory (its
+// per-pass tables are read with strided indices that L1 serves poorly).  Returns the table the
+// transforms read; the caller synchronises the block before using a staged copy.
+template <int FP, typename T>
+__device__ __forceinline__ const cpx<T>* block_twiddles(unsigned char* smem, const cpx<T>* __restrict__ twr, int n) {
+    if constexpr (FP != 0) {
+        return twr;
+    } else {
+        cpx<T>* st = reinterpret_cast<cpx<T>*>(smem);
+        for (int k = threadIdx.x; k < tw_region(n); k += blockDim.x) st[k] = twr[k];
+        return st;
+    }
+}
+// Shared-memory bytes the twiddles take in front of the lines.
+template <typename T>
+__host__ __device__ constexpr size_t twiddle_smem(int n, int fp) {
+    return fp == 0 ? (size_t)tw_region(n) * sizeof(cpx<T>) : 0;
+}
+
 // Per-line scratch for the 64-thread path's prefix sum (16 values per line).
 constexpr int kLineScratch = 16;
 
@@ -573,14 +594,13 @@ rows_fwd_body(int NX, int NY, int n, int logn, int row0, int nrows, const double
               T* __restrict__ out) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
-    T* lines = reinterpret_cast<T*>(s_tw + tw_region(n));
+    T* lines = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));
     T* b0 = lines + (size_t)grp * (2 * n);
     T* b1 = b0 + n;
     T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
-    load_twiddles<FP>(s_tw, g_tw, n, logn);
-    __syncthreads();
+    if (FP == 0) __syncthreads();
     const int r = row0 + blockIdx.x * LPB + grp;
     if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
     if (dense && dld == n && doff == 1) {
@@ -641,17 +661,16 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
           const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);   // synchronised with the tile below
     constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
     const int stride = 2 * n + PAD;
-    T* s_lam = reinterpret_cast<T*>(s_tw + tw_region(n));   // lam_y, NY values
+    T* s_lam = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));   // lam_y, NY values
     T* lines = s_lam + n;
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
     T* tot = lines + (size_t)C * stride + grp * kLineScratch;
     const int ld = NX + 1;
     const int col0 = blockIdx.x * C;   // padded column index
     constexpr int nthr = C * TN;
-    load_twiddles<FP>(s_tw, g_tw, n, logn);
     for (int l = threadIdx.x; l < NY; l += nthr) s_lam[l] = lam_y[l];
     // tile load: C consecutive padded columns of rows [in0, in1]; rows outside are zero
     constexpr int V = 16 / sizeof(T);
@@ -719,7 +738,7 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
 }
 
 template <typename T, int C, int FP>
-__global__ void __launch_bounds__(C * line_threads(FP))
+__global__ void __launch_bounds__(C * line_threads(FP), sizeof(T) == 4 ? 2 : 1)
 k_cols(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
        const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw,
        const int* __restrict__ stop, long fstride) {
@@ -743,14 +762,13 @@ rows_inv_body(int NX, int NY, int n, int logn, int row0, int nrows, const T* __r
               const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cpx<T>* s_tw = reinterpret_cast<cpx<T>*>(smem_raw);
+    const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
-    T* lines = reinterpret_cast<T*>(s_tw + tw_region(n));
+    T* lines = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));
     T* b0 = lines + (size_t)grp * (2 * n);
     T* b1 = b0 + n;
     T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
-    load_twiddles<FP>(s_tw, g_tw, n, logn);
-    __syncthreads();
+    if (FP == 0) __syncthreads();
     const int r = row0 + blockIdx.x * LPB + grp;
     if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
     load_row_vec<T, TN>(b0, in + (size_t)r * n, n, tid);

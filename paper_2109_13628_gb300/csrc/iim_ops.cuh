@@ -37,13 +37,13 @@ constexpr int cols_per_block() { return 4; }
 constexpr int kRowWarps = 4;
 
 template <typename T>
-inline size_t rows_smem(int n) {
-    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)kRowWarps * (2 * n + kLineScratch) * sizeof(T);
+inline size_t rows_smem(int n, bool wide = false) {
+    return twiddle_smem<T>(n, fft_path(n, wide)) + (size_t)kRowWarps * (2 * n + kLineScratch) * sizeof(T);
 }
 template <typename T>
-inline size_t cols_smem(int n, int C = cols_per_block<T>()) {
+inline size_t cols_smem(int n, int C = cols_per_block<T>(), bool wide = false) {
     const int pad = sizeof(T) == 4 ? 4 : 2;
-    return (size_t)tw_region(n) * sizeof(cpx<T>) + (size_t)n * sizeof(T) +
+    return twiddle_smem<T>(n, fft_path(n, wide)) + (size_t)n * sizeof(T) +
            (size_t)C * (2 * n + pad + kLineScratch) * sizeof(T);
 }
 // Rows per block of the row passes for lines of n points.

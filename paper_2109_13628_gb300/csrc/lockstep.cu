@@ -108,7 +108,7 @@ kb_rows_fwd(const LsProb* __restrict__ P, int mode, int gate, const cpx<T>* __re
 }
 
 template <typename T, int C, int FP>
-__global__ void __launch_bounds__(C * line_threads(FP))
+__global__ void __launch_bounds__(C * line_threads(FP), sizeof(T) == 4 ? 2 : 1)
 kb_cols(const LsProb* __restrict__ P, int mode, int gate, T norm, const cpx<T>* __restrict__ tw) {
     const LsProb& p = P[blockIdx.z];
     if (ls_off(p, gate) || (mode != M_RECOVER && p.na == 0)) return;
@@ -588,7 +588,7 @@ struct LsEmit {
             IIM_CHECK(allow_smem(kern, sm));
             launch(sizeof(T) == 8 ? "ls_rows_fwd_f64" : "ls_rows_fwd_f32", bytes, 0.0, kern,
                    grid((rows + rpb - 1) / rpb), kRowWarps * 32, sm, s, (const LsProb*)G->d_probs, mode, gate,
-                   sizeof(T) == 8 ? (const cpx<T>*)twiddles64() : (const cpx<T>*)twiddles32());
+                   twiddle_region<T>(G->nx, fft_path(G->nx, G->wide)));
             return IIM_OK;
         };
         const int fp = fft_path(G->nx, G->wide);
@@ -615,8 +615,7 @@ struct LsEmit {
             IIM_CHECK(allow_smem(kern, sm));
             launch(sizeof(T) == 8 ? "ls_cols_f64" : "ls_cols_f32", bytes, 0.0, kern,
                    dim3(G->nx / C, 1, G->n()), C * line_threads(fft_path(G->ny, G->wide)), sm, s,
-                   (const LsProb*)G->d_probs, mode, gate, norm,
-                   sizeof(T) == 8 ? (const cpx<T>*)twiddles64() : (const cpx<T>*)twiddles32());
+                   (const LsProb*)G->d_probs, mode, gate, norm, twiddle_region<T>(G->ny, fft_path(G->ny, G->wide)));
             return IIM_OK;
         };
         const int fp = fft_path(G->ny, G->wide);
@@ -670,7 +669,7 @@ struct LsEmit {
             IIM_CHECK(allow_smem(kern, sm));
             launch(sizeof(T) == 8 ? "ls_rows_inv_f64" : "ls_rows_inv_f32", bytes, 0.0, kern,
                    grid((rows + rpb - 1) / rpb), kRowWarps * 32, sm, s, (const LsProb*)G->d_probs, gate,
-                   sizeof(T) == 8 ? (const cpx<T>*)twiddles64() : (const cpx<T>*)twiddles32());
+                   twiddle_region<T>(G->nx, fft_path(G->nx, G->wide)));
             return IIM_OK;
         };
         const int fp = fft_path(G->nx, G->wide);

@@ -42,10 +42,49 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
 __device__ cpx<double> g_tw64[kTwN];
 __device__ cpx<float> g_tw32[kTwN];
 
+// Twiddle regions of the DST kernels, one per line length n = 2^4..2^12 (the one-warp path of
+// that length) plus the 64-thread path of n = 1024: read by the kernels from global memory
+// (L1-cached) instead of a copy in every block's shared memory.
+constexpr int twr_slot(int logn, bool wide) { return wide ? 9 : logn - 4; }
+constexpr int kTwrSlots = 10;
+constexpr long twr_total() {
+    long t = 0;
+    for (int l = 4; l <= kTwLog; ++l) t += tw_region(1 << l);
+    return t + tw_region(1024);
+}
+__device__ cpx<double> g_twr64[twr_total()];
+__device__ cpx<float> g_twr32[twr_total()];
+
+template <typename T, int FP>
+__global__ void k_twiddle_region(const cpx<T>* __restrict__ g_tw, int n, int logn, cpx<T>* __restrict__ out) {
+    load_twiddles<FP>(out, g_tw, n, logn);
+}
+
 static std::mutex g_tw_mutex;
 static bool g_tw_ready[64];
 static const cpx<double>* g_tw64_addr[64];
 static const cpx<float>* g_tw32_addr[64];
+static const cpx<double>* g_twr64_addr[64][kTwrSlots];
+static const cpx<float>* g_twr32_addr[64][kTwrSlots];
+
+template <typename T>
+static iim_status fill_regions(const cpx<T>* base, cpx<T>* regions, const cpx<T>** addr) {
+    long off = 0;
+    for (int slot = 0; slot < kTwrSlots; ++slot) {
+        const bool wide = slot == 9;
+        const int logn = wide ? 10 : slot + 4, n = 1 << logn;
+        const int fp = fft_path(n, wide);
+        cpx<T>* out = regions + off;
+        if (fp == 64) k_twiddle_region<T, 64><<<1, 256>>>(base, n, logn, out);
+        else if (fp == 16) k_twiddle_region<T, 16><<<1, 256>>>(base, n, logn, out);
+        else if (fp == 8) k_twiddle_region<T, 8><<<1, 256>>>(base, n, logn, out);
+        else k_twiddle_region<T, 0><<<1, 256>>>(base, n, logn, out);
+        IIM_TRY(cudaGetLastError());
+        addr[slot] = out;
+        off += tw_region(n);
+    }
+    return IIM_OK;
+}
 
 iim_status ensure_twiddles() {
     int dev = 0;
@@ -68,8 +107,28 @@ iim_status ensure_twiddles() {
     IIM_TRY(cudaGetSymbolAddress(&p32, g_tw32));
     g_tw64_addr[dev] = (const cpx<double>*)p64;
     g_tw32_addr[dev] = (const cpx<float>*)p32;
+    void* r64 = nullptr;
+    void* r32 = nullptr;
+    IIM_TRY(cudaGetSymbolAddress(&r64, g_twr64));
+    IIM_TRY(cudaGetSymbolAddress(&r32, g_twr32));
+    IIM_CHECK(fill_regions<double>(g_tw64_addr[dev], (cpx<double>*)r64, g_twr64_addr[dev]));
+    IIM_CHECK(fill_regions<float>(g_tw32_addr[dev], (cpx<float>*)r32, g_twr32_addr[dev]));
+    IIM_TRY(cudaDeviceSynchronize());
     g_tw_ready[dev] = true;
     return IIM_OK;
+}
+
+template <>
+const cpx<double>* twiddle_region<double>(int n, int fp) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_twr64_addr[dev][twr_slot(ilog2(n), fp == 64)];
+}
+template <>
+const cpx<float>* twiddle_region<float>(int n, int fp) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return g_twr32_addr[dev][twr_slot(ilog2(n), fp == 64)];
 }
 
 const cpx<double>* twiddles64() {
@@ -97,7 +156,8 @@ static iim_status rows_fwd(const Plan<T>& p, int row0, int nrows, const double* 
                (double)nrows * p.NX * ((dense ? 8.0 : 0.0) + sizeof(T)), (double)nrows * dst_flops(p.nx), kern,
                (nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), kRowWarps * 32, sm, s, p.NX,
                p.NY, p.nx,
-               p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign, p.tw, out, stop);
+               p.lognx, row0, nrows, dense, dld, doff, ring, ih2, row_ptr, aff_node, gam, gsign,
+               twiddle_region<T>(p.nx, fft_path(p.nx, p.wide)), out, stop);
         return IIM_OK;
     };
     const int fp = fft_path(p.nx, p.wide);
@@ -171,7 +231,8 @@ static iim_status cols_tile(const Plan<T>& p, int in0, int in1, int out0, int ou
                (double)batch * (in1 - in0 + 1 + out1 - out0 + 1) * p.NX * sizeof(T),
                (double)batch * p.NX * (2.0 * dst_flops(p.ny) + 2.0 * p.NY), kern, dim3(p.nx / C, batch),
                C * line_threads(fft_path(p.ny, p.wide)), sm, s,
-               p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm, p.tw, stop, fstride);
+               p.NX, p.NY, p.ny, p.logny, in0, in1, out0, out1, buf, p.lam_x, p.lam_y, p.norm,
+               twiddle_region<T>(p.ny, fft_path(p.ny, p.wide)), stop, fstride);
         return IIM_OK;
     };
     const int fp = fft_path(p.ny, p.wide);
@@ -196,7 +257,8 @@ static iim_status rows_inv(const Plan<T>& p, int row0, int nrows, const T* in, T
                    (sizeof(T) + (MODE == INV_STORE_T ? sizeof(T) : MODE == INV_STORE_F64 ? 8.0 : 17.0)),
                (double)batch * nrows * dst_flops(p.nx), kern,
                dim3((nrows + rows_per_block(p.nx, p.wide) - 1) / rows_per_block(p.nx, p.wide), batch),
-               kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls, p.tw,
+               kRowWarps * 32, sm, s, p.NX, p.NY, p.nx, p.lognx, row0, nrows, in, outT, out64, old, ooff, cls,
+               twiddle_region<T>(p.nx, fft_path(p.nx, p.wide)),
                stop, fstride);
         return IIM_OK;
     };
