@@ -223,7 +223,7 @@ def orders(errs, key):
 def test_lamb_oseen_cylinder_second_order():
     """Sec. 6.1: velocity (max and L2) and vorticity (L2) errors fall at second order from
     256^2 to 512^2 (t = 1 -> 1.05).  The vorticity's max error sits in the first cells off the
-    wall and falls at about 1.5 with this build's reading of the wall-vorticity stencils (their
+    wall and falls at about 1.5 with the reading of the wall-vorticity stencils used here (their
     figure is missing from the paper; the paper reports second order), which the last bound
     records."""
     errs = [lamb_oseen_run(n, 1.05) for n in (256, 512)]

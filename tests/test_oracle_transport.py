@@ -206,7 +206,7 @@ def test_rk3_stage_times_integrate_quadratics_exactly():
 
 
 def test_vorticity_bc_second_order_with_exact_velocity():
-    """Sec. 5.3 stencils (this build's reading of the missing figure): fed the exact Lamb-Oseen
+    """Sec. 5.3 stencils (the reading of the missing figure used here): fed the exact Lamb-Oseen
     velocity around the Sec. 6.1 cylinder (extended into the body with u_b as the transport
     step does), the wall vorticity converges at second order at every control point."""
     c = inputs.LAMB_OSEEN_CYLINDER
