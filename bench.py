@@ -37,15 +37,15 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
 # the kernel source hash below (null otherwise).
 NCU_TRAFFIC = {
     # python -m paper_2109_13628_gb300.passes --n 1024 --col 0 --batch 40 under ncu --set full
-    # (-k regex:k_cols -c 1): 40 fields in one launch, DRAM 167.7 MB read + 111.5 MB written, L2
-    # (requests from the SMs) 15.70 M read + 5.24 M write sectors; scaled by the fields to the
+    # (-k regex:k_cols -c 1): 40 fields in one launch, DRAM 167.7 MB read + 111.9 MB written, L2
+    # (requests from the SMs) 12.75 M read + 5.24 M write sectors; scaled by the fields to the
     # roofline's launch of 95 fields
-    "dst_cols_f32": {"bytes_per_launch": 279203840 / 40 * 95, "l2_bytes_per_launch": 20934584 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "9efd3db833065476",
+    "dst_cols_f32": {"bytes_per_launch": 279548160 / 40 * 95, "l2_bytes_per_launch": 17989366 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "1acf6ddd786067bd",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
-    # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 111.9 MB, L2 11.03 M + 5.24 M
-    "tri_cols_f32": {"bytes_per_launch": 279616768 / 40 * 95, "l2_bytes_per_launch": 16271334 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "9efd3db833065476",
+    # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 111.8 MB, L2 11.04 M + 5.24 M
+    "tri_cols_f32": {"bytes_per_launch": 279469824 / 40 * 95, "l2_bytes_per_launch": 16279091 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "1acf6ddd786067bd",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
 }
 
