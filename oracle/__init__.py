@@ -19,6 +19,12 @@ Modules
                  form, circulation, velocity, residual
   transport      Sec. 3, Sec. 5.1, 5.3, 5.5, App. B: vorticity BC, conservative transport
                  RHS, Kelvin ODE, low-storage RK3, stable time step
+  lgf            Sec. 4.1 / 4.2: lattice Green's function of the five-point Laplacian (the
+                 free-space rectangular solve)
+  forces         App. C: control-volume force and moment
+  net            the learned initial guess's convolution network, its loss and gradients
+  pressure       Sec. 5.4: total-pressure Poisson problem -- right-hand side, Neumann wall
+                 datum, the IIM solve with the Neumann extrapolation (Sec. 2.1), surface values
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py.  The vorticity
 boundary condition stencils (Sec. 5.3) are a reading of a figure missing from the paper; they

@@ -8,6 +8,10 @@ stencil discussion).  A direction is usable only when all its fluid nodes exist 
 crossing another control point (Sec. 2.2, nonconvex fallback); the ghost is the plain mean
 over usable directions (Sec. 2.2, averaging).  Degree p-1 gives an extension of order p.
 The variant without a boundary condition replaces x_alpha by x_i (Sec. 2.1, last variant).
+The Neumann variant (Sec. 2.1) keeps the same fluid nodes g+2d, g+3d, g+4d and replaces the
+boundary value by the derivative along the line at x_alpha: the cubic p with p(m) = f(g+md),
+m = 2, 3, 4, and p'(1 - t) = h * (d . grad f)(x_alpha), evaluated at g.  Its weights come from
+solving that 4 x 4 system for the monomial coefficients.
 
 Weights come from the Lagrange basis written out directly (independent of any Neville
 recursion).  Positions along the line are in units of h measured from g: the boundary point
@@ -99,6 +103,61 @@ def ghost_operator(geo, phi, degree=3, with_bc=True):
                 rows_b.append(r)
                 cols_b.append(c)
                 vals_b.append(wb * inv)
+            for qi, qj, wq in plist:
+                rows_p.append(r)
+                cols_p.append(qj * nx1 + qi)
+                vals_p.append(wq * inv)
+    n_minus = len(mi)
+    Gpsi = sp.csr_matrix((vals_p, (rows_p, cols_p)), shape=(n_minus, ny1 * nx1))
+    Gbc = sp.csr_matrix((vals_b, (rows_b, cols_b)), shape=(n_minus, len(cps["t"])))
+    return list(zip(mi.tolist(), mj.tolist())), Gpsi, Gbc, n_valid
+
+
+def hermite_weights(a, nodes=(2.0, 3.0, 4.0)):
+    """Weights (w_d, w_2, w_3, w_4) with p(0) = w_d p'(a) + sum_m w_m p(m) for every cubic p:
+    row 0 of the inverse of the system [p(m) = sum_k c_k m^k; p'(a) = sum_k k c_k a^(k-1)]."""
+    M = np.zeros((4, 4))
+    M[0] = [0.0, 1.0, 2.0 * a, 3.0 * a * a]
+    for r, m in enumerate(nodes):
+        M[1 + r] = [1.0, m, m * m, m ** 3]
+    return np.linalg.inv(M)[0]
+
+
+def ghost_operator_neumann(geo, phi, h):
+    """Ghost values at every A- node for a Neumann wall (Sec. 2.1, Neumann variant; Sec. 2.2
+    averaging), as sparse operators like ghost_operator.  The data at a control point is the
+    derivative along its grid line pointing into the fluid, d . grad f at x_alpha; the cubic's
+    derivative in units of h is h times it.  Usable directions: those of the degree-3 Dirichlet
+    stencil (g+2d, g+3d, g+4d fluid interior nodes)."""
+    solid = phi < 0
+    ny1, nx1 = phi.shape
+    cps = geo["cp"]
+    cmap = cp_index_map(cps, phi.shape)
+    mj, mi = np.nonzero(geo["minus"])
+    rows_p, cols_p, vals_p = [], [], []
+    rows_b, cols_b, vals_b = [], [], []
+    n_valid = np.zeros(len(mi), dtype=np.int64)
+    for r, (gi, gj) in enumerate(zip(mi.tolist(), mj.tolist())):
+        entries = []
+        for di, dj in DIRS:
+            if solid[gj + dj, gi + di]:
+                continue
+            axis = 0 if di != 0 else 1
+            c = cmap[(axis, min(gi, gi + di), min(gj, gj + dj))]
+            ok = all(1 <= gi + m * di <= nx1 - 2 and 1 <= gj + m * dj <= ny1 - 2 and not solid[gj + m * dj, gi + m * di]
+                     for m in (2, 3, 4))
+            if not ok:
+                continue
+            w = hermite_weights(1.0 - cps["t"][c])
+            entries.append((c, w[0] * h, [(gi + m * di, gj + m * dj, w[m - 1]) for m in (2, 3, 4)]))
+        if not entries:
+            raise UnderResolved(f"A- node ({gi},{gj}) has no usable extrapolation direction")
+        n_valid[r] = len(entries)
+        inv = 1.0 / len(entries)
+        for c, wb, plist in entries:
+            rows_b.append(r)
+            cols_b.append(c)
+            vals_b.append(wb * inv)
             for qi, qj, wq in plist:
                 rows_p.append(r)
                 cols_p.append(qj * nx1 + qi)

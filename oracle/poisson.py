@@ -184,16 +184,31 @@ def ring_residual(nodes, sym=False, plane=None, h=None):
 class Setup:
     """Geometry, ghost operators and index maps of one problem (Sec. 2.2, App. A)."""
 
-    def __init__(self, prob, degree=3):
+    def __init__(self, prob, degree=3, wall="dirichlet", wall_data=None):
+        """wall = "dirichlet": psi = psi_b + psibar_k on the bodies (Sec. 4.2).  wall = "neumann":
+        the Neumann variant of the extrapolation (Sec. 2.1, used by the total-pressure problem of
+        Sec. 5.4); the data at each control point is the derivative along its grid line into the
+        fluid (wall_data, else prob.psi_b_fn), every body has fixed mode and psibar = 0."""
         self.prob = prob
         g = prob.grid
         self.nx, self.ny, self.h = g.nx, g.ny, g.h
+        self.wall = wall
         self.geo = geom.process_geometry(g, prob.phi, prob.regions)
-        self.ghosts = ex.ghost_operator(self.geo, prob.phi, degree=degree, with_bc=True)
+        if wall == "dirichlet":
+            self.ghosts = ex.ghost_operator(self.geo, prob.phi, degree=degree, with_bc=True)
+        elif wall == "neumann":
+            if any(m != 0 for m in prob.modes):
+                raise ValueError("a Neumann wall has no circulation unknowns: every body must be fixed")
+            self.ghosts = ex.ghost_operator_neumann(self.geo, prob.phi, g.h)
+        else:
+            raise ValueError(wall)
         self.solid = prob.phi < 0
         cps = self.geo["cp"]
         self.cp_body = self.geo["cp_body"]
-        self.psi_b = np.asarray(prob.psi_b_fn(cps["x"], cps["y"], self.cp_body), dtype=np.float64)
+        if wall_data is not None:
+            self.psi_b = np.asarray(wall_data, dtype=np.float64)
+        else:
+            self.psi_b = np.asarray(prob.psi_b_fn(cps["x"], cps["y"], self.cp_body), dtype=np.float64)
         self.modes = list(prob.modes)
         self.nb = len(prob.regions)
         self.circ = [k for k in range(self.nb) if self.modes[k] == 1]
