@@ -148,6 +148,7 @@ iim_status iim_geometry_affected_points(iim_geometry g, int* node_i, int* node_j
  *   psi_box    box ring, or NULL for zero box data
  *   gamma      n_bodies values (entries of fixed-mode bodies ignored), or NULL for zeros
  *   psibar     n_bodies values: read for fixed bodies, written for circulation bodies
+ *              (ignored and may be NULL on a geometry in Neumann mode, iim_geometry_set_wall_condition)
  *   psi_out    interior array: fluid values, 0 in the solid
  *   ux_out, uy_out  interior arrays (0 in the solid), or NULL to skip the velocity
  *   psi_guess  interior array used when opts->guess is 1 or 2, else ignored (may be NULL)
@@ -275,6 +276,22 @@ iim_status iim_geometry_outer_ring(iim_geometry g, double* ring, iim_stream stre
  * 0 or 1). */
 iim_status iim_geometry_set_column_solver(iim_geometry g, int mode);
 
+/* Wall condition of the geometry's ghost stencils (Sec. 2.1).  0 (default): Dirichlet, the
+ * ghost at an A- node g along a usable direction d is the cubic through the crossing (carrying
+ * psi_b + psibar_k) and the fluid nodes g+2d, g+3d, g+4d, at g.  1: Neumann, the variant of
+ * Sec. 2.1 for a derivative condition: the cubic p through the same three fluid nodes whose
+ * derivative along the line at the crossing is the wall datum, at g; the ghost is again the
+ * mean over usable directions.  In Neumann mode the psi_b argument of the solves is that datum,
+ * d . grad u at each control point with d the unit grid direction from the solid node of the
+ * control point's edge to its fluid node (into the fluid); there are no body constants: the
+ * psibar arguments are ignored (read as zeros, never written; NULL is accepted).  This is the
+ * solve of the total-pressure problem of Sec. 5.4 (iim_total_pressure).  Requires every body in
+ * IIM_BODY_FIXED mode for kind 1.  The transport and vorticity-boundary kernels do not use these
+ * stencils (they keep their own Dirichlet extensions).  Changing it rewrites the stencils
+ * (synchronizes `stream`) and drops the preconditioner, circulation responses and solve graphs.
+ * Errors: IIM_ERR_INVALID_ARG (kind not 0 or 1, or kind 1 with a circulation body), IIM_ERR_CUDA. */
+iim_status iim_geometry_set_wall_condition(iim_geometry g, int kind, iim_stream stream);
+
 /* Threads per transformed line for 1024-point lines: 32 (default: one warp, fewest
  * instructions, best when many solves share the GPU) or 64 (two warps per line: lower latency
  * of one solve, about 6 % more instructions).  Other line lengths use one warp.  Errors:
@@ -373,6 +390,47 @@ iim_status iim_cv_terms(iim_geometry g, const double* psi, const double* ux, con
 iim_status iim_transport_rhs(iim_geometry g, const double* omega, const double* ux, const double* uy,
                              const double* u_b, const double Uinf[2], double nu, const double* omega_b_in,
                              double* omega_b_out, double* rhs_out, double* dgamma_out, iim_stream stream);
+
+/* The data of the total-pressure problem (Sec. 5.4) from a flow: H = (p - p_inf) +
+ * (|u|^2 - |u_inf|^2) / 2 solves nabla^2 H = div(u x omega k) (Eq. pressurepoisson) with a
+ * Neumann wall condition (Eq. totalpressurebc).
+ *   f_out      interior array: f = -div(u x omega k) = -(d_x(u_y omega) - d_y(u_x omega)) at fluid
+ *              nodes (the right-hand side of -nabla_h^2 H = f), centred differences of the
+ *              products; at A- nodes the third-order extensions (u with u_b, omega with omega_b),
+ *              at and beyond the box the box values of iim_transport_rhs (u = Uinf; omega 0,
+ *              copied from the last interior column at the right edge); 0 in the solid
+ *   data_out   |C| values: the wall datum of the Neumann stencils (iim_geometry_set_wall_condition),
+ *              d . grad H at each crossing.  On a stationary no-slip wall grad(|u|^2/2) =
+ *              (grad u)^T u vanishes and Eq. pressuregrad1 gives grad H = grad p = nu k x grad omega:
+ *              the normal part is Eq. totalpressurebc's -nu d omega/ds, the tangential part the nu
+ *              d omega/dn of Eq. pressureflux.  An x-line needs d_y omega, a y-line d_x omega at the
+ *              crossing: the cross-line stencil of the vorticity boundary condition (Sec. 5.3, as
+ *              in iim_transport_rhs) on the vorticity extended at third order with omega_b.
+ *   other arguments as in iim_transport_rhs (u_b only extends the velocity: the wall relation
+ *              above assumes a stationary wall).
+ * Errors: IIM_ERR_INVALID_ARG, IIM_ERR_CUDA.  Asynchronous. */
+iim_status iim_total_pressure_problem(iim_geometry g, const double* omega, const double* ux, const double* uy,
+                                      const double* u_b, const double Uinf[2], double nu, const double* omega_b_in,
+                                      double* omega_b_out, double* f_out, double* data_out, iim_stream stream);
+
+/* A field (interior array, fluid values) at every control point (|C| outputs, canonical
+ * order): the quadratic through the fluid node next to the crossing and the next two fluid
+ * interior nodes along its grid line, evaluated at the crossing (a third-order extrapolation,
+ * Sec. 5.4's surface pressure), the line or the node value where those nodes are not fluid.
+ * Errors: IIM_ERR_INVALID_ARG.  Asynchronous. */
+iim_status iim_wall_values(iim_geometry g, const double* field, double* out, iim_stream stream);
+
+/* The global surface-pressure method of Sec. 5.4 on a geometry in Neumann mode: the problem data
+ * of iim_total_pressure_problem (stationary no-slip walls, omega_b from the velocity), the IIM
+ * solve of -nabla_h^2 H = f with the Neumann stencils (iim_poisson_solve: opts, stats and
+ * errors as there; H_box is the box ring of H or NULL for zero, ignored in free space), and the
+ * surface values of H (iim_wall_values) into H_wall_out (|C| values, or NULL).  The static
+ * pressure on the wall is p - p_inf = H + |u_inf|^2 / 2.  The right-hand side and the datum are
+ * kept in the geometry's own scratch.  Errors: IIM_ERR_INVALID_ARG (also when the geometry is
+ * not in Neumann mode), those of iim_poisson_solve.  Synchronizes `stream`. */
+iim_status iim_total_pressure(iim_geometry g, const double* omega, const double* ux, const double* uy,
+                              const double Uinf[2], double nu, const double* H_box, double* H_out,
+                              double* H_wall_out, const iim_opts* opts, iim_stats* stats, iim_stream stream);
 
 /* One time step of the full algorithm (Sec. 5.5): three stages of the low-storage RK3 of
  * Williamson (1980) (A = 0, -5/9, -153/128; B = 1/3, 15/16, 8/15) on (omega, Gamma_k); each stage

@@ -88,6 +88,11 @@ SIGNATURES = [
     ("iim_net_compose_guess", _i, [ctypes.c_longlong, _vp, _vp, ctypes.c_float, _vp, _vp]),
     ("iim_net_destroy", None, [_vp]),
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
+    ("iim_geometry_set_wall_condition", _i, [_vp, _i, _vp]),
+    ("iim_total_pressure_problem", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
+    ("iim_wall_values", _i, [_vp, _vp, _vp, _vp]),
+    ("iim_total_pressure", _i, [_vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, ctypes.POINTER(iim_opts),
+                                ctypes.POINTER(iim_stats), _vp]),
     ("iim_rk3_step", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d, ctypes.POINTER(_d),
                           ctypes.POINTER(iim_opts), ctypes.POINTER(iim_stats), _vp]),
     ("iim_rk3_step_moving_wall", _i, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _d,
@@ -454,6 +459,57 @@ def iim_transport_rhs(g: Geometry, omega, ux, uy, u_b, Uinf, nu, rhs_out, omega_
                                   _ptr(omega_b_out, f64, g.n_control, "omega_b_out"), _ptr(rhs_out, f64, NXY, "rhs_out"),
                                   _ptr(dgamma_out, f64, g.n_bodies, "dgamma_out"), _stream(stream))
     _check(st, "iim_transport_rhs")
+
+
+def iim_geometry_set_wall_condition(g: Geometry, kind: int, stream=None):
+    """0 Dirichlet ghost stencils (default), 1 Neumann (the psi_b argument of the solves is then
+    the derivative along each control point's grid line into the fluid)."""
+    _check(load().iim_geometry_set_wall_condition(g.handle, int(kind), _stream(stream)),
+           "iim_geometry_set_wall_condition")
+
+
+def iim_total_pressure_problem(g: Geometry, omega, ux, uy, u_b, Uinf, nu, f_out, data_out, omega_b_in=None,
+                               omega_b_out=None, stream=None):
+    """Right-hand side f and Neumann wall datum of the total-pressure problem (Sec. 5.4)."""
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
+    st = load().iim_total_pressure_problem(g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(ux, f64, NXY, "ux"),
+                                           _ptr(uy, f64, NXY, "uy"), _ptr(u_b, f64, 2 * g.n_control, "u_b"), U,
+                                           float(nu), _ptr(omega_b_in, f64, g.n_control, "omega_b_in"),
+                                           _ptr(omega_b_out, f64, g.n_control, "omega_b_out"),
+                                           _ptr(f_out, f64, NXY, "f_out"), _ptr(data_out, f64, g.n_control, "data_out"),
+                                           _stream(stream))
+    _check(st, "iim_total_pressure_problem")
+
+
+def iim_wall_values(g: Geometry, field, out, stream=None):
+    """A field (interior array) extrapolated to every control point."""
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    st = load().iim_wall_values(g.handle, _ptr(field, torch.float64, NXY, "field"),
+                                _ptr(out, torch.float64, g.n_control, "out"), _stream(stream))
+    _check(st, "iim_wall_values")
+
+
+def iim_total_pressure(g: Geometry, omega, ux, uy, Uinf, nu, H_out, H_box=None, H_wall_out=None,
+                       opts: iim_opts | None = None, stream=None, check=True):
+    """The global surface-pressure method (Sec. 5.4) on a geometry in Neumann mode; returns the
+    solve's iim_stats as a dict."""
+    NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
+    f64 = torch.float64
+    U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
+    stats = iim_stats()
+    o = opts if opts is not None else default_opts()
+    st = load().iim_total_pressure(g.handle, _ptr(omega, f64, NXY, "omega"), _ptr(ux, f64, NXY, "ux"),
+                                   _ptr(uy, f64, NXY, "uy"), U, float(nu),
+                                   _ptr(H_box, f64, 2 * (g.grid.nx + g.grid.ny), "H_box"),
+                                   _ptr(H_out, f64, NXY, "H_out"), _ptr(H_wall_out, f64, g.n_control, "H_wall_out"),
+                                   ctypes.byref(o), ctypes.byref(stats), _stream(stream))
+    d = stats.as_dict()
+    d["status"] = st
+    if check:
+        _check(st, "iim_total_pressure")
+    return d
 
 
 def iim_rk3_step(g: Geometry, omega, gamma, psibar, u_b, psi_b, psi_box, Uinf, nu, c_stab, dt=0.0,

@@ -133,6 +133,12 @@ struct iim_geometry_s {
     uint8_t* minus_mask = nullptr;       // per A- node: bit d fourth-order usable, bit 4+d third-order
     int* minus_map = nullptr;            // padded node -> A- index or -1
     double* tr_buf = nullptr;            // transport workspace (allocated on first use)
+    // wall condition of the ghost stencils (iim_geometry_set_wall_condition): 0 Dirichlet
+    // (psi_b + psibar_k), 1 Neumann (derivative along the grid line into the fluid); zeros read
+    // as psibar in Neumann mode; scratch of iim_total_pressure (right-hand side, wall data)
+    int wall = 0;
+    double* psibar_zero = nullptr;
+    double* pr_buf = nullptr;
     uint8_t* node_class = nullptr;       // padded layout
     int* body_circ = nullptr;            // per body: index among circulation bodies or -1
     iim_region* d_regions = nullptr;
@@ -230,6 +236,9 @@ iim_status lockstep_enqueue(const std::vector<int>& idx, iim_geometry const* geo
 void lockstep_finish(void* handle, const std::vector<int>& idx, const iim_opts& o, bool host_driven,
                      std::vector<iim_status>& status, std::vector<iim_stats>& stats);
 void lockstep_forget(iim_geometry g);
+// Rewrites the ghost-stencil weights (gop rows of A+ points, gh rows) for wall condition `kind`
+// (0 Dirichlet, 1 Neumann) from the stored crossings; synchronizes `s`.
+iim_status rewrite_wall_weights(iim_geometry g, int kind, cudaStream_t s);
 // free-space rectangular solve (freespace.cu)
 iim_status lgf_table(int nx, int ny, const double** out);
 template <typename T>

@@ -316,6 +316,70 @@ __global__ void k_fill(int nx, int ny, double h, const double* __restrict__ phi,
     (void)NY;
 }
 
+// Weights at s = 0 of the Neumann variant (Sec. 2.1): the cubic p with p(m) = f(g + m d),
+// m = 2, 3, 4, and p'(a) = h (d . grad f) at the crossing.  With L the quadratic through the three
+// nodes and pi(s) = (s - 2)(s - 3)(s - 4), p = L + c pi, so p(0) = L(0) - 24 (p'(a) - L'(a)) / pi'(a);
+// w[0] multiplies the derivative in units of h.
+__device__ __forceinline__ void neumann_weights4(double a, double w[4]) {
+    const double dpi = (3.0 * a - 18.0) * a + 26.0;   // pi'(a) > 0 on [0, 1]
+    const double k = 24.0 / dpi;
+    w[0] = -k;
+    w[1] = 6.0 + k * (a - 3.5);    // l_2(0) + 24 l_2'(a) / pi'(a), l_2' = (2a - 7) / 2
+    w[2] = -8.0 + k * (6.0 - 2.0 * a);
+    w[3] = 3.0 + k * (a - 2.5);
+}
+
+// Rewrites the ghost blocks of every gop row of an A+ point (rows 0..na-1) and every gh row
+// (rows na..na+nm-1) for wall condition `kind`.  A block is [control point, g+2d, g+3d, g+4d];
+// the scale of the block is that of k_fill: 1 / nv (gh) or -1/h^2 / nv (gop), nv the usable
+// directions of the ghost g (bits 0..3 of minus_mask).
+__global__ void k_wall_weights(int na, int nm, int nx, double h, int kind, const int* __restrict__ gop_ptr,
+                               const int* __restrict__ gop_idx, double* __restrict__ gop_w,
+                               const uint8_t* __restrict__ aff_solid, const int* __restrict__ gh_ptr,
+                               const int* __restrict__ gh_idx, double* __restrict__ gh_w,
+                               const uint8_t* __restrict__ minus_mask, const int* __restrict__ minus_map,
+                               const double* __restrict__ cp_t) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= na + nm) return;
+    const bool is_gh = r >= na;
+    if (!is_gh && aff_solid[r]) return;   // A- rows: fluid neighbours, no ghost blocks
+    const int* ptr = is_gh ? gh_ptr : gop_ptr;
+    const int* idx = is_gh ? gh_idx : gop_idx;
+    double* w = is_gh ? gh_w : gop_w;
+    const int row = is_gh ? r - na : r;
+    const double ih2 = 1.0 / (h * h);
+    const double scale = is_gh ? 1.0 : -ih2;
+    for (int o = ptr[row]; o + 3 < ptr[row + 1]; o += 4) {
+        const int c = -idx[o] - 1;
+        const int step = idx[o + 2] - idx[o + 1];
+        const int m = is_gh ? row : minus_map[idx[o + 1] - 2 * step];
+        const int nv = __popc(minus_mask[m] & 15);
+        const double s = scale / nv;
+        const double a = 1.0 - cp_t[c];
+        double wt[4];
+        if (kind == 1) {
+            neumann_weights4(a, wt);
+            wt[0] *= h;
+        } else {
+            ghost_weights4(a, wt);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) w[o + k] = wt[k] * s;
+    }
+}
+
+iim_status rewrite_wall_weights(iim_geometry g, int kind, cudaStream_t s) {
+    const int rows = g->na + g->nminus;
+    if (rows > 0) {
+        k_wall_weights<<<(rows + 127) / 128, 128, 0, s>>>(g->na, g->nminus, g->nx, g->h, kind, g->gop_ptr, g->gop_idx,
+                                                          g->gop_w, g->aff_solid, g->gh_ptr, g->gh_idx, g->gh_w,
+                                                          g->minus_mask, g->minus_map, g->cp_t);
+        IIM_TRY(cudaGetLastError());
+    }
+    IIM_TRY(cudaStreamSynchronize(s));
+    return IIM_OK;
+}
+
 // Box ring must be fluid.
 __global__ void k_check_box(int nx, int ny, const double* __restrict__ phi, int* err) {
     const int W = nx + 1;
@@ -651,7 +715,7 @@ void free_geometry(iim_geometry g) {
                     g->lam_x32, g->lam_y32, g->sc32_delta, g->sc64_delta, g->sc32_rowoff, g->sc32_lim, g->sc64_rowoff, g->sc64_lim,
                     g->sc32_dstar, g->sc64_dstar, g->sc32_par, g->psi_ext, g->res, g->tbuf, g->psiT, g->partial, g->small, g->V, g->H,
                     g->xsol, g->bvec, g->d_int, g->minus_cp, g->minus_mask, g->minus_map, g->tr_buf,
-                    g->pc_aug, g->pc_S, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->fs_plane, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
+                    g->pc_aug, g->pc_S, g->psibar_zero, g->pr_buf, g->fs_ring, g->fs_rho, g->fs_bnd, g->fs_rres, g->fs_plane, g->cap_ring, g->pc_f, g->pc_info, g->pc_z, g->x0g, g->cap_psi, g->cap_dev, g->io};
     for (void* p : ptrs) cudaFree(p);
     if (g->h_pinned) cudaFreeHost(g->h_pinned);
     if (g->ev0) cudaEventDestroy(g->ev0);

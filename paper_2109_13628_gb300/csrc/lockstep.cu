@@ -556,6 +556,7 @@ static void fill_prob(LsProb& q, iim_geometry g, int prec, const double* omega, 
     }
     q.di = g->d_int;
     q.cap_psi = g->cap_psi; q.cap_dev = g->cap_dev;
+    if (g->wall == 1 && g->psibar_zero) psibar = g->psibar_zero;   // a Neumann wall has no body constants
     q.omega = omega; q.psi_b = psi_b; q.ring = ring; q.gamma = gamma; q.psibar = psibar; q.psi_out = psi_out;
     q.ux_out = ux; q.uy_out = uy;
 }

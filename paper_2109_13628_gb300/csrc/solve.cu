@@ -1696,6 +1696,7 @@ static iim_status poisson_solve(iim_geometry g, const double* omega, const doubl
                                 bool capacitance, int* enqueued) {
     iim_opts opts{IIM_FP64, 1e-10, 2000, 64, 12, 0, 0.0, 0};
     if (opts_in) opts = *opts_in;
+    if (g && g->wall == 1 && g->psibar_zero) psibar = g->psibar_zero;   // a Neumann wall has no body constants
     if (enqueued) {
         *enqueued = 0;
         if (!(g && g->host_solves > 0 && !g->solve_graph_failed && opts.guess == 0 && opts.precond != 2 &&
@@ -1984,6 +1985,29 @@ extern "C" iim_status iim_geometry_set_column_solver(iim_geometry g, int mode) {
             IterGraph* G = (IterGraph*)*gp;
             if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
         }
+    }
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_geometry_set_wall_condition(iim_geometry g, int kind, iim_stream stream) {
+    if (!g || (kind != 0 && kind != 1)) return IIM_ERR_INVALID_ARG;
+    if (kind == 1 && g->ncirc > 0) return IIM_ERR_INVALID_ARG;   // circulation bodies need psibar_k unknowns
+    if (g->wall == kind) return IIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (kind == 1 && !g->psibar_zero && g->nb > 0) {
+        IIM_TRY(cudaMalloc(&g->psibar_zero, g->nb * sizeof(double)));
+        IIM_TRY(cudaMemsetAsync(g->psibar_zero, 0, g->nb * sizeof(double), s));
+    }
+    IIM_CHECK(rewrite_wall_weights(g, kind, s));
+    g->wall = kind;
+    // the operator A, B changed: preconditioner, dense operator and captured solves are rebuilt
+    g->pc_ready = 0;
+    g->cap_ready = 0;
+    lockstep_forget(g);
+    drop_solve_graph(g);
+    for (void** gp : {&g->graph64, &g->graph32}) {
+        IterGraph* G = (IterGraph*)*gp;
+        if (G && G->exec) { cudaGraphExecDestroy(G->exec); G->exec = nullptr; }
     }
     return IIM_OK;
 }

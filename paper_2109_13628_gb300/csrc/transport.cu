@@ -244,6 +244,110 @@ __global__ void k_vorticity_bc(int ncp, TrView v, int nx_cells, int ny_cells, co
     wb[c] = along_x ? (d_along - d_cross) : (d_cross - d_along);
 }
 
+// ---- total pressure (Sec. 5.4)
+// f = -div(u x omega k) = -(d_x(u_y omega) - d_y(u_x omega)) at fluid interior nodes by centred
+// differences of the products, the third-order extensions (velocity with u_b, vorticity with
+// omega_b) at A- nodes and the box values beyond (caller layout, 0 in the solid).
+__global__ void k_pressure_rhs(TrView v, double* __restrict__ f) {
+    const long n = (long)v.NX * v.NY;
+    const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = (int)(k % v.NX), j = (int)(k / v.NX);
+    double r = 0.0;
+    if (v.cls[t_pidx(v, i, j)] <= CLS_PLUS) {
+        const double qe = t_vel(v, 1, i + 1, j) * t_omega(v, 1, i + 1, j);
+        const double qw = t_vel(v, 1, i - 1, j) * t_omega(v, 1, i - 1, j);
+        const double rn = t_vel(v, 0, i, j + 1) * t_omega(v, 1, i, j + 1);
+        const double rs = t_vel(v, 0, i, j - 1) * t_omega(v, 1, i, j - 1);
+        r = -((qe - qw) - (rn - rs)) / (2.0 * v.h);
+    }
+    f[k] = r;
+}
+
+// Wall datum of the Neumann extrapolation at each control point: d . grad H with d along the
+// grid line into the fluid.  On a stationary no-slip wall grad H = grad p = nu k x grad omega
+// (Eq. pressuregrad1; grad |u|^2 / 2 = (grad u)^T u vanishes where u = 0), so an x-line needs
+// d_y omega and a y-line d_x omega at the crossing: the cross-line stencil of the vorticity
+// boundary condition applied to the vorticity extended at third order with omega_b.
+__global__ void k_pressure_wall_data(int ncp, TrView v, int nx_cells, int ny_cells, const int* __restrict__ cp_axis,
+                                     const int* __restrict__ cp_ei, const int* __restrict__ cp_ej,
+                                     const double* __restrict__ cp_t, const double* __restrict__ wb, double nu,
+                                     double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncp) return;
+    const bool along_x = cp_axis[c] == 0;
+    const int ei = cp_ei[c], ej = cp_ej[c];
+    const int oi = along_x ? ei + 1 : ei, oj = along_x ? ej : ej + 1;
+    const bool lower_solid = t_solid(v, ei - 1, ej - 1);
+    const int si = lower_solid ? ei : oi, sj = lower_solid ? ej : oj;
+    const int fi = lower_solid ? oi : ei, fj = lower_solid ? oj : ej;
+    const int di = fi - si, dj = fj - sj;
+    const double t = cp_t[c], h = v.h, w0 = wb[c];
+    auto defined = [&](int gi, int gj) {
+        if (gi <= 0 || gj <= 0 || gi >= nx_cells || gj >= ny_cells) return true;
+        return v.cls[t_pidx(v, gi - 1, gj - 1)] <= CLS_MINUS;
+    };
+    double est = 0.0, first = 0.0;
+    int nest = 0;
+    bool have_first = false;
+    for (int sgn = 1; sgn >= -1; sgn -= 2) {
+        double vals[2];
+        bool ok = true;
+        for (int k = 1; k <= 2 && ok; ++k) {
+            const int pi_ = along_x ? 0 : k * sgn, pj_ = along_x ? k * sgn : 0;
+            const int n0i = si + pi_, n0j = sj + pj_, n1i = fi + pi_, n1j = fj + pj_, n2i = fi + di + pi_,
+                      n2j = fj + dj + pj_;
+            if (!defined(n0i, n0j) || !defined(n1i, n1j) || !defined(n2i, n2j)) { ok = false; break; }
+            const double Wm = t_omega(v, 1, n0i - 1, n0j - 1), W0 = t_omega(v, 1, n1i - 1, n1j - 1),
+                         Wp = t_omega(v, 1, n2i - 1, n2j - 1);
+            vals[k - 1] = W0 + (-t) * (Wp - Wm) / 2.0 + t * t * (Wp - 2.0 * W0 + Wm) / 2.0;
+            if (k == 1 && !have_first) {
+                first = sgn * (vals[0] - w0) / h;
+                have_first = true;
+            }
+        }
+        if (ok) {
+            est += sgn * (-3.0 * w0 + 4.0 * vals[0] - vals[1]) / (2.0 * h);
+            ++nest;
+        }
+    }
+    const double d_cross = nest ? est / nest : (have_first ? first : 0.0);
+    out[c] = along_x ? -nu * di * d_cross : nu * dj * d_cross;
+}
+
+// A field (caller layout) at each control point: the quadratic through the fluid node next to
+// the crossing and the next two fluid interior nodes on its line, at the crossing (fewer nodes
+// where those are not fluid interior nodes).
+__global__ void k_wall_values(int ncp, TrView v, const int* __restrict__ cp_axis, const int* __restrict__ cp_ei,
+                              const int* __restrict__ cp_ej, const double* __restrict__ cp_t,
+                              const double* __restrict__ field, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncp) return;
+    const bool along_x = cp_axis[c] == 0;
+    const int ei = cp_ei[c], ej = cp_ej[c];
+    const int oi = along_x ? ei + 1 : ei, oj = along_x ? ej : ej + 1;
+    const bool lower_solid = t_solid(v, ei - 1, ej - 1);
+    const int si = lower_solid ? ei : oi, sj = lower_solid ? ej : oj;
+    const int fi = lower_solid ? oi : ei, fj = lower_solid ? oj : ej;
+    const int di = fi - si, dj = fj - sj;
+    auto fluid = [&](int gi, int gj) {   // global node coordinates
+        return gi >= 1 && gj >= 1 && gi <= v.NX && gj <= v.NY && v.cls[t_pidx(v, gi - 1, gj - 1)] <= CLS_PLUS;
+    };
+    auto at = [&](int gi, int gj) { return field[(long)(gj - 1) * v.NX + (gi - 1)]; };
+    const double x = -cp_t[c];
+    const double F0 = at(fi, fj);
+    double r;
+    if (fluid(fi + di, fj + dj) && fluid(fi + 2 * di, fj + 2 * dj)) {
+        const double F1 = at(fi + di, fj + dj), F2 = at(fi + 2 * di, fj + 2 * dj);
+        r = F0 * (x - 1.0) * (x - 2.0) * 0.5 - F1 * x * (x - 2.0) + F2 * x * (x - 1.0) * 0.5;
+    } else if (fluid(fi + di, fj + dj)) {
+        r = F0 * (1.0 - x) + at(fi + di, fj + dj) * x;
+    } else {
+        r = F0;
+    }
+    out[c] = r;
+}
+
 // Transport right-hand side at fluid nodes.  mode 0: out_user = rhs (caller layout);
 // mode 1: dw = a * dw + dt * rhs (padded).
 __global__ void k_transport_rhs(TrView v, double nu, int mode, double a, double dt, double* __restrict__ out_user,
@@ -409,6 +513,57 @@ extern "C" iim_status iim_transport_rhs(iim_geometry g, const double* omega, con
         launch("tr_kelvin", 0.0, 0.0, k_kelvin<256>, g->nb, 256, 0, s, v, nu, g->d_regions, g->body_circ, dgamma_out, 0,
                0.0, 0.0, 0.0, W.dG, (double*)nullptr);
     IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_total_pressure_problem(iim_geometry g, const double* omega, const double* ux,
+                                                 const double* uy, const double* u_b, const double Uinf[2], double nu,
+                                                 const double* omega_b_in, double* omega_b_out, double* f_out,
+                                                 double* data_out, iim_stream stream) {
+    if (!g || !omega || !ux || !uy || !f_out || (g->ncp > 0 && !data_out) || !(nu >= 0.0)) return IIM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    TrWork W;
+    IIM_CHECK(tr_work(g, &W));
+    const TrView v = make_view(g, W, Uinf);
+    IIM_CHECK(prepare_stage(g, W, v, omega, ux, uy, u_b, omega_b_in, omega_b_out, s));
+    const long n = (long)g->NX * g->NY;
+    launch("pressure_rhs", 48.0 * (double)n, 0.0, k_pressure_rhs, (unsigned)((n + 255) / 256), 256, 0, s, v, f_out);
+    if (g->ncp > 0)
+        launch("pressure_wall_data", 0.0, 0.0, k_pressure_wall_data, (g->ncp + 127) / 128, 128, 0, s, g->ncp, v, g->nx,
+               g->ny, g->cp_axis, g->cp_ei, g->cp_ej, g->cp_t, (const double*)W.wb, nu, data_out);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_wall_values(iim_geometry g, const double* field, double* out, iim_stream stream) {
+    if (!g || !field || (g->ncp > 0 && !out)) return IIM_ERR_INVALID_ARG;
+    if (g->ncp == 0) return IIM_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    TrWork W;
+    IIM_CHECK(tr_work(g, &W));
+    const TrView v = make_view(g, W, nullptr);
+    launch("wall_values", 0.0, 0.0, k_wall_values, (g->ncp + 127) / 128, 128, 0, s, g->ncp, v, g->cp_axis, g->cp_ei,
+           g->cp_ej, g->cp_t, field, out);
+    IIM_LAUNCHED();
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_total_pressure(iim_geometry g, const double* omega, const double* ux, const double* uy,
+                                         const double Uinf[2], double nu, const double* H_box, double* H_out,
+                                         double* H_wall_out, const iim_opts* opts, iim_stats* stats, iim_stream stream) {
+    if (!g || !omega || !ux || !uy || !H_out || !(nu >= 0.0)) return IIM_ERR_INVALID_ARG;
+    if (g->wall != 1) return IIM_ERR_INVALID_ARG;   // the solve needs the Neumann stencils
+    const size_t n = (size_t)g->NX * g->NY, ncp = (size_t)std::max(g->ncp, 1);
+    if (!g->pr_buf) {
+        IIM_TRY(cudaMalloc(&g->pr_buf, (n + ncp) * sizeof(double)));
+        IIM_TRY(cudaMemset(g->pr_buf, 0, (n + ncp) * sizeof(double)));
+    }
+    double* f = g->pr_buf;
+    double* data = g->pr_buf + n;
+    IIM_CHECK(iim_total_pressure_problem(g, omega, ux, uy, nullptr, Uinf, nu, nullptr, nullptr, f, data, stream));
+    IIM_CHECK(iim_poisson_solve(g, f, data, H_box, nullptr, nullptr, H_out, nullptr, nullptr, nullptr, opts, stats,
+                                stream));
+    if (H_wall_out) IIM_CHECK(iim_wall_values(g, H_out, H_wall_out, stream));
     return IIM_OK;
 }
 

@@ -44,3 +44,8 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
     g = binding.make_grid(0, 1, 0, 1, 100, 64)        # nx not a power of two
     assert lib.iim_setup_geometry(ctypes.byref(g), ctypes.c_void_p(8), 0, None, None, None, ctypes.byref(out)) == -1
     assert lib.iim_poisson_solve(None, None, None, None, None, None, None, None, None, None, None, None, None) == -1
+    assert lib.iim_geometry_set_wall_condition(None, 1, None) == -1
+    U = (ctypes.c_double * 2)(0.0, 0.0)
+    assert lib.iim_total_pressure_problem(None, None, None, None, None, U, 0.0, None, None, None, None, None) == -1
+    assert lib.iim_wall_values(None, None, None, None) == -1
+    assert lib.iim_total_pressure(None, None, None, None, U, 0.0, None, None, None, None, None, None) == -1
