@@ -90,6 +90,7 @@ def parse():
     ap.add_argument("--tiles", type=int, default=0, help="column-pass tile width (0: tuned on the batch)")
     ap.add_argument("--no-cufft", action="store_true", help="skip the cuFFT box-solve cross-check")
     ap.add_argument("--no-free", action="store_true", help="skip the free-space (unbounded) leg")
+    ap.add_argument("--no-pressure", action="store_true", help="skip the total-pressure (Sec. 5.4) leg")
     ap.add_argument("--col-solver", type=int, default=-1,
                     help="column pass of the chosen form: 1 tridiagonal scans, 0 column DSTs, -1 tuned on the batch")
     return ap.parse_args()
@@ -431,6 +432,75 @@ def rk3_c2(iim, inputs, dev, steps=3):
             "speedup_mixed_precond_vs_fp64": out["fp64"]["ms_per_step"] / out["mixed_precond"]["ms_per_step"],
             "kelvin_note": "box-wide invariant (Gamma + h^2 sum omega off the bodies' regions) also moves by the "
                            "vorticity flux through the box edges"}
+
+
+def total_pressure_c2(iim, inputs, dev, flow_steps=30, steps=3):
+    """The global surface-pressure method (Sec. 5.4) on the impulsively started cylinder of the
+    1024 x 512 flow-past-a-cylinder workload: `flow_steps` RK3 steps from rest (mixed, dense
+    Schur preconditioner), then the total-pressure problem -- right-hand side and Neumann wall
+    datum from the flow, the IIM solve with the Neumann stencils on a second geometry of the same
+    level set, surface values -- timed per call in FP64 and in the mixed forms."""
+    import numpy as np
+    import torch
+    P = inputs.c2_cylinder_flow(1024, 512)
+    g = P.grid
+    T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    mk = lambda modes: iim.iim_setup_geometry(iim.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny), T(P.phi), P.regions,
+                                              modes)
+    nu, U = 0.005, (1.0, 0.0)
+    flow = mk(P.modes)
+    iim.iim_build_preconditioner(flow)
+    h = g.h
+    lx, rx, ly, ry = P.regions[0]
+    w = T(P.omega.ravel())
+    gam = T([h * h * P.omega[ly - 1:ry, lx - 1:rx].sum()])
+    pbar = torch.zeros(1, dtype=torch.float64, device=dev)
+    ring = T(P.psi_box)
+    fopts = iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10, precond=1)
+    t = 0.0
+    for _ in range(flow_steps):
+        dt, _, _ = iim.iim_rk3_step(flow, w, gam, pbar, None, None, ring, U, nu, 0.5, opts=fopts)
+        t += dt
+    psi = torch.empty_like(w)
+    ux, uy = torch.empty_like(w), torch.empty_like(w)
+    iim.iim_poisson_solve(flow, w, torch.zeros(flow.n_control, dtype=torch.float64, device=dev), ring, gam, pbar, psi,
+                          ux, uy, opts=fopts)
+    flow.close()
+    geo = mk([0])
+    iim.iim_geometry_set_wall_condition(geo, 1)
+    t0 = time.perf_counter()
+    pc_ms = iim.iim_build_preconditioner(geo)
+    t_pc = time.perf_counter() - t0
+    H = torch.empty_like(w)
+    Hw = torch.empty(geo.n_control, dtype=torch.float64, device=dev)
+    out = {"config": f"impulsively started cylinder (R 0.5, U 1, Re 200) after {flow_steps} RK3 steps (t = {t:.4f}), "
+                     f"1024 x 512, |C| = {geo.n_control}, |A| = {geo.n_affected}; H = 0 on the box",
+           "precond_setup_s": t_pc, "precond_setup_gpu_ms": pc_ms}
+    walls = {}
+    for name, prec, pc in (("fp64", iim.IIM_FP64, 0), ("mixed", iim.IIM_MIXED, 0), ("mixed_precond", iim.IIM_MIXED, 1),
+                           ("mixed_dense_op", iim.IIM_MIXED, 3)):
+        opts = iim.default_opts(prec=prec, rtol=1e-10, precond=pc, max_iter=4000, max_refine=30)
+        iim.iim_total_pressure(geo, w, ux, uy, U, nu, H, H_wall_out=Hw, opts=opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            st = iim.iim_total_pressure(geo, w, ux, uy, U, nu, H, H_wall_out=Hw, opts=opts)
+        e1.record()
+        torch.cuda.synchronize()
+        walls[name] = Hw.cpu().numpy().copy()
+        out[name] = {"ms_per_call": e0.elapsed_time(e1) / steps, "krylov_iters": st["iters"],
+                     "refinements": st["refinements"], "rel_res": st["rel_res"]}
+    geo.close()
+    ref = walls["fp64"]
+    for k in ("mixed", "mixed_precond", "mixed_dense_op"):
+        out[k]["wall_H_vs_fp64_max_abs"] = float(np.abs(walls[k] - ref).max())
+    # static pressure coefficient on the wall, 2 (p - p_inf) / U^2 = 2 H / U^2 + 1
+    cp = 2.0 * ref + 1.0
+    out["wall_cp_range"] = [float(cp.min()), float(cp.max())]
+    out["speedup_mixed_dense_op_vs_fp64"] = out["fp64"]["ms_per_call"] / out["mixed_dense_op"]["ms_per_call"]
+    out["speedup_mixed_precond_vs_fp64"] = out["fp64"]["ms_per_call"] / out["mixed_precond"]["ms_per_call"]
+    return out
 
 
 PLAIN_INNER = (1e-10, 5e-11, 2e-11, 1e-11, 5e-12)
@@ -980,6 +1050,7 @@ def main():
     c3 = None if args.no_c3 else c3_multibody(iim, inputs, dev)
     cufft = None if args.no_cufft else cufft_crosscheck(iim, dev)
     free = None if args.no_free else free_space_c43(iim, inputs, dev)
+    pressure = None if args.no_pressure else total_pressure_c2(iim, inputs, dev)
     c5 = None
     if not args.no_learned:
         c5 = learned_c5(iim, dev, opts_for)
@@ -1043,6 +1114,7 @@ def main():
         "multibody_c3": c3,
         "cufft_crosscheck": cufft,
         "free_space_c43": free,
+        "total_pressure_c2": pressure,
         "cpu_baseline": cpu,
     }
     if rank == 0:

@@ -514,7 +514,7 @@ def iim_total_pressure(g: Geometry, omega, ux, uy, Uinf, nu, H_out, H_box=None, 
 
 def iim_rk3_step(g: Geometry, omega, gamma, psibar, u_b, psi_b, psi_box, Uinf, nu, c_stab, dt=0.0,
                  opts: iim_opts | None = None, stream=None, check=True):
-    """One RK3 step in place on omega, gamma, psibar; returns (dt used, [stats per stage])."""
+    """One RK3 step in place on omega, gamma, psibar; returns (dt used, [stats per stage], status)."""
     NXY = (g.grid.nx - 1) * (g.grid.ny - 1)
     f64 = torch.float64
     U = (_d * 2)(float(Uinf[0]), float(Uinf[1]))
