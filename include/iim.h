@@ -508,6 +508,17 @@ iim_status iim_net_prepare_input(int nx, int ny, const double* omega, const doub
 /* psi_guess = u_box + y / s_out (n values). */
 iim_status iim_net_compose_guess(long long n, const double* u_box, const float* y, float s_out,
                                  double* psi_guess, iim_stream stream);
+/* Tensor cores for the hidden 32 -> 32 convolutions (on = 1, the default; 0 = the CUDA-core
+ * kernel).  On: each such convolution (forward, and the input gradient of training) is an
+ * implicit GEMM on the fifth-generation tensor cores: the layer input is rounded to BF16, the
+ * products with the BF16 weights are summed in FP32 in tensor memory; the first and last layers
+ * (3 -> 32, 32 -> 1) stay on the CUDA cores.  Off: every layer keeps FP32 inputs.
+ * Errors: IIM_ERR_INVALID_ARG (net NULL, on not 0 or 1). */
+iim_status iim_net_set_tensor_cores(iim_net net, int on);
+/* *on = the current setting; *timed_out = 1 if a tensor-core convolution of this net ever gave up
+ * waiting (one second) for its MMAs and skipped its output, else 0.  Synchronizes the device.
+ * Errors: IIM_ERR_INVALID_ARG (NULL argument), IIM_ERR_CUDA. */
+iim_status iim_net_tensor_core_status(iim_net net, int* on, int* timed_out);
 void iim_net_destroy(iim_net net);
 
 /* Number of kernels the library has launched in this process (all threads, all devices);

@@ -86,6 +86,8 @@ SIGNATURES = [
     ("iim_net_train_step", _i, [_vp, _i, _i, _i, _vp, _vp, _vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float), _vp]),
     ("iim_net_prepare_input", _i, [_i, _i, _vp, _vp, _vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, _vp, _vp]),
     ("iim_net_compose_guess", _i, [ctypes.c_longlong, _vp, _vp, ctypes.c_float, _vp, _vp]),
+    ("iim_net_set_tensor_cores", _i, [_vp, _i]),
+    ("iim_net_tensor_core_status", _i, [_vp, _ip, _ip]),
     ("iim_net_destroy", None, [_vp]),
     ("iim_transport_rhs", _i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(_d), _d, _vp, _vp, _vp, _vp, _vp]),
     ("iim_geometry_set_wall_condition", _i, [_vp, _i, _vp]),

@@ -17,6 +17,7 @@
 
 #include "common.cuh"
 #include "iim_ops.cuh"
+#include "tcgen05.cuh"
 
 struct iim_net_s {
     int device = 0;
@@ -36,6 +37,9 @@ struct iim_net_s {
     float* red = nullptr;                // reductions
     long long cap = 0;                   // floats per activation buffer
     float* h_red = nullptr;              // pinned
+    int tc = 0;                          // 32 -> 32 convolutions on the tensor cores (k_conv_tc)
+    __nv_bfloat16* wtc = nullptr;        // one layer's weights in the tensor-core operand layout
+    int* tc_err = nullptr;               // set by k_conv_tc when its wait for the MMAs timed out
 };
 
 namespace iim {
@@ -94,6 +98,130 @@ k_conv(const float* __restrict__ x, const float* __restrict__ gate, const __nv_b
             if (relu) v = fmaxf(v, 0.f);
             y[((size_t)b * Co + co0 + c) * plane + (size_t)gy * W + gx] = v;
         }
+    }
+}
+
+// 32 -> 32 channel convolution as an implicit GEMM on the tensor cores (tcgen05, BF16 operands,
+// FP32 accumulation in tensor memory).  One CTA computes a run of TC_M = 128 pixels of one image
+// row for all 32 output channels: D (128 x 32) = sum over the 9 taps and two 16-channel halves of
+// A_tap (128 pixels x 16 channels) * B_tap^T (32 outputs x 16 channels), 18 MMAs of
+// M = 128, N = 32, K = 16.
+//
+// Shared memory, in 16-byte units of 8 BF16 channels:
+//   A: input rows row - d, row, row + d (r = 0, 1, 2), channel group g (8 channels), pixel
+//      p = 0 .. NP - 1 standing for column x0 - d + p (NP = 128 + 2 d), unit (r * 4 + g) * NP + p;
+//      zero outside the image.  The operand of tap (ky, kx) starts at pixel kx * d of row ky:
+//      consecutive pixels are 16 bytes apart (stride byte offset 128 per 8 rows), the second
+//      channel group of an MMA is NP units further (leading byte offset).
+//   B: tap t, channel group g, output o: unit (t * 4 + g) * 32 + o (packed by k_pack_w_tc).
+// The input is rounded to BF16 on the way in (optionally gated by gate > 0, as k_conv); the
+// epilogue adds the bias, applies the ReLU and writes FP32 in the NCHW layout of k_conv.
+// A wait for the MMAs that runs past one second sets *err and skips the epilogue.
+constexpr int TC_M = 128, TC_C = 32;
+
+__host__ __device__ constexpr size_t conv_tc_smem(int d) {
+    return (size_t)16 * (12 * (TC_M + 2 * d) + 9 * 4 * TC_C) + 16;
+}
+
+// wp[((t * 4 + g) * 32 + o) * 8 + e] = w[(o * 32 + 8 g + e) * 9 + t]
+__global__ void k_pack_w_tc(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wp) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 9 * 4 * TC_C * 8) return;
+    const int e = i & 7, o = (i >> 3) & 31, g = (i >> 8) & 3, t = i >> 10;
+    wp[i] = w[(o * TC_C + 8 * g + e) * 9 + t];
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);   // a at the lower address
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(128)
+k_conv_tc(const float* __restrict__ x, const float* __restrict__ gate, const __nv_bfloat16* __restrict__ wp,
+          const float* __restrict__ bias, float* __restrict__ y, int H, int W, int d, int relu, int* __restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int NP = TC_M + 2 * d;
+    uint4* sA = reinterpret_cast<uint4*>(smem_raw);
+    uint4* sB = sA + 12 * NP;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * 4 * TC_C);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int x0 = blockIdx.x * TC_M, row = blockIdx.y, b = blockIdx.z;
+    const size_t plane = (size_t)H * W;
+    const float* xb = x + (size_t)b * TC_C * plane;
+    const float* gb = gate ? gate + (size_t)b * TC_C * plane : nullptr;
+
+    if (warp == 0) tc::tmem_alloc(tslot, 32);
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    const uint4* wsrc = reinterpret_cast<const uint4*>(wp);
+    for (int i = tid; i < 9 * 4 * TC_C; i += 128) sB[i] = wsrc[i];
+    const int units = 12 * NP;
+    for (int u = tid; u < units; u += 128) {
+        const int rg = u / NP, p = u - rg * NP;
+        const int r = rg >> 2, g = rg & 3;
+        const int gy = row + (r - 1) * d, gx = x0 - d + p;
+        float v[8];
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            const size_t off = (size_t)(8 * g) * plane + (size_t)gy * W + gx;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = xb[off + (size_t)e * plane];
+            if (gb) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e)
+                    if (!(gb[off + (size_t)e * plane] > 0.f)) v[e] = 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+        }
+        sA[u] = make_uint4(bf16x2_bits(v[0], v[1]), bf16x2_bits(v[2], v[3]), bf16x2_bits(v[4], v[5]),
+                           bf16x2_bits(v[6], v[7]));
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_C);
+#pragma unroll 1
+        for (int t = 0; t < 9; ++t) {
+            const int ky = t / 3, kx = t - 3 * ky;
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                const uint64_t ad =
+                    tc::desc_kmajor(a0 + (uint32_t)(16 * ((ky * 4 + 2 * s) * NP + kx * d)), (uint32_t)(16 * NP), 128u);
+                const uint64_t bd = tc::desc_kmajor(b0 + (uint32_t)(16 * (t * 4 + 2 * s) * TC_C), 16u * TC_C, 128u);
+                tc::mma_bf16(tmem, ad, bd, idesc, (t | s) != 0);
+            }
+        }
+        tc::commit(mbar);
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(mbar, 0, 1000000000ull));
+    tc::fence_after_sync();
+    if (ok) {
+        float acc[32];
+        tc::tmem_ld_32x32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+        const int gx = x0 + 32 * warp + lane;
+        if (gx < W) {
+            float* yo = y + (size_t)b * TC_C * plane + (size_t)row * W + gx;
+#pragma unroll
+            for (int o = 0; o < TC_C; ++o) {
+                float v = acc[o] + (bias ? bias[o] : 0.f);
+                if (relu) v = fmaxf(v, 0.f);
+                yo[(size_t)o * plane] = v;
+            }
+        }
+    } else if (lane == 0) {
+        atomicExch(err, 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        if (!ok) (void)tc::mbar_wait_bounded(mbar, 0, 1000000000ull);
+        tc::tmem_dealloc(tmem, 32);
     }
 }
 
@@ -258,6 +386,17 @@ static size_t conv_smem(int d, int co_t) { return sizeof(float) * ((size_t)(TX +
 static iim_status conv(iim_net_s* net, const float* x, const float* gate, const __nv_bfloat16* w, const float* bias,
                        float* y, int B, int Ci, int Co, int H, int W, int d, int relu, cudaStream_t s) {
     const dim3 blk(TX, TY);
+    if (net->tc && Ci == TC_C && Co == TC_C) {
+        launch("net_pack_w_tc", 0.0, 0.0, k_pack_w_tc, (9 * 4 * TC_C * 8 + 255) / 256, 256, 0, s, w, net->wtc);
+        IIM_LAUNCHED();
+        const size_t sm = conv_tc_smem(d);
+        IIM_CHECK(allow_smem(k_conv_tc, sm));
+        launch("net_conv_tc", 4.0 * (double)B * H * W * (Ci * (gate ? 2 : 1) + Co), 18.0 * (double)B * H * W * Ci * Co,
+               k_conv_tc, dim3((W + TC_M - 1) / TC_M, H, B), 128, sm, s, x, gate, (const __nv_bfloat16*)net->wtc, bias, y,
+               H, W, d, relu, net->tc_err);
+        IIM_LAUNCHED();
+        return IIM_OK;
+    }
     if (Co > 1) {
         const int ncot = (Co + 31) / 32;
         const size_t sm = conv_smem(d, 32);
@@ -270,7 +409,6 @@ static iim_status conv(iim_net_s* net, const float* x, const float* gate, const 
                dim3((W + TX - 1) / TX, (H + TY - 1) / TY, B), blk, sm, s, x, gate, w, bias, y, Ci, Co, H, W, d, relu);
     }
     IIM_LAUNCHED();
-    (void)net;
     return IIM_OK;
 }
 
@@ -370,7 +508,7 @@ extern "C" iim_status iim_net_create(int in_channels, int hidden, int n_layers, 
     auto fail = [&](cudaError_t e) {
         record_cuda_error(e, "iim_net_create", __FILE__, __LINE__);
         cudaFree(net->p); cudaFree(net->gr); cudaFree(net->m); cudaFree(net->v); cudaFree(net->wb); cudaFree(net->wt);
-        cudaFree(net->red);
+        cudaFree(net->red); cudaFree(net->wtc); cudaFree(net->tc_err);
         delete net;
         return IIM_ERR_CUDA;
     };
@@ -382,6 +520,10 @@ extern "C" iim_status iim_net_create(int in_channels, int hidden, int n_layers, 
     if ((e = cudaMalloc(&net->wb, sizeof(__nv_bfloat16) * off)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&net->wt, sizeof(__nv_bfloat16) * 32 * 32 * 9)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&net->red, sizeof(float) * 4096)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&net->wtc, sizeof(__nv_bfloat16) * 9 * 4 * TC_C * 8)) != cudaSuccess) return fail(e);
+    if ((e = cudaMalloc(&net->tc_err, sizeof(int))) != cudaSuccess) return fail(e);
+    cudaMemset(net->tc_err, 0, sizeof(int));
+    net->tc = 1;
     if ((e = cudaMemcpy(net->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     cudaMemset(net->m, 0, sizeof(float) * off);
     cudaMemset(net->v, 0, sizeof(float) * off);
@@ -487,10 +629,24 @@ extern "C" iim_status iim_net_compose_guess(long long n, const double* u_box, co
     return IIM_OK;
 }
 
+extern "C" iim_status iim_net_set_tensor_cores(iim_net net, int on) {
+    if (!net || (on != 0 && on != 1)) return IIM_ERR_INVALID_ARG;
+    net->tc = on;
+    return IIM_OK;
+}
+
+extern "C" iim_status iim_net_tensor_core_status(iim_net net, int* on, int* timed_out) {
+    if (!net || !on || !timed_out) return IIM_ERR_INVALID_ARG;
+    *on = net->tc;
+    IIM_TRY(cudaDeviceSynchronize());
+    IIM_TRY(cudaMemcpy(timed_out, net->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    return IIM_OK;
+}
+
 extern "C" void iim_net_destroy(iim_net net) {
     if (!net) return;
     cudaFree(net->p); cudaFree(net->gr); cudaFree(net->m); cudaFree(net->v); cudaFree(net->wb); cudaFree(net->wt);
-    cudaFree(net->act); cudaFree(net->g0); cudaFree(net->red);
+    cudaFree(net->act); cudaFree(net->g0); cudaFree(net->red); cudaFree(net->wtc); cudaFree(net->tc_err);
     if (net->h_red) cudaFreeHost(net->h_red);
     delete net;
 }

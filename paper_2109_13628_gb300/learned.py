@@ -25,7 +25,7 @@ IN_CHANNELS = 3
 
 
 class Net:
-    def __init__(self, in_channels=IN_CHANNELS, hidden=HIDDEN, dilations=DILATIONS, seed=0):
+    def __init__(self, in_channels=IN_CHANNELS, hidden=HIDDEN, dilations=DILATIONS, seed=0, tensor_cores=True):
         lib = B.load()
         d = (ctypes.c_int * len(dilations))(*dilations)
         h = ctypes.c_void_p()
@@ -33,6 +33,18 @@ class Net:
         self.h = h
         self.n = int(lib.iim_net_num_params(h))
         self.dilations = tuple(dilations)
+        self.set_tensor_cores(tensor_cores)
+
+    def set_tensor_cores(self, on):
+        """32 -> 32 convolutions on the tensor cores (BF16 layer inputs) or the CUDA cores (FP32)."""
+        B._check(B.load().iim_net_set_tensor_cores(self.h, 1 if on else 0), "iim_net_set_tensor_cores")
+
+    def tensor_core_status(self):
+        """(setting, 1 if a tensor-core convolution ever timed out waiting for its MMAs)."""
+        on, t = ctypes.c_int(), ctypes.c_int()
+        B._check(B.load().iim_net_tensor_core_status(self.h, ctypes.byref(on), ctypes.byref(t)),
+                 "iim_net_tensor_core_status")
+        return on.value, t.value
 
     def close(self):
         if self.h:
