@@ -41,11 +41,11 @@ NCU_TRAFFIC = {
     # (requests from the SMs) 12.75 M read + 5.24 M write sectors; scaled by the fields to the
     # roofline's launch of 95 fields
     "dst_cols_f32": {"bytes_per_launch": 279548160 / 40 * 95, "l2_bytes_per_launch": 17989366 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "1acf6ddd786067bd",
+                     "launches": 1, "tile_width": 8, "source_hash": "aaa5adefadcf1624",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
     # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 111.8 MB, L2 11.04 M + 5.24 M
     "tri_cols_f32": {"bytes_per_launch": 279469824 / 40 * 95, "l2_bytes_per_launch": 16279091 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "1acf6ddd786067bd",
+                     "launches": 1, "tile_width": 8, "source_hash": "aaa5adefadcf1624",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
 }
 
@@ -57,9 +57,10 @@ PASS_NAMES = {0: ("dst_rows_fwd_f32", "dst_cols_f32", "dst_rows_inv_f32"),
 
 
 def kernel_source_hash():
-    """Hash of the files holding the transform kernels and their launch configuration."""
+    """Hash of the files holding the transform kernels' code (the launch shape of a capture is
+    recorded beside it: tile width, fields per launch)."""
     h = hashlib.sha256()
-    for f in ("dst.cuh", "tri.cuh", "iim_ops.cuh", "solve.cu", "lockstep.cu"):
+    for f in ("dst.cuh", "tri.cuh"):
         with open(os.path.join(ROOT, "paper_2109_13628_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -338,6 +339,7 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
         except iim.IIMError:
             continue
         om, pb, gm = T(P.omega.ravel()), T(np.zeros(geo.n_control)), T(learned.gamma_of(P))
+        phi_d = T(P.phi)
         out = torch.empty(P.omega.size, dtype=torch.float64, device=dev)
         pbar = torch.zeros(len(P.regions), dtype=torch.float64, device=dev)
         res = {}
@@ -347,7 +349,7 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
             e0.record()
             guess = None
             if tag == "learned":
-                S = learned.Sample(P, dev)
+                S = learned.Sample(P, dev, omega=om, phi=phi_d, mask=False, box_prec=iim.IIM_MIXED)
                 guess = S.guess(net, dev)
             st = iim.iim_poisson_solve(geo, om, pb, None, gm, pbar, out, psi_guess=guess,
                                        opts=iim.default_opts(prec=iim.IIM_MIXED, rtol=1e-10,
@@ -360,6 +362,9 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
     net.close()
     if not rows:
         return None
+    # the net alone at the evaluation size: tensor-core and CUDA-core hidden layers
+    fwd = {("tensor_cores" if tc else "cuda_cores"): learned.time_forward(eval_n - 1, tensor_cores=tc)
+           for tc in (True, False)}
     mean = lambda tag, k: float(np.mean([r[tag][k] for r in rows]))
     return {"config": f"train {train_count} method solves at {train_n}^2 (random 2-5 circles/ellipses, Gaussian "
                       f"vortices; 8 grid symmetries), eval {len(rows)} unseen {eval_n}^2 geometries, mixed to 1e-10",
@@ -372,7 +377,10 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
                               "ms_per_solve": mean("learned", 1),
                               "solves_per_s": 1e3 / mean("learned", 1),
                               "seed_rel_res_mean": mean("learned", 2),
-                              "max_rel_res": max(r["learned"][3] for r in rows)}}
+                              "max_rel_res": max(r["learned"][3] for r in rows)},
+            "net_forward": {k: {"ms": v["forward_ms"], "kernels": v["kernels"]} for k, v in fwd.items()},
+            "guess_path": "body-free box solve (FP32 transforms) of the device omega, net input, forward pass "
+                          "(hidden layers on the tensor cores), composition; all inside the learned solve's events"}
 
 
 def rk3_c2(iim, inputs, dev, steps=3):

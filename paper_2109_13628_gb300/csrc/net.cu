@@ -155,27 +155,38 @@ k_conv_tc(const float* __restrict__ x, const float* __restrict__ gate, const __n
     if (tid == 0) tc::mbar_init(mbar, 1);
     const uint4* wsrc = reinterpret_cast<const uint4*>(wp);
     for (int i = tid; i < 9 * 4 * TC_C; i += 128) sB[i] = wsrc[i];
+    // UB units per thread and round, all their loads issued before any conversion
+    constexpr int UB = 2;
     const int units = 12 * NP;
-    for (int u = tid; u < units; u += 128) {
-        const int rg = u / NP, p = u - rg * NP;
-        const int r = rg >> 2, g = rg & 3;
-        const int gy = row + (r - 1) * d, gx = x0 - d + p;
-        float v[8];
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            const size_t off = (size_t)(8 * g) * plane + (size_t)gy * W + gx;
+    for (int u0 = tid; u0 < units; u0 += UB * 128) {
+        float v[UB][8];
+        bool in[UB];
+        size_t off[UB];
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = xb[off + (size_t)e * plane];
-            if (gb) {
+        for (int q = 0; q < UB; ++q) {
+            const int u = u0 + q * 128;
+            const int rg = u / NP, p = u - rg * NP;
+            const int r = rg >> 2, g = rg & 3;
+            const int gy = row + (r - 1) * d, gx = x0 - d + p;
+            in[q] = u < units && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            off[q] = in[q] ? (size_t)(8 * g) * plane + (size_t)gy * W + gx : 0;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[q][e] = in[q] ? xb[off[q] + (size_t)e * plane] : 0.f;
+        }
+        if (gb) {
+#pragma unroll
+            for (int q = 0; q < UB; ++q)
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
-                    if (!(gb[off + (size_t)e * plane] > 0.f)) v[e] = 0.f;
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = 0.f;
+                    if (in[q] && !(gb[off[q] + (size_t)e * plane] > 0.f)) v[q][e] = 0.f;
         }
-        sA[u] = make_uint4(bf16x2_bits(v[0], v[1]), bf16x2_bits(v[2], v[3]), bf16x2_bits(v[4], v[5]),
-                           bf16x2_bits(v[6], v[7]));
+#pragma unroll
+        for (int q = 0; q < UB; ++q) {
+            const int u = u0 + q * 128;
+            if (u < units)
+                sA[u] = make_uint4(bf16x2_bits(v[q][0], v[q][1]), bf16x2_bits(v[q][2], v[q][3]),
+                                   bf16x2_bits(v[q][4], v[q][5]), bf16x2_bits(v[q][6], v[q][7]));
+        }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();

@@ -98,24 +98,29 @@ def scales(P):
 class Sample:
     """Device tensors of one problem: the network input, the rectangular solve, the mask."""
 
-    def __init__(self, P, dev):
+    def __init__(self, P, dev, omega=None, phi=None, mask=True, box_prec=B.IIM_FP64):
+        """omega / phi: device FP64 copies the caller already holds (else uploaded from P);
+        mask: build the fluid mask (training only); box_prec: precision of the body-free box
+        solve that feeds the net and the guess (IIM_MIXED = FP32 transforms)."""
         g = P.grid
         self.P = P
         self.grid = B.make_grid(g.x0, g.x1, g.y0, g.y1, g.nx, g.ny)
         self.sc = scales(P)
         T = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
-        self.omega = T(P.omega.ravel())
-        self.phi = T(P.phi)
+        self.omega = omega if omega is not None else T(P.omega.ravel())
+        self.phi = phi if phi is not None else T(P.phi)
         n = P.omega.size
         self.ubox = torch.empty(n, dtype=torch.float64, device=dev)
         work = torch.empty(2 * n + 4 * g.nx, dtype=torch.float64, device=dev)
-        B.iim_box_poisson(self.grid, self.omega, None, self.ubox, B.IIM_FP64, work)
+        B.iim_box_poisson(self.grid, self.omega, None, self.ubox, box_prec, work)
         self.x = torch.empty((1, IN_CHANNELS, g.ny - 1, g.nx - 1), dtype=torch.float32, device=dev)
         B._check(B.load().iim_net_prepare_input(g.nx, g.ny, B._ptr(self.omega), B._ptr(self.phi), B._ptr(self.ubox),
                                                 self.sc["s_omega"], self.sc["s_phi"], self.sc["s_box"],
                                                 B._ptr(self.x), B._stream(None)), "iim_net_prepare_input")
-        self.mask = torch.as_tensor((P.phi[1:-1, 1:-1] >= 0).astype(np.float32), device=dev).reshape(1, 1, g.ny - 1,
-                                                                                                      g.nx - 1)
+        self.mask = None
+        if mask:
+            self.mask = torch.as_tensor((P.phi[1:-1, 1:-1] >= 0).astype(np.float32),
+                                        device=dev).reshape(1, 1, g.ny - 1, g.nx - 1)
 
     def guess(self, net, dev):
         g = self.P.grid
@@ -225,3 +230,59 @@ def train(net, data, epochs, batch, lr, time_budget_s=None, seed=0, augment=True
         if time_budget_s is not None and time.perf_counter() - t0 > time_budget_s:
             break
     return losses
+
+
+def time_forward(n, batch=1, reps=10, tensor_cores=True, backward=False, seed=0):
+    """Device milliseconds of one forward pass (and, with backward, of one backward pass) of the
+    production net on batch x 3 x n x n random inputs: CUDA events around reps launches after
+    three warm-up passes."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev).manual_seed(seed)
+    x = torch.randn(batch, IN_CHANNELS, n, n, device=dev, generator=g)
+    y = torch.empty(batch, 1, n, n, device=dev)
+    net = Net(seed=seed, tensor_cores=tensor_cores)
+    out = {}
+    try:
+        for _ in range(3):
+            net.forward(x, y)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.forward(x, y)
+        e1.record()
+        torch.cuda.synchronize()
+        out["forward_ms"] = e0.elapsed_time(e1) / reps
+        # per-kernel split of one more forward pass (CUDA events around every launch)
+        B.iim_profile_begin()
+        net.forward(x, y)
+        out["kernels"] = {r["name"]: {"launches": r["launches"], "ms": r["ms"],
+                                      "gbs": r["bytes"] / (r["ms"] * 1e6) if r["ms"] > 0 else None,
+                                      "tflops": r["flops"] / (r["ms"] * 1e9) if r["ms"] > 0 else None}
+                          for r in B.iim_profile_end()}
+        if backward:
+            dy = torch.randn_like(y)
+            net.backward(x, dy)
+            t0 = time.perf_counter()
+            for _ in range(3):
+                net.backward(x, dy)   # synchronous (copies the gradient to the host)
+            out["backward_ms_wall"] = (time.perf_counter() - t0) / 3 * 1e3
+        out["tensor_cores"], out["timed_out"] = net.tensor_core_status()
+    finally:
+        net.close()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="time the learned guess's network (forward, optional backward)")
+    ap.add_argument("--n", type=int, default=1023)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--reps", type=int, default=10)
+    ap.add_argument("--tc", type=int, choices=[0, 1], default=1)
+    ap.add_argument("--backward", action="store_true")
+    a = ap.parse_args()
+    r = time_forward(a.n, a.batch, a.reps, bool(a.tc), a.backward)
+    print(json.dumps({"n": a.n, "batch": a.batch, **r}))
