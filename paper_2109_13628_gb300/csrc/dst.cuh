@@ -135,16 +135,35 @@ __device__ __forceinline__ void dft<float, 16>(cpx<float>* v) { dft16_impl(v); }
 template <>
 __device__ __forceinline__ void dft<double, 16>(cpx<double>* v) { dft16_impl(v); }
 
-// Packed FFT input c_m = y_{2m} + i y_{2m+1} from the line x (x_0 = x_n = 0).
+// Position of line element j in a line buffer: plain (j), or padded with two elements after
+// every 32 (the column pass's register paths), which keeps each lane's run of 32 consecutive
+// elements in its own banks when the lanes of a warp store contiguous chunks.
+template <bool PADL>
+__host__ __device__ __forceinline__ constexpr int lp(int j) { return PADL ? j + ((j >> 5) << 1) : j; }
+
 template <typename T>
+using vec2_t = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+
+// Packed FFT input c_m = y_{2m} + i y_{2m+1} from the line x (x_0 = x_n = 0).
+template <typename T, bool PADL = false>
 __device__ __forceinline__ cpx<T> packed(const T* x, const cpx<T>* tw, int n, int m) {
     const int j0 = 2 * m, j1 = j0 + 1;
+    T a0, a1;
+    if constexpr (PADL) {
+        // x_{2m}, x_{2m+1} are adjacent and 2-element aligned in the padded layout
+        const vec2_t<T> v = *reinterpret_cast<const vec2_t<T>*>(x + lp<PADL>(j0));
+        a0 = v.x;
+        a1 = v.y;
+    } else {
+        a0 = x[j0];
+        a1 = x[j1];
+    }
     T y0 = T(0);
     if (j0 != 0) {
-        const T a = x[j0], b = x[n - j0];
-        y0 = (-tw[j0].y) * (a + b) + T(0.5) * (a - b);
+        const T b = x[lp<PADL>(n - j0)];
+        y0 = (-tw[j0].y) * (a0 + b) + T(0.5) * (a0 - b);
     }
-    const T a1 = x[j1], b1 = x[n - j1];
+    const T b1 = x[lp<PADL>(n - j1)];
     const T y1 = (-tw[j1].y) * (a1 + b1) + T(0.5) * (a1 - b1);
     return {y0, y1};
 }
@@ -258,6 +277,48 @@ __device__ __forceinline__ void dst_finish(const cpx<T>* C, T* dst, const cpx<T>
     __syncwarp();
 }
 
+// The split step and the odd outputs' running sum with each lane on P consecutive k
+// (k = P lane + i): the split values come straight from C (swizzled), the running sum is a
+// sequential sum within the lane plus one warp scan of the lane totals, and each lane stores
+// (X_2k, X_2k+1) pairs into dst in the padded layout.  tws[i * 32 + lane] = tw[2 (P lane + i)].
+template <typename T, int P>
+__device__ __forceinline__ void dst_finish_chunked(const cpx<T>* C, T* dst, const cpx<T>* tws, int lane) {
+    constexpr int M = 32 * P;
+    T ev[P], od[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const int k = P * lane + i;
+        const cpx<T> ck = C[swz<T>(k)];
+        const cpx<T> cm = C[swz<T>(k == 0 ? 0 : M - k)];
+        const T ex = T(0.5) * (ck.x + cm.x), ey = T(0.5) * (ck.y - cm.y);
+        const T dx = T(0.5) * (ck.x - cm.x), dy = T(0.5) * (ck.y + cm.y);
+        const cpx<T> w = tws[i * 32 + lane];
+        const T yx = ex + (w.x * dy + w.y * dx);
+        const T yy = ey + (w.y * dy - w.x * dx);
+        ev[i] = k == 0 ? T(0) : -yy;
+        od[i] = k == 0 ? T(0.5) * yx : yx;
+    }
+#pragma unroll
+    for (int i = 1; i < P; ++i) od[i] += od[i - 1];
+    const T tot = od[P - 1];
+    T incl = tot;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T u = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += u;
+    }
+    const T excl = incl - tot;
+#pragma unroll
+    for (int i = 0; i < P; ++i) {
+        const int k = P * lane + i;
+        vec2_t<T> v;
+        v.x = ev[i];
+        v.y = od[i] + excl;
+        *reinterpret_cast<vec2_t<T>*>(dst + lp<true>(2 * k)) = v;
+    }
+    __syncwarp();
+}
+
 template <typename T>
 __device__ __forceinline__ cpx<T> shfl_cpx(cpx<T> v, int src) {
     return {__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src)};
@@ -265,7 +326,7 @@ __device__ __forceinline__ cpx<T> shfl_cpx(cpx<T> v, int src) {
 
 // Register-path DST-I (P = 8 or 16, n = 64 P).  rtw = tw + n: [k * 32 + l] = W_M^(l k) for
 // k < P, then W_32^j, j < 32.  buf1 is the transpose buffer, C goes to buf0; returns buf1.
-template <typename T, int P>
+template <typename T, int P, bool PADL = false>
 __device__ __forceinline__ T* dst1_warp_reg(T* buf0, T* buf1, const cpx<T>* tw, int n, int lane) {
     constexpr int M = 32 * P;
     constexpr int G = 32 / P;   // lanes per 32-point DFT in the second stage
@@ -273,7 +334,7 @@ __device__ __forceinline__ T* dst1_warp_reg(T* buf0, T* buf1, const cpx<T>* tw, 
     const cpx<T>* w32 = rtw + M;
     cpx<T> v[P];
 #pragma unroll
-    for (int p = 0; p < P; ++p) v[p] = packed(buf0, tw, n, 32 * p + lane);
+    for (int p = 0; p < P; ++p) v[p] = packed<T, PADL>(buf0, tw, n, 32 * p + lane);
     dft<T, P>(v);
 #pragma unroll
     for (int k = 1; k < P; ++k) v[k] = cmul(v[k], rtw[k * 32 + lane]);
@@ -308,7 +369,8 @@ __device__ __forceinline__ T* dst1_warp_reg(T* buf0, T* buf1, const cpx<T>* tw, 
 #pragma unroll
     for (int q = 0; q < P; ++q) C[swz<T>(k1 + P * q + P * P * h)] = v[q];
     __syncwarp();
-    dst_finish(C, buf1, tw, M, lane);
+    if constexpr (PADL) dst_finish_chunked<T, P>(C, buf1, w32 + 32, lane);
+    else dst_finish(C, buf1, tw, M, lane);
     return buf1;
 }
 
@@ -397,8 +459,9 @@ __device__ __forceinline__ T* dst1_line64(T* buf0, T* buf1, const cpx<T>* tw, in
     return dst;
 }
 
-// One DST-I of a line on the FP path's threads (tid < line_threads(FP), group grp of the block).
-template <typename T, int FP>
+// One DST-I of a line on the FP path's threads (tid < line_threads(FP), group grp of the block);
+// PADL: the line (input and result) in the padded layout of lp (register paths only).
+template <typename T, int FP, bool PADL = false>
 __device__ __forceinline__ T* dst_line(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int tid, int grp, T* tot);
 
 // DST-I of the line held in buf0[1..n-1] (buf0[0] ignored), with buf1 (n values) as scratch.
@@ -406,9 +469,9 @@ __device__ __forceinline__ T* dst_line(T* buf0, T* buf1, const cpx<T>* tw, int n
 // the buffer holding the result in [1..n-1] (natural layout).
 // FP = 16 or 8 selects the register path (n = 1024 or 512), FP = 0 the Stockham passes; the
 // kernels are instantiated per path so that each holds the code of one path only.
-template <typename T, int FP>
+template <typename T, int FP, bool PADL = false>
 __device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int lane) {
-    if constexpr (FP != 0) return dst1_warp_reg<T, FP>(buf0, buf1, tw, n, lane);
+    if constexpr (FP != 0) return dst1_warp_reg<T, FP, PADL>(buf0, buf1, tw, n, lane);
     const int M = n >> 1;
     const int logM = logn - 1;
     const cpx<T>* ptw = tw + n;
@@ -436,16 +499,21 @@ __device__ __forceinline__ T* dst1_warp(T* buf0, T* buf1, const cpx<T>* tw, int 
     return dst;
 }
 
-template <typename T, int FP>
+template <typename T, int FP, bool PADL>
 __device__ __forceinline__ T* dst_line(T* buf0, T* buf1, const cpx<T>* tw, int n, int logn, int tid, int grp, T* tot) {
     if constexpr (FP == 64) return dst1_line64<T>(buf0, buf1, tw, tid, grp, tot);
-    else return dst1_warp<T, FP>(buf0, buf1, tw, n, logn, tid);
+    else return dst1_warp<T, FP, PADL>(buf0, buf1, tw, n, logn, tid);
 }
 
 // Complex entries of the shared-memory twiddle region for lines of n points: the full table
 // exp(-i pi k / n), k < n, then the register-path tables (n / 2 + 32 entries) or the per-pass
 // tables (fewer than n / 2 entries).
-__host__ __device__ constexpr int tw_region(int n) { return n + n / 2 + 64; }
+__host__ __device__ constexpr int tw_region(int n) { return n + n / 2 + 64 + (reg_fft(n) ? n / 2 : 0); }
+
+// Elements a line buffer takes: padded (lp) on the register paths, whose transforms store their
+// result in contiguous chunks per lane (dst_finish_chunked).
+__host__ __device__ constexpr bool padded_lines(int fp) { return fp == 8 || fp == 16; }
+__host__ __device__ constexpr int line_len(int n, int fp) { return padded_lines(fp) ? lp<true>(n) : n; }
 
 // Fills the twiddle region from the 4096-entry table; the loads of one thread are issued back
 // to back (batches of 8) before their shared-memory stores.
@@ -475,10 +543,14 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, 
             s_tw[n + e] = t >= n ? cpx<T>{-w.x, -w.y} : w;
         }
     } else if (FP == 8 || FP == 16) {
-        // W_M^(l k) at [k * 32 + l] (M = n / 2), then W_32^j
-        const int M = n >> 1;
-        for (int e = threadIdx.x; e < M + 32; e += nt) {
-            const int t = e < M ? (4 * (e & 31) * (e >> 5)) % (2 * n) : (e - M) * (n / 16);
+        // W_M^(l k) at [k * 32 + l] (M = n / 2), then W_32^j, then the split step's twiddles in
+        // lane-major order for the chunked finish: [i * 32 + l] = exp(-i pi 2 (P l + i) / n)
+        const int M = n >> 1, P = M / 32;
+        for (int e = threadIdx.x; e < 2 * M + 32; e += nt) {
+            int t;
+            if (e < M) t = (4 * (e & 31) * (e >> 5)) % (2 * n);
+            else if (e < M + 32) t = (e - M) * (n / 16);
+            else t = 2 * (P * ((e - M - 32) & 31) + ((e - M - 32) >> 5));
             const cpx<T> w = g_tw[(t & (n - 1)) << stride_shift];
             s_tw[n + e] = t >= n ? cpx<T>{-w.x, -w.y} : w;
         }
@@ -494,14 +566,36 @@ __device__ __forceinline__ void load_twiddles(cpx<T>* s_tw, const cpx<T>* g_tw, 
 template <typename T>
 using vec16_t = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
 
+// 16-byte vector q of a row in a line buffer (plain or padded layout).  In the padded layout a
+// vector's elements 0-1 and 2-3 (FP32) stay adjacent pairs: no multiple of 32 falls inside a pair.
+template <typename T, bool PADL>
+__device__ __forceinline__ void line_put16(T* line, int q, vec16_t<T> v) {
+    if constexpr (!PADL || sizeof(T) == 8) {
+        *reinterpret_cast<vec16_t<T>*>(line + lp<PADL>(q * (16 / (int)sizeof(T)))) = v;
+    } else {
+        float2* d = reinterpret_cast<float2*>(line + lp<true>(4 * q));
+        d[0] = make_float2(v.x, v.y);
+        d[1] = make_float2(v.z, v.w);
+    }
+}
+template <typename T, bool PADL>
+__device__ __forceinline__ vec16_t<T> line_get16(const T* line, int q) {
+    if constexpr (!PADL || sizeof(T) == 8) {
+        return *reinterpret_cast<const vec16_t<T>*>(line + lp<PADL>(q * (16 / (int)sizeof(T))));
+    } else {
+        const float2* d = reinterpret_cast<const float2*>(line + lp<true>(4 * q));
+        const float2 a = d[0], b = d[1];
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
 // Loads nx values of a padded row (16-byte aligned) into a line buffer with vector loads,
 // batches of 8 loads in flight per lane.
-template <typename T, int TN = 32>
+template <typename T, int TN = 32, bool PADL = false>
 __device__ __forceinline__ void load_row_vec(T* line, const T* __restrict__ g, int nx, int lane) {
     constexpr int V = 16 / sizeof(T);
     using VT = vec16_t<T>;
     const VT* src = reinterpret_cast<const VT*>(g);
-    VT* dst = reinterpret_cast<VT*>(line);
     const int nv = nx / V;
     for (int q0 = lane; q0 < nv; q0 += 8 * TN) {
         VT v[8];
@@ -510,23 +604,22 @@ __device__ __forceinline__ void load_row_vec(T* line, const T* __restrict__ g, i
             if (q0 + TN * b < nv) v[b] = src[q0 + TN * b];
 #pragma unroll
         for (int b = 0; b < 8; ++b)
-            if (q0 + TN * b < nv) dst[q0 + TN * b] = v[b];
+            if (q0 + TN * b < nv) line_put16<T, PADL>(line, q0 + TN * b, v[b]);
     }
 }
 
-template <typename T, int TN = 32>
+template <typename T, int TN = 32, bool PADL = false>
 __device__ __forceinline__ void store_row_vec(T* __restrict__ g, const T* line, int nx, int lane) {
     constexpr int V = 16 / sizeof(T);
     using VT = vec16_t<T>;
-    const VT* src = reinterpret_cast<const VT*>(line);
     VT* dst = reinterpret_cast<VT*>(g);
     const int nv = nx / V;
 #pragma unroll 4
-    for (int q = lane; q < nv; q += TN) dst[q] = src[q];
+    for (int q = lane; q < nv; q += TN) dst[q] = line_get16<T, PADL>(line, q);
 }
 
 // Loads a padded FP64 row (16-byte aligned, nx values) into a line buffer of T.
-template <typename T, int TN = 32>
+template <typename T, int TN = 32, bool PADL = false>
 __device__ __forceinline__ void load_row_f64(T* line, const double* __restrict__ g, int nx, int lane) {
     const double2* src = reinterpret_cast<const double2*>(g);
     const int nv = nx / 2;
@@ -539,8 +632,10 @@ __device__ __forceinline__ void load_row_f64(T* line, const double* __restrict__
         for (int b = 0; b < 8; ++b) {
             const int q = q0 + TN * b;
             if (q < nv) {
-                line[2 * q] = (T)v[b].x;
-                line[2 * q + 1] = (T)v[b].y;
+                vec2_t<T> w;
+                w.x = (T)v[b].x;
+                w.y = (T)v[b].y;
+                *reinterpret_cast<vec2_t<T>*>(line + lp<PADL>(2 * q)) = w;
             }
         }
     }
@@ -593,50 +688,52 @@ rows_fwd_body(int NX, int NY, int n, int logn, int row0, int nrows, const double
               const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
               T* __restrict__ out) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
+    constexpr bool PADL = padded_lines(FP);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
+    const int LN = line_len(n, FP);
     T* lines = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));
-    T* b0 = lines + (size_t)grp * (2 * n);
-    T* b1 = b0 + n;
-    T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
+    T* b0 = lines + (size_t)grp * (2 * LN);
+    T* b1 = b0 + LN;
+    T* tot = lines + (size_t)LPB * 2 * LN + grp * kLineScratch;
     if (FP == 0) __syncthreads();
     const int r = row0 + blockIdx.x * LPB + grp;
     if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
     if (dense && dld == n && doff == 1) {
-        load_row_f64<T, TN>(b0, dense + (size_t)r * n, n, tid);   // padded row: slot 0 is a pad
+        load_row_f64<T, TN, PADL>(b0, dense + (size_t)r * n, n, tid);   // padded row: slot 0 is a pad
     } else if (dense) {
         const double* src = dense + (size_t)r * dld + doff;
 #pragma unroll 8
-        for (int i = tid; i < NX; i += TN) b0[i + 1] = (T)src[i];
+        for (int i = tid; i < NX; i += TN) b0[lp<PADL>(i + 1)] = (T)src[i];
     } else {
-        for (int i = tid; i < NX; i += TN) b0[i + 1] = T(0);
+        for (int i = tid; i < NX; i += TN) b0[lp<PADL>(i + 1)] = T(0);
     }
     line_sync<TN>(grp);
     if (ring) {
         // ring: bottom row (nx+1), top row (nx+1), left column (ny-1), right column (ny-1)
         const int nxp1 = NX + 2;
         if (tid == 0) {
-            b0[1] += (T)(ring[2 * nxp1 + r] * ih2);
-            b0[NX] += (T)(ring[2 * nxp1 + NY + r] * ih2);
+            b0[lp<PADL>(1)] += (T)(ring[2 * nxp1 + r] * ih2);
+            b0[lp<PADL>(NX)] += (T)(ring[2 * nxp1 + NY + r] * ih2);
         }
         line_sync<TN>(grp);
         if (r == 0)
-            for (int i = tid; i < NX; i += TN) b0[i + 1] += (T)(ring[i + 1] * ih2);
+            for (int i = tid; i < NX; i += TN) b0[lp<PADL>(i + 1)] += (T)(ring[i + 1] * ih2);
         if (r == NY - 1)
-            for (int i = tid; i < NX; i += TN) b0[i + 1] += (T)(ring[nxp1 + i + 1] * ih2);
+            for (int i = tid; i < NX; i += TN) b0[lp<PADL>(i + 1)] += (T)(ring[nxp1 + i + 1] * ih2);
         line_sync<TN>(grp);
     }
     if (gam.base) {
         const double* gv = gam.get();
         const int a0 = aff_row_ptr[r], a1 = aff_row_ptr[r + 1];
-        for (int a = a0 + tid; a < a1; a += TN) b0[aff_node[a] - r * n] += (T)(gsign * gv[a]);
+        for (int a = a0 + tid; a < a1; a += TN) b0[lp<PADL>(aff_node[a] - r * n)] += (T)(gsign * gv[a]);
         line_sync<TN>(grp);
     }
-    T* res = dst_line<T, FP>(b0, b1, s_tw, n, logn, tid, grp, tot);
+    T* res = dst_line<T, FP, PADL>(b0, b1, s_tw, n, logn, tid, grp, tot);
     if (tid == 0) res[0] = T(0);
     line_sync<TN>(grp);
-    store_row_vec<T, TN>(out + (size_t)r * n, res, n, tid);
+    store_row_vec<T, TN, PADL>(out + (size_t)r * n, res, n, tid);
 }
 
 template <typename T, int WARPS, int FP>
@@ -660,10 +757,12 @@ __device__ __forceinline__ void
 cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1, T* __restrict__ buf,
           const T* __restrict__ lam_x, const T* __restrict__ lam_y, T norm, const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP);
+    constexpr bool PADL = padded_lines(FP);   // lines in the padded layout (lp)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);   // synchronised with the tile below
     constexpr int PAD = sizeof(T) == 4 ? 4 : 2;
-    const int stride = 2 * n + PAD;
+    const int LN = line_len(n, FP);
+    const int stride = 2 * LN + PAD;
     T* s_lam = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));   // lam_y, NY values
     T* lines = s_lam + n;
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
@@ -694,7 +793,7 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
                 const int rr = t / VPR, q = t - rr * VPR;
                 const T* vs = reinterpret_cast<const T*>(&v[b]);
 #pragma unroll
-                for (int c = 0; c < V; ++c) lines[(q * V + c) * stride + rr + 1] = vs[c];
+                for (int c = 0; c < V; ++c) lines[(q * V + c) * stride + lp<PADL>(rr + 1)] = vs[c];
             }
         }
     }
@@ -702,16 +801,16 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
     const int p = col0 + grp;
     if (p >= 1 && p <= NX) {   // uniform over the column's threads
         T* b0 = lines + grp * stride;
-        T* b1 = b0 + n;
+        T* b1 = b0 + LN;
         // forward transform, division, inverse transform: one copy of the transform code
         T* in = b0;
         T* other = b1;
         const T lx = lam_x[p - 1];
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
-            T* f = dst_line<T, FP>(in, other, s_tw, n, logn, tid, grp, tot);
+            T* f = dst_line<T, FP, PADL>(in, other, s_tw, n, logn, tid, grp, tot);
             if (pass == 0) {
-                for (int l = tid; l < NY; l += TN) f[l + 1] = f[l + 1] * (norm / (lx + s_lam[l]));
+                for (int l = tid; l < NY; l += TN) f[lp<PADL>(l + 1)] = f[lp<PADL>(l + 1)] * (norm / (lx + s_lam[l]));
                 line_sync<TN>(grp);
             }
             other = (f == in) ? other : in;
@@ -719,7 +818,7 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
         }
         // bring the result back to b0 so that the tile store below has a fixed layout
         if (in != b0) {
-            for (int l = tid; l < NY; l += TN) b0[l + 1] = in[l + 1];
+            for (int l = tid; l < NY; l += TN) b0[lp<PADL>(l + 1)] = in[lp<PADL>(l + 1)];
         }
     }
     __syncthreads();
@@ -731,7 +830,7 @@ cols_body(int NX, int NY, int n, int logn, int in0, int in1, int out0, int out1,
 #pragma unroll
         for (int c = 0; c < V; ++c) {
             const int pc = col0 + q * V + c;
-            vs[c] = (pc >= 1 && pc <= NX) ? lines[(q * V + c) * stride + rr + 1] : T(0);
+            vs[c] = (pc >= 1 && pc <= NX) ? lines[(q * V + c) * stride + lp<PADL>(rr + 1)] : T(0);
         }
         *reinterpret_cast<VT*>(buf + (size_t)rr * ld + col0 + q * V) = v;
     }
@@ -761,36 +860,38 @@ rows_inv_body(int NX, int NY, int n, int logn, int row0, int nrows, const T* __r
               double* __restrict__ out64, int old, int ooff, const uint8_t* __restrict__ cls,
               const cpx<T>* __restrict__ g_tw) {
     constexpr int TN = line_threads(FP), LPB = WARPS * 32 / TN;
+    constexpr bool PADL = padded_lines(FP);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const cpx<T>* s_tw = block_twiddles<FP, T>(smem_raw, g_tw, n);
     const int grp = threadIdx.x / TN, tid = threadIdx.x - grp * TN;
+    const int LN = line_len(n, FP);
     T* lines = reinterpret_cast<T*>(smem_raw + twiddle_smem<T>(n, FP));
-    T* b0 = lines + (size_t)grp * (2 * n);
-    T* b1 = b0 + n;
-    T* tot = lines + (size_t)LPB * 2 * n + grp * kLineScratch;
+    T* b0 = lines + (size_t)grp * (2 * LN);
+    T* b1 = b0 + LN;
+    T* tot = lines + (size_t)LPB * 2 * LN + grp * kLineScratch;
     if (FP == 0) __syncthreads();
     const int r = row0 + blockIdx.x * LPB + grp;
     if (r >= row0 + nrows || r >= NY) return;   // uniform over the line's threads
-    load_row_vec<T, TN>(b0, in + (size_t)r * n, n, tid);
+    load_row_vec<T, TN, PADL>(b0, in + (size_t)r * n, n, tid);
     line_sync<TN>(grp);
-    T* res = dst_line<T, FP>(b0, b1, s_tw, n, logn, tid, grp, tot);
+    T* res = dst_line<T, FP, PADL>(b0, b1, s_tw, n, logn, tid, grp, tot);
     if (MODE == INV_STORE_T) {
         if (tid == 0) res[0] = T(0);
         line_sync<TN>(grp);
-        store_row_vec<T, TN>(outT + (size_t)r * n, res, n, tid);
+        store_row_vec<T, TN, PADL>(outT + (size_t)r * n, res, n, tid);
     } else if (MODE == INV_STORE_F64) {
         double* dst = out64 + (size_t)r * old + ooff;
 #pragma unroll 4
-        for (int i = tid; i < NX; i += TN) dst[i] = (double)res[i + 1];
+        for (int i = tid; i < NX; i += TN) dst[i] = (double)res[lp<PADL>(i + 1)];
     } else if (MODE == INV_ACCUM_T) {
         T* dst = outT + (size_t)r * n + 1;
 #pragma unroll 4
-        for (int i = tid; i < NX; i += TN) dst[i] += res[i + 1];
+        for (int i = tid; i < NX; i += TN) dst[i] += res[lp<PADL>(i + 1)];
     } else {
         const size_t base = (size_t)r * n;
 #pragma unroll 4
         for (int i = tid; i < NX; i += TN)
-            if (cls[base + 1 + i] <= CLS_PLUS) out64[base + 1 + i] += (double)res[i + 1];
+            if (cls[base + 1 + i] <= CLS_PLUS) out64[base + 1 + i] += (double)res[lp<PADL>(i + 1)];
     }
 }
 

@@ -38,13 +38,15 @@ constexpr int kRowWarps = 4;
 
 template <typename T>
 inline size_t rows_smem(int n, bool wide = false) {
-    return twiddle_smem<T>(n, fft_path(n, wide)) + (size_t)kRowWarps * (2 * n + kLineScratch) * sizeof(T);
+    const int fp = fft_path(n, wide);
+    return twiddle_smem<T>(n, fp) + (size_t)kRowWarps * (2 * line_len(n, fp) + kLineScratch) * sizeof(T);
 }
 template <typename T>
 inline size_t cols_smem(int n, int C = cols_per_block<T>(), bool wide = false) {
     const int pad = sizeof(T) == 4 ? 4 : 2;
-    return twiddle_smem<T>(n, fft_path(n, wide)) + (size_t)n * sizeof(T) +
-           (size_t)C * (2 * n + pad + kLineScratch) * sizeof(T);
+    const int fp = fft_path(n, wide);
+    return twiddle_smem<T>(n, fp) + (size_t)n * sizeof(T) +
+           (size_t)C * (2 * line_len(n, fp) + pad + kLineScratch) * sizeof(T);
 }
 // Rows per block of the row passes for lines of n points.
 inline int rows_per_block(int n, bool wide) { return kRowWarps * 32 / line_threads(fft_path(n, wide)); }
