@@ -36,16 +36,16 @@ WORKLOAD = ("c1_cylinder_1024: [-2,2]^2, 1024x1024 cells (1023^2 unknowns), one 
 # DRAM traffic per launch of the dominant kernel from the committed ncu capture, valid for
 # the kernel source hash below (null otherwise).
 NCU_TRAFFIC = {
-    # python -m paper_2109_13628_gb300.passes --n 1024 --col 0 --batch 40 under ncu --set full
-    # (-k regex:k_cols -c 1): 40 fields in one launch, DRAM 167.7 MB read + 111.9 MB written, L2
-    # (requests from the SMs) 12.75 M read + 5.24 M write sectors; scaled by the fields to the
-    # roofline's launch of 95 fields
-    "dst_cols_f32": {"bytes_per_launch": 279548160 / 40 * 95, "l2_bytes_per_launch": 17989366 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "aaa5adefadcf1624",
+    # python -m paper_2109_13628_gb300.passes --n 1024 --col 0 --batch 40 under ncu --metrics (DRAM
+    # and L2 sector counters, -k regex:k_cols -c 1): 40 fields in one launch, DRAM 167.7 MB read +
+    # 111.7 MB written, L2 (requests from the SMs) 12.92 M read + 5.24 M write sectors; scaled by
+    # the fields to the roofline's launch of 95 fields
+    "dst_cols_f32": {"bytes_per_launch": 279431424 / 40 * 95, "l2_bytes_per_launch": 18158481 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "18e9d663050fbe46",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
-    # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 111.8 MB, L2 11.04 M + 5.24 M
-    "tri_cols_f32": {"bytes_per_launch": 279469824 / 40 * 95, "l2_bytes_per_launch": 16279091 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "aaa5adefadcf1624",
+    # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 112.1 MB, L2 11.08 M + 5.24 M
+    "tri_cols_f32": {"bytes_per_launch": 279818240 / 40 * 95, "l2_bytes_per_launch": 16315596 * 32 / 40 * 95,
+                     "launches": 1, "tile_width": 8, "source_hash": "18e9d663050fbe46",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
 }
 
