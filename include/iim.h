@@ -321,8 +321,8 @@ iim_status iim_box_poisson(const iim_grid* grid, const double* f, const double* 
  * benchmarks, not part of any solve).  Runs, in precision `prec` (IIM_FP64 or IIM_MIXED = FP32
  * transforms) and with the geometry's current column pass and tile width, the three passes of
  * the Sec. 4.2 rectangular solve on `batch` synthetic fields of g's grid: forward row transforms
- * of a dense FP64 field (one launch per field), the column pass and the inverse row transforms
- * (one launch over all fields); each pass is launched `reps` times back to back inside a CUDA
+ * of dense FP64 fields, the column pass and the inverse row transforms, each pass one launch
+ * over all fields; each pass is launched `reps` times back to back inside a CUDA
  * graph of its own, timed with CUDA events around one launch of that graph.  Outputs (host): us[3] = average device time per
  * launch in microseconds, bytes[3] = algorithmic bytes one launch moves (inputs read once,
  * outputs written once).  The call allocates and frees its own device scratch (3 fields), uses

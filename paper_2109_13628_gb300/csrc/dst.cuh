@@ -736,15 +736,17 @@ rows_fwd_body(int NX, int NY, int n, int logn, int row0, int nrows, const double
     store_row_vec<T, TN, PADL>(out + (size_t)r * n, res, n, tid);
 }
 
+// blockIdx.y selects one of several fields: dense input dfs and output ofs elements apart.
 template <typename T, int WARPS, int FP>
 __global__ void __launch_bounds__(WARPS * 32)
 k_rows_fwd(int NX, int NY, int n, int logn, int row0, int nrows, const double* __restrict__ dense, int dld, int doff,
            const double* __restrict__ ring, double ih2, const int* __restrict__ aff_row_ptr,
            const int* __restrict__ aff_node, VecArg gam, double gsign, const cpx<T>* __restrict__ g_tw,
-           T* __restrict__ out, const int* __restrict__ stop) {
+           T* __restrict__ out, const int* __restrict__ stop, long dfs, long ofs) {
     if (stop && *stop) return;
-    rows_fwd_body<T, WARPS, FP>(NX, NY, n, logn, row0, nrows, dense, dld, doff, ring, ih2, aff_row_ptr, aff_node, gam,
-                                gsign, g_tw, out);
+    rows_fwd_body<T, WARPS, FP>(NX, NY, n, logn, row0, nrows, dense ? dense + (long)blockIdx.y * dfs : nullptr, dld,
+                                doff, ring, ih2, aff_row_ptr, aff_node, gam, gsign, g_tw,
+                                out + (long)blockIdx.y * ofs);
 }
 
 // Column pass on padded columns p = 1..NX (p = 0 is the pad): forward y transform, division
@@ -888,10 +890,38 @@ rows_inv_body(int NX, int NY, int n, int logn, int row0, int nrows, const T* __r
 #pragma unroll 4
         for (int i = tid; i < NX; i += TN) dst[i] += res[lp<PADL>(i + 1)];
     } else {
+        // padded positions p = 1..NX of the row: p = 1 alone, then the pairs (p, p + 1) for even
+        // p, each one 16-byte FP64 read-modify-write (rows start on even indices) with a 2-byte
+        // class load; each lane issues all its loads before its first add
         const size_t base = (size_t)r * n;
-#pragma unroll 4
-        for (int i = tid; i < NX; i += TN)
-            if (cls[base + 1 + i] <= CLS_PLUS) out64[base + 1 + i] += (double)res[lp<PADL>(i + 1)];
+        if (tid == 0 && cls[base + 1] <= CLS_PLUS) out64[base + 1] += (double)res[lp<PADL>(1)];
+        const int npair = (NX - 1) / 2;
+        double2* o2 = reinterpret_cast<double2*>(out64 + base + 2);
+        const uchar2* c2 = reinterpret_cast<const uchar2*>(cls + base + 2);
+        constexpr int B = 8;
+        for (int q0 = tid; q0 < npair; q0 += B * TN) {
+            double2 o[B];
+            uchar2 c[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int q = q0 + b * TN;
+                if (q < npair) {
+                    c[b] = c2[q];
+                    o[b] = o2[q];
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int q = q0 + b * TN;
+                if (q < npair) {
+                    const int pp = 2 + 2 * q;   // even: lp keeps (pp, pp + 1) adjacent
+                    const vec2_t<T> v = *reinterpret_cast<const vec2_t<T>*>(res + lp<PADL>(pp));
+                    if (c[b].x <= CLS_PLUS) o[b].x += (double)v.x;
+                    if (c[b].y <= CLS_PLUS) o[b].y += (double)v.y;
+                    o2[q] = o[b];
+                }
+            }
+        }
     }
 }
 

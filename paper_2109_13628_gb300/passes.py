@@ -4,8 +4,9 @@ one JSON line: microseconds and algorithmic bytes per launch, and the column pas
 
     python -m paper_2109_13628_gb300.passes --n 1024 --col 1 --batch 40
 
---col: 1 tridiagonal scans, 0 column DSTs; --batch: fields per launch of the column and inverse
-row passes; --prec: mixed (FP32 transforms) or fp64.  Used to profile one pass in isolation."""
+--col: 1 tridiagonal scans, 0 column DSTs; --batch: fields per launch of each pass (forward rows,
+column pass, inverse rows); --prec: mixed (FP32 transforms) or fp64.  Used to profile one pass in
+isolation."""
 from __future__ import annotations
 
 import argparse
