@@ -552,6 +552,16 @@ dense_matvec4_body(int n, const float* __restrict__ M, long ldm, const double* _
         const float4* v4 = reinterpret_cast<const float4*>(s_v + head * stride);
         const int nq = (n - head) >> 2;
         int q = lane;
+        // the at most seven vectors of the remainder loop are loaded first, so that they are in
+        // flight together with the main batches; the sums keep the order of the loops below
+        int qr = lane;
+        while (qr + 7 * 32 < nq) qr += 8 * 32;
+        float4 xr[7];
+#pragma unroll
+        for (int u = 0; u < 7; ++u) {
+            const int qq = qr + 32 * u;
+            xr[u] = qq < nq ? r4[qq] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (; q + 7 * 32 < nq; q += 8 * 32) {
             float4 x[8];
 #pragma unroll
@@ -563,9 +573,13 @@ dense_matvec4_body(int n, const float* __restrict__ M, long ldm, const double* _
                 a = fmaf(x[u].x, y.x, fmaf(x[u].y, y.y, fmaf(x[u].z, y.z, fmaf(x[u].w, y.w, a))));
             }
         }
-        for (; q < nq; q += 32) {
-            const float4 x = r4[q], y = v4[q];
-            a1 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a1))));
+#pragma unroll
+        for (int u = 0; u < 7; ++u) {
+            const int qq = qr + 32 * u;   // qr == q here
+            if (qq < nq) {
+                const float4 x = xr[u], y = v4[qq];
+                a1 = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, a1))));
+            }
         }
         const int rem = (n - head) & 3;
         if (lane < rem) {
