@@ -49,3 +49,6 @@ def test_invalid_arguments_rejected_before_any_cuda_call():
     assert lib.iim_total_pressure_problem(None, None, None, None, None, U, 0.0, None, None, None, None, None) == -1
     assert lib.iim_wall_values(None, None, None, None) == -1
     assert lib.iim_total_pressure(None, None, None, None, U, 0.0, None, None, None, None, None, None) == -1
+    on, t = ctypes.c_int(), ctypes.c_int()
+    assert lib.iim_net_set_tensor_cores(None, 1) == -1
+    assert lib.iim_net_tensor_core_status(None, ctypes.byref(on), ctypes.byref(t)) == -1
