@@ -41,21 +41,21 @@ NCU_TRAFFIC = {
     # 111.7 MB written, L2 (requests from the SMs) 12.92 M read + 5.24 M write sectors; scaled by
     # the fields to the roofline's launch of 95 fields
     "dst_cols_f32": {"bytes_per_launch": 279431424 / 40 * 95, "l2_bytes_per_launch": 18158481 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "a35ca7d4819aba6f",
+                     "launches": 1, "tile_width": 8, "source_hash": "9d871bd9078dccd9",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
     # the same with --col 1 (-k regex:k_cols_scan): DRAM 167.7 MB + 112.1 MB, L2 11.08 M + 5.24 M
     "tri_cols_f32": {"bytes_per_launch": 279818240 / 40 * 95, "l2_bytes_per_launch": 16315596 * 32 / 40 * 95,
-                     "launches": 1, "tile_width": 8, "source_hash": "a35ca7d4819aba6f",
+                     "launches": 1, "tile_width": 8, "source_hash": "9d871bd9078dccd9",
                      "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
     # the same with --col 1, -k regex:k_rows_inv (FP32-store mode, the form iim_time_box_passes
     # times): DRAM 167.7 MB read + 117.8 MB written, L2 9.12 M + 5.24 M sectors
     # the same, -k regex:k_rows_fwd (dense FP64 input rows, FP32 output): DRAM 335.4 MB read +
     # 132.3 MB written (algorithmic 40 x 1023^2 x 12 B = 502.3 MB), L2 15.22 M + 5.24 M sectors
     "dst_rows_fwd_f32": {"bytes_per_launch": 467641088 / 40 * 95, "l2_bytes_per_launch": 20460365 * 32 / 40 * 95,
-                         "launches": 1, "tile_width": None, "source_hash": "a35ca7d4819aba6f",
+                         "launches": 1, "tile_width": None, "source_hash": "9d871bd9078dccd9",
                          "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
     "dst_rows_inv_f32": {"bytes_per_launch": 285513728 / 40 * 95, "l2_bytes_per_launch": 14361815 * 32 / 40 * 95,
-                         "launches": 1, "tile_width": None, "source_hash": "a35ca7d4819aba6f",
+                         "launches": 1, "tile_width": None, "source_hash": "9d871bd9078dccd9",
                          "note": "one launch over 40 fields of 1023^2 (cold caches under ncu), scaled to 95 fields"},
 }
 

@@ -136,8 +136,9 @@ template <>
 __device__ __forceinline__ void dft<double, 16>(cpx<double>* v) { dft16_impl(v); }
 
 // Position of line element j in a line buffer: plain (j), or padded with two elements after
-// every 32 (the column pass's register paths), which keeps each lane's run of 32 consecutive
-// elements in its own banks when the lanes of a warp store contiguous chunks.
+// every 32 (the line buffers of the register paths, n = 512 and 1024), which keeps each lane's
+// run of 32 consecutive elements in its own banks when the lanes of a warp store contiguous
+// chunks.
 template <bool PADL>
 __host__ __device__ __forceinline__ constexpr int lp(int j) { return PADL ? j + ((j >> 5) << 1) : j; }
 
