@@ -373,8 +373,8 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
     if not rows:
         return None
     # the net alone at the evaluation size: tensor-core and CUDA-core hidden layers
-    fwd = {("tensor_cores" if tc else "cuda_cores"): learned.time_forward(eval_n - 1, tensor_cores=tc)
-           for tc in (True, False)}
+    fwd = {name: learned.time_forward(eval_n - 1, tensor_cores=tc)
+           for name, tc in (("tensor_cores", 2), ("tensor_cores_hidden_only", 1), ("cuda_cores", 0))}
     mean = lambda tag, k: float(np.mean([r[tag][k] for r in rows]))
     return {"config": f"train {train_count} method solves at {train_n}^2 (random 2-5 circles/ellipses, Gaussian "
                       f"vortices; 8 grid symmetries), eval {len(rows)} unseen {eval_n}^2 geometries, mixed to 1e-10",
@@ -390,7 +390,7 @@ def learned_c5(iim, dev, opts_for, train_n=128, train_count=256, train_s=30.0, e
                               "max_rel_res": max(r["learned"][3] for r in rows)},
             "net_forward": {k: {"ms": v["forward_ms"], "kernels": v["kernels"]} for k, v in fwd.items()},
             "guess_path": "body-free box solve (FP32 transforms) of the device omega, net input, forward pass "
-                          "(hidden layers on the tensor cores), composition; all inside the learned solve's events"}
+                          "(every layer on the tensor cores), composition; all inside the learned solve's events"}
 
 
 def rk3_c2(iim, inputs, dev, steps=3):

@@ -508,12 +508,13 @@ iim_status iim_net_prepare_input(int nx, int ny, const double* omega, const doub
 /* psi_guess = u_box + y / s_out (n values). */
 iim_status iim_net_compose_guess(long long n, const double* u_box, const float* y, float s_out,
                                  double* psi_guess, iim_stream stream);
-/* Tensor cores for the hidden 32 -> 32 convolutions (on = 1, the default; 0 = the CUDA-core
- * kernel).  On: each such convolution (forward, and the input gradient of training) is an
- * implicit GEMM on the fifth-generation tensor cores: the layer input is rounded to BF16, the
- * products with the BF16 weights are summed in FP32 in tensor memory; the first and last layers
- * (3 -> 32, 32 -> 1) stay on the CUDA cores.  Off: every layer keeps FP32 inputs.
- * Errors: IIM_ERR_INVALID_ARG (net NULL, on not 0 or 1). */
+/* Convolutions on the tensor cores: on = 2 (the default) every layer, 1 the hidden 32 -> 32
+ * layers only, 0 none (the CUDA-core kernel).  A convolution on the tensor cores (forward, and the
+ * input gradient of training) is an implicit GEMM on the fifth-generation tensor cores: the layer
+ * input is rounded to BF16, the products with the BF16 weights are summed in FP32 in tensor
+ * memory; layers with fewer than 16 or 32 channels are padded with zero channels to the MMA
+ * shape.  The weight gradient stays on the CUDA cores.  Layers off the tensor cores keep FP32
+ * inputs.  Errors: IIM_ERR_INVALID_ARG (net NULL, on not 0, 1 or 2). */
 iim_status iim_net_set_tensor_cores(iim_net net, int on);
 /* *on = the current setting; *timed_out = 1 if a tensor-core convolution of this net ever gave up
  * waiting (one second) for its MMAs and skipped its output, else 0.  Synchronizes the device.

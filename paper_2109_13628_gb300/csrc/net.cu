@@ -37,7 +37,7 @@ struct iim_net_s {
     float* red = nullptr;                // reductions
     long long cap = 0;                   // floats per activation buffer
     float* h_red = nullptr;              // pinned
-    int tc = 0;                          // 32 -> 32 convolutions on the tensor cores (k_conv_tc)
+    int tc = 0;                          // tensor cores (k_conv_tc): 0 off, 1 the 32 -> 32 layers, 2 every layer
     __nv_bfloat16* wtc = nullptr;        // one layer's weights in the tensor-core operand layout
     int* tc_err = nullptr;               // set by k_conv_tc when its wait for the MMAs timed out
 };
@@ -101,34 +101,38 @@ k_conv(const float* __restrict__ x, const float* __restrict__ gate, const __nv_b
     }
 }
 
-// 32 -> 32 channel convolution as an implicit GEMM on the tensor cores (tcgen05, BF16 operands,
-// FP32 accumulation in tensor memory).  One CTA computes a run of TC_M = 128 pixels of one image
-// row for all 32 output channels: D (128 x 32) = sum over the 9 taps and two 16-channel halves of
-// A_tap (128 pixels x 16 channels) * B_tap^T (32 outputs x 16 channels), 18 MMAs of
-// M = 128, N = 32, K = 16.
+// Convolution of Ci <= 32 input to Co <= 32 output channels as an implicit GEMM on the tensor
+// cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).  One CTA computes a run of
+// TC_M = 128 pixels of one image row for NO output columns (16 or 32, the MMA's N; outputs
+// o >= Co are zero columns): D (128 x NO) = sum over the 9 taps and the CG / 2 16-channel parts of
+// the CG staged 8-channel groups (CG = 2 or 4; channels c >= Ci are zero) of
+// A_tap (128 pixels x 16 channels) * B_tap^T (NO outputs x 16 channels), MMAs of M = 128, K = 16.
 //
 // Shared memory, in 16-byte units of 8 BF16 channels:
-//   A: input rows row - d, row, row + d (r = 0, 1, 2), channel group g (8 channels), pixel
-//      p = 0 .. NP - 1 standing for column x0 - d + p (NP = 128 + 2 d), unit (r * 4 + g) * NP + p;
-//      zero outside the image.  The operand of tap (ky, kx) starts at pixel kx * d of row ky:
-//      consecutive pixels are 16 bytes apart (stride byte offset 128 per 8 rows), the second
-//      channel group of an MMA is NP units further (leading byte offset).
-//   B: tap t, channel group g, output o: unit (t * 4 + g) * 32 + o (packed by k_pack_w_tc).
+//   A: input rows row - d, row, row + d (r = 0, 1, 2), channel group g, pixel p = 0 .. NP - 1
+//      standing for column x0 - d + p (NP = 128 + 2 d), unit (r * CG + g) * NP + p; zero outside
+//      the image.  The operand of tap (ky, kx) starts at pixel kx * d of row ky: consecutive
+//      pixels are 16 bytes apart (stride byte offset 128 per 8 rows), the second channel group of
+//      an MMA is NP units further (leading byte offset).
+//   B: tap t, channel group g, output o: unit (t * CG + g) * NO + o (packed by k_pack_w_tc).
 // The input is rounded to BF16 on the way in (optionally gated by gate > 0, as k_conv); the
 // epilogue adds the bias, applies the ReLU and writes FP32 in the NCHW layout of k_conv.
 // A wait for the MMAs that runs past one second sets *err and skips the epilogue.
 constexpr int TC_M = 128, TC_C = 32;
 
-__host__ __device__ constexpr size_t conv_tc_smem(int d) {
-    return (size_t)16 * (12 * (TC_M + 2 * d) + 9 * 4 * TC_C) + 16;
+__host__ __device__ constexpr size_t conv_tc_smem(int d, int cg, int no) {
+    return (size_t)16 * (3 * cg * (TC_M + 2 * d) + 9 * cg * no) + 16;
 }
 
-// wp[((t * 4 + g) * 32 + o) * 8 + e] = w[(o * 32 + 8 g + e) * 9 + t]
-__global__ void k_pack_w_tc(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wp) {
+// wp[((t * CG + g) * NO + o) * 8 + e] = w[(o * Ci + 8 g + e) * 9 + t], zero for o >= Co or
+// 8 g + e >= Ci
+template <int CG, int NO>
+__global__ void k_pack_w_tc(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wp, int Ci, int Co) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 9 * 4 * TC_C * 8) return;
-    const int e = i & 7, o = (i >> 3) & 31, g = (i >> 8) & 3, t = i >> 10;
-    wp[i] = w[(o * TC_C + 8 * g + e) * 9 + t];
+    if (i >= 9 * CG * NO * 8) return;
+    const int e = i & 7, o = (i >> 3) % NO, g = ((i >> 3) / NO) % CG, t = (i >> 3) / (NO * CG);
+    const int c = 8 * g + e;
+    wp[i] = (o < Co && c < Ci) ? w[(o * Ci + c) * 9 + t] : __float2bfloat16(0.f);
 }
 
 __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
@@ -136,49 +140,53 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&v);
 }
 
+template <int CG, int NO>
 __global__ void __launch_bounds__(128)
 k_conv_tc(const float* __restrict__ x, const float* __restrict__ gate, const __nv_bfloat16* __restrict__ wp,
-          const float* __restrict__ bias, float* __restrict__ y, int H, int W, int d, int relu, int* __restrict__ err) {
+          const float* __restrict__ bias, float* __restrict__ y, int Ci, int Co, int H, int W, int d, int relu,
+          int* __restrict__ err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int NP = TC_M + 2 * d;
     uint4* sA = reinterpret_cast<uint4*>(smem_raw);
-    uint4* sB = sA + 12 * NP;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * 4 * TC_C);
+    uint4* sB = sA + 3 * CG * NP;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + 9 * CG * NO);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int x0 = blockIdx.x * TC_M, row = blockIdx.y, b = blockIdx.z;
     const size_t plane = (size_t)H * W;
-    const float* xb = x + (size_t)b * TC_C * plane;
-    const float* gb = gate ? gate + (size_t)b * TC_C * plane : nullptr;
+    const float* xb = x + (size_t)b * Ci * plane;
+    const float* gb = gate ? gate + (size_t)b * Ci * plane : nullptr;
 
     if (warp == 0) tc::tmem_alloc(tslot, 32);
     if (tid == 0) tc::mbar_init(mbar, 1);
     const uint4* wsrc = reinterpret_cast<const uint4*>(wp);
-    for (int i = tid; i < 9 * 4 * TC_C; i += 128) sB[i] = wsrc[i];
+    for (int i = tid; i < 9 * CG * NO; i += 128) sB[i] = wsrc[i];
     // UB units per thread and round, all their loads issued before any conversion
     constexpr int UB = 2;
-    const int units = 12 * NP;
+    const int units = 3 * CG * NP;
     for (int u0 = tid; u0 < units; u0 += UB * 128) {
         float v[UB][8];
         bool in[UB];
         size_t off[UB];
+        int c0[UB];
 #pragma unroll
         for (int q = 0; q < UB; ++q) {
             const int u = u0 + q * 128;
             const int rg = u / NP, p = u - rg * NP;
-            const int r = rg >> 2, g = rg & 3;
+            const int r = rg / CG, g = rg - r * CG;
             const int gy = row + (r - 1) * d, gx = x0 - d + p;
             in[q] = u < units && gy >= 0 && gy < H && gx >= 0 && gx < W;
+            c0[q] = 8 * g;
             off[q] = in[q] ? (size_t)(8 * g) * plane + (size_t)gy * W + gx : 0;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[q][e] = in[q] ? xb[off[q] + (size_t)e * plane] : 0.f;
+            for (int e = 0; e < 8; ++e) v[q][e] = (in[q] && c0[q] + e < Ci) ? xb[off[q] + (size_t)e * plane] : 0.f;
         }
         if (gb) {
 #pragma unroll
             for (int q = 0; q < UB; ++q)
 #pragma unroll
                 for (int e = 0; e < 8; ++e)
-                    if (in[q] && !(gb[off[q] + (size_t)e * plane] > 0.f)) v[q][e] = 0.f;
+                    if (in[q] && c0[q] + e < Ci && !(gb[off[q] + (size_t)e * plane] > 0.f)) v[q][e] = 0.f;
         }
 #pragma unroll
         for (int q = 0; q < UB; ++q) {
@@ -195,15 +203,15 @@ k_conv_tc(const float* __restrict__ x, const float* __restrict__ gate, const __n
     const uint32_t tmem = *tslot;
     if (tid == 0) {
         const uint32_t a0 = tc::smem_u32(sA), b0 = tc::smem_u32(sB);
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, TC_C);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_M, NO);
 #pragma unroll 1
         for (int t = 0; t < 9; ++t) {
             const int ky = t / 3, kx = t - 3 * ky;
 #pragma unroll
-            for (int s = 0; s < 2; ++s) {
+            for (int s = 0; s < CG / 2; ++s) {
                 const uint64_t ad =
-                    tc::desc_kmajor(a0 + (uint32_t)(16 * ((ky * 4 + 2 * s) * NP + kx * d)), (uint32_t)(16 * NP), 128u);
-                const uint64_t bd = tc::desc_kmajor(b0 + (uint32_t)(16 * (t * 4 + 2 * s) * TC_C), 16u * TC_C, 128u);
+                    tc::desc_kmajor(a0 + (uint32_t)(16 * ((ky * CG + 2 * s) * NP + kx * d)), (uint32_t)(16 * NP), 128u);
+                const uint64_t bd = tc::desc_kmajor(b0 + (uint32_t)(16 * (t * CG + 2 * s) * NO), 16u * NO, 128u);
                 tc::mma_bf16(tmem, ad, bd, idesc, (t | s) != 0);
             }
         }
@@ -213,13 +221,15 @@ k_conv_tc(const float* __restrict__ x, const float* __restrict__ gate, const __n
     const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(mbar, 0, 1000000000ull));
     tc::fence_after_sync();
     if (ok) {
-        float acc[32];
-        tc::tmem_ld_32x32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+        float acc[NO];
+        if constexpr (NO == 32) tc::tmem_ld_32x32(tmem + ((uint32_t)(32 * warp) << 16), acc);
+        else tc::tmem_ld_32x16(tmem + ((uint32_t)(32 * warp) << 16), acc);
         const int gx = x0 + 32 * warp + lane;
         if (gx < W) {
-            float* yo = y + (size_t)b * TC_C * plane + (size_t)row * W + gx;
+            float* yo = y + (size_t)b * Co * plane + (size_t)row * W + gx;
 #pragma unroll
-            for (int o = 0; o < TC_C; ++o) {
+            for (int o = 0; o < NO; ++o) {
+                if (o >= Co) break;
                 float v = acc[o] + (bias ? bias[o] : 0.f);
                 if (relu) v = fmaxf(v, 0.f);
                 yo[(size_t)o * plane] = v;
@@ -397,16 +407,23 @@ static size_t conv_smem(int d, int co_t) { return sizeof(float) * ((size_t)(TX +
 static iim_status conv(iim_net_s* net, const float* x, const float* gate, const __nv_bfloat16* w, const float* bias,
                        float* y, int B, int Ci, int Co, int H, int W, int d, int relu, cudaStream_t s) {
     const dim3 blk(TX, TY);
-    if (net->tc && Ci == TC_C && Co == TC_C) {
-        launch("net_pack_w_tc", 0.0, 0.0, k_pack_w_tc, (9 * 4 * TC_C * 8 + 255) / 256, 256, 0, s, w, net->wtc);
-        IIM_LAUNCHED();
-        const size_t sm = conv_tc_smem(d);
-        IIM_CHECK(allow_smem(k_conv_tc, sm));
-        launch("net_conv_tc", 4.0 * (double)B * H * W * (Ci * (gate ? 2 : 1) + Co), 18.0 * (double)B * H * W * Ci * Co,
-               k_conv_tc, dim3((W + TC_M - 1) / TC_M, H, B), 128, sm, s, x, gate, (const __nv_bfloat16*)net->wtc, bias, y,
-               H, W, d, relu, net->tc_err);
-        IIM_LAUNCHED();
-        return IIM_OK;
+    // tensor cores: mode 1 the 32 -> 32 layers, mode 2 every layer (K and N padded to 16 / 32)
+    if ((net->tc == 1 && Ci == TC_C && Co == TC_C) || (net->tc == 2 && Ci <= TC_C && Co <= TC_C)) {
+        auto go = [&](auto pack, auto kern, int cg, int no) -> iim_status {
+            launch("net_pack_w_tc", 0.0, 0.0, pack, (9 * cg * no * 8 + 255) / 256, 256, 0, s, w, net->wtc, Ci, Co);
+            IIM_LAUNCHED();
+            const size_t sm = conv_tc_smem(d, cg, no);
+            IIM_CHECK(allow_smem(kern, sm));
+            launch("net_conv_tc", 4.0 * (double)B * H * W * (Ci * (gate ? 2 : 1) + Co),
+                   18.0 * (double)B * H * W * Ci * Co, kern, dim3((W + TC_M - 1) / TC_M, H, B), 128, sm, s, x, gate,
+                   (const __nv_bfloat16*)net->wtc, bias, y, Ci, Co, H, W, d, relu, net->tc_err);
+            IIM_LAUNCHED();
+            return IIM_OK;
+        };
+        if (Ci <= 16 && Co <= 16) return go(k_pack_w_tc<2, 16>, k_conv_tc<2, 16>, 2, 16);
+        if (Ci <= 16) return go(k_pack_w_tc<2, 32>, k_conv_tc<2, 32>, 2, 32);
+        if (Co <= 16) return go(k_pack_w_tc<4, 16>, k_conv_tc<4, 16>, 4, 16);
+        return go(k_pack_w_tc<4, 32>, k_conv_tc<4, 32>, 4, 32);
     }
     if (Co > 1) {
         const int ncot = (Co + 31) / 32;
@@ -534,7 +551,7 @@ extern "C" iim_status iim_net_create(int in_channels, int hidden, int n_layers, 
     if ((e = cudaMalloc(&net->wtc, sizeof(__nv_bfloat16) * 9 * 4 * TC_C * 8)) != cudaSuccess) return fail(e);
     if ((e = cudaMalloc(&net->tc_err, sizeof(int))) != cudaSuccess) return fail(e);
     cudaMemset(net->tc_err, 0, sizeof(int));
-    net->tc = 1;
+    net->tc = 2;
     if ((e = cudaMemcpy(net->p, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice)) != cudaSuccess) return fail(e);
     cudaMemset(net->m, 0, sizeof(float) * off);
     cudaMemset(net->v, 0, sizeof(float) * off);
@@ -641,7 +658,7 @@ extern "C" iim_status iim_net_compose_guess(long long n, const double* u_box, co
 }
 
 extern "C" iim_status iim_net_set_tensor_cores(iim_net net, int on) {
-    if (!net || (on != 0 && on != 1)) return IIM_ERR_INVALID_ARG;
+    if (!net || on < 0 || on > 2) return IIM_ERR_INVALID_ARG;
     net->tc = on;
     return IIM_OK;
 }

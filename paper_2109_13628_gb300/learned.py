@@ -25,7 +25,7 @@ IN_CHANNELS = 3
 
 
 class Net:
-    def __init__(self, in_channels=IN_CHANNELS, hidden=HIDDEN, dilations=DILATIONS, seed=0, tensor_cores=True):
+    def __init__(self, in_channels=IN_CHANNELS, hidden=HIDDEN, dilations=DILATIONS, seed=0, tensor_cores=2):
         lib = B.load()
         d = (ctypes.c_int * len(dilations))(*dilations)
         h = ctypes.c_void_p()
@@ -36,8 +36,9 @@ class Net:
         self.set_tensor_cores(tensor_cores)
 
     def set_tensor_cores(self, on):
-        """32 -> 32 convolutions on the tensor cores (BF16 layer inputs) or the CUDA cores (FP32)."""
-        B._check(B.load().iim_net_set_tensor_cores(self.h, 1 if on else 0), "iim_net_set_tensor_cores")
+        """Convolutions on the tensor cores (BF16 layer inputs): 2 every layer, 1 (or True) the
+        32 -> 32 layers only, 0 (or False) none (FP32 inputs on the CUDA cores)."""
+        B._check(B.load().iim_net_set_tensor_cores(self.h, int(on)), "iim_net_set_tensor_cores")
 
     def tensor_core_status(self):
         """(setting, 1 if a tensor-core convolution ever timed out waiting for its MMAs)."""
@@ -232,7 +233,7 @@ def train(net, data, epochs, batch, lr, time_budget_s=None, seed=0, augment=True
     return losses
 
 
-def time_forward(n, batch=1, reps=10, tensor_cores=True, backward=False, seed=0):
+def time_forward(n, batch=1, reps=10, tensor_cores=2, backward=False, seed=0):
     """Device milliseconds of one forward pass (and, with backward, of one backward pass) of the
     production net on batch x 3 x n x n random inputs: CUDA events around reps launches after
     three warm-up passes."""
@@ -281,8 +282,8 @@ if __name__ == "__main__":
     ap.add_argument("--n", type=int, default=1023)
     ap.add_argument("--batch", type=int, default=1)
     ap.add_argument("--reps", type=int, default=10)
-    ap.add_argument("--tc", type=int, choices=[0, 1], default=1)
+    ap.add_argument("--tc", type=int, choices=[0, 1, 2], default=2)
     ap.add_argument("--backward", action="store_true")
     a = ap.parse_args()
-    r = time_forward(a.n, a.batch, a.reps, bool(a.tc), a.backward)
+    r = time_forward(a.n, a.batch, a.reps, a.tc, a.backward)
     print(json.dumps({"n": a.n, "batch": a.batch, **r}))
